@@ -1,0 +1,25 @@
+"""FP64 CPU oracle of the SVD-compressed KIFMM M2L translation (arXiv 1211.2517).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+this package.  The product path (``paper_1211_2517_gb300``) never imports,
+links or executes anything here, and this package never imports the product.
+The two share only the seeded input generators of ``synth``.
+
+The oracle is plain NumPy in float64: slow, unblocked, written to be read
+against the paper.  Each function cites the section / equation it follows.
+
+Modules:
+  geometry  -- surfaces (Sec. 2.1), the 316 offsets (Sec. 3.1), interaction
+               lists (Sec. 2.1), the Laplace kernel (Sec. 4).
+  m2l       -- dense M2L (Eq. eq-m2l), the fat/thin SVDs and the truncated
+               compressed M2L (Eqs. eq-kfat, fat, thin, eq-cmpM2Ls, evalcmp1),
+               level scaling by homogeneity (Sec. 3.1), the adjoint, the
+               stage-2 per-offset low-rank factors (Eq. eq-lra).
+  upward    -- S2M / M2M (Eqs. eq-s2m, eq-m2m) to make realistic M2L inputs,
+               and direct summation (Eq. eq_eval) for brute-force checks.
+
+Every function here is pinned by a ``-m "not gpu"`` test against a closed
+form, an invariant, a bound or brute force; none is "parity unpinned".
+"""
+from . import geometry, m2l, upward  # noqa: F401
