@@ -1,0 +1,189 @@
+/*
+ * kifmm_m2l.h -- C ABI of the SVD-compressed KIFMM M2L translation on GB300.
+ *
+ * The library implements the multipole-to-local (M2L) translation of the
+ * kernel-independent FMM compressed by the SVD, after Cao, Wen & Rong,
+ * "A SVD accelerated kernel-independent fast multipole method and its
+ * application to BEM" (arXiv 1211.2517):
+ *
+ *   dense M2L            p^{t,d} = sum_{s in I^t} K(t,s) q^{s,u}        (Eq. eq-m2l)
+ *   compressed M2L       p^{t,d} = U~ [ s_l sum_{s in I^t} K~_{t-s} (R~^T q^{s,u}) ]
+ *                                                     (Eqs. eq-cmpM2Ls, evalcmp1)
+ *
+ * with K(t,s)_ij = G(x_i^{t,d}, y_j^{s,u}), G = 1/(4 pi |x-y|) (Sec. 4), the
+ * target's downward check surface x^{t,d} and the source's upward equivalent
+ * surface y^{s,u} both at half-width (1+d) h (Sec. 2.1), I^t the
+ * interaction field (Sec. 2.1), the 316 unit-level cores
+ * K~_o = U~^T K_o R~ from the SVDs of K_fat and K_thin (Sec. 3.1), and the
+ * level scale s_l = (r0 / 2^l)^(-1) from homogeneity (Sec. 3.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status: KIFMM_OK (0) or a negative
+ *    KIFMM_ERR_* code.  No C++ exception crosses this boundary.  The message
+ *    of the last failure on the calling thread is kifmm_m2l_last_error().
+ *  - Surface points: the p^3 - (p-2)^3 = 6(p-1)^2+2 = n grid points
+ *    c + h (1+d) (2 (i,j,k)/(p-1) - 1) with min(i,j,k) = 0 or
+ *    max(i,j,k) = p-1, in lexicographic (i,j,k) order.
+ *  - Offsets: the 316 vectors o in {-3..3}^3 with max|o_i| >= 2, in
+ *    lexicographic order; a pair (t, s) has offset o = t - s (box units).
+ *  - Boxes of a level are given by integer coordinates box_ijk[b] =
+ *    (i,j,k), 0 <= i,j,k < 2^level, int32, row-major [n_boxes][3], no
+ *    duplicates.  Their order is the caller's and indexes the density arrays.
+ *  - Density arrays are float32, row-major [n_boxes][nrhs][n], contiguous.
+ *  - Device pointers must be CUDA device (or managed) memory on the device
+ *    that was current when the plan was made; host pointers are ordinary
+ *    host memory.
+ *  - Streams are passed as a cudaStream_t cast to void* (NULL = legacy
+ *    default stream).  Device work is asynchronous on that stream; argument
+ *    errors are reported synchronously, CUDA launch errors at the call that
+ *    launched, device-side faults at the next synchronising call.
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the
+ *    caller, and work on one (instance, level) state must not run on two
+ *    streams at once (they share the plan's scratch buffers).
+ */
+#ifndef KIFMM_M2L_H
+#define KIFMM_M2L_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define KIFMM_OK               0
+#define KIFMM_ERR_INVALID_ARG  (-1) /* a pointer, size or enum is out of range        */
+#define KIFMM_ERR_UNSUPPORTED  (-2) /* a valid request this build does not implement  */
+#define KIFMM_ERR_CUDA         (-3) /* a CUDA runtime/driver call failed              */
+#define KIFMM_ERR_OOM          (-4) /* host or device allocation failed               */
+#define KIFMM_ERR_TIMEOUT      (-5) /* a bounded device wait ran out                   */
+#define KIFMM_ERR_STATE        (-6) /* call order violated (e.g. apply before set_level) */
+
+/* ---- enums ------------------------------------------------------------- */
+#define KIFMM_KERNEL_LAPLACE   0    /* G(x,y) = 1 / (4 pi |x - y|), Sec. 4 */
+
+/* Arithmetic of the core products sum_o K~_o q~ (Sec. 3.1).  Vt compression
+ * and U expansion are FP32 in every mode. */
+#define KIFMM_PREC_FP32        0    /* FP32 CUDA-core FMA                                  */
+#define KIFMM_PREC_BF16        1    /* tcgen05 BF16 x BF16, FP32 accumulate (1 product)    */
+#define KIFMM_PREC_SPLIT3      2    /* 2-piece BF16 split, 3 products (hi*hi+hi*lo+lo*hi)  */
+#define KIFMM_PREC_SPLIT6      3    /* 3-piece BF16 split, 6 products (all terms <= 2^-16)  */
+
+#define KIFMM_N_OFFSETS        316  /* unique M2L offsets per level, Sec. 3.1 */
+
+/* ---- types ------------------------------------------------------------- */
+typedef struct kifmm_m2l_params {
+    int    kernel_id;  /* KIFMM_KERNEL_LAPLACE (others: KIFMM_ERR_UNSUPPORTED)          */
+    int    p;          /* points per cube edge, 2 <= p <= 12; n = 6(p-1)^2+2             */
+    double eps;        /* rank cutoff eps_1: keep sigma_i >= eps * sigma_0 (Sec. 3.1);
+                          1e-12 <= eps < 1, or eps <= 0 to keep all n                    */
+    double d;          /* surface ratio: surfaces at half-width (1+d) h, 0 <= d <= 2/3   */
+    int    precision;  /* KIFMM_PREC_*                                                   */
+} kifmm_m2l_params;
+
+typedef struct kifmm_m2l_plan_s* kifmm_m2l_plan;   /* opaque; owned by the library */
+
+/* ---- plan lifetime ----------------------------------------------------- */
+
+/* Build the translation operators for `params` (Sec. 3.1, Step 1.4 of the
+ * paper's algorithm): forms the 316 unit-level K_o, takes the SVD of K_fat
+ * in FP64 on the host (TSQR + one-sided Jacobi), truncates at eps (a cut
+ * through a cluster of equal singular values moves past the cluster: values
+ * within 1e-13 sigma_0 count as equal), sets R~ = U~ (K_o^T = K_{-o} for this
+ * radial kernel, so the thin SVD's right basis spans U~'s space), forms
+ * K~_o = U~^T K_o U~ in FP64 and uploads FP32 / BF16-split copies to the
+ * current CUDA device.  The FP64 factors are cached on disk under
+ * $KIFMM_M2L_CACHE (default: no cache) keyed by (kernel, p, d, eps).
+ * On success *out owns device memory until kifmm_m2l_destroy(). */
+int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out);
+
+/* Release every host and device resource of the plan (NULL is a no-op).
+ * The caller must have synchronised streams that used it. */
+int kifmm_m2l_destroy(kifmm_m2l_plan plan);
+
+/* Rank introspection: *r = retained rank, *r_pad = r rounded up to a
+ * multiple of 16 (device layout; the extra columns are zero), *n = surface
+ * points.  Any output pointer may be NULL. */
+int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n);
+
+/* ---- per-level state --------------------------------------------------- */
+
+/* Register the non-empty boxes of one octree level of one FMM instance
+ * (Step 1.2: interaction lists).  `box_ijk` is HOST memory [n_boxes][3]
+ * int32, copied.  `root_halfwidth` is r0 (> 0); boxes of this level have
+ * half-width r0 / 2^level.  Builds the interaction-list pairs grouped by
+ * offset on the host and uploads them.  Replaces an earlier registration of
+ * the same (instance, level).  0 <= level <= 20, n_boxes >= 0, coordinates
+ * in [0, 2^level), instance >= 0. */
+int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth,
+                        int n_boxes, const int32_t* box_ijk);
+
+/* Number of M2L pairs (target, source) of a registered level. */
+int kifmm_m2l_level_pairs(kifmm_m2l_plan plan, int instance, int level, int64_t* n_pairs);
+
+/* ---- the translation --------------------------------------------------- */
+
+/* Compressed M2L of one registered level (Eq. evalcmp1 restricted to M2L):
+ *   q~ = R~^T q_up ;  p~^t = s_l sum_{s in I^t} K~_{t-s} q~^s ;
+ *   p_down = beta * p_down + U~ p~
+ * q_up, p_down: DEVICE float32 [n_boxes][nrhs][n]; they must not overlap.
+ * beta is 0 (overwrite; p_down need not be initialised) or any value
+ * (accumulate, Step 3.1 "add to the downward check potentials").
+ * nrhs >= 1.  Runs on `stream`. */
+int kifmm_m2l_apply(kifmm_m2l_plan plan, int instance, int level, int nrhs,
+                    const float* q_up, float* p_down, float beta, void* stream);
+
+/* Adjoint (transpose) of kifmm_m2l_apply's linear map:
+ *   p~bar = U~^T pbar_down ;  q~bar^s = s_l sum_{t: s in I^t} K~_{t-s}^T p~bar^t ;
+ *   qbar_up = beta * qbar_up + R~ q~bar
+ * applied as the core of the reversed offset, K~_o^T = K~_{-o} (which holds
+ * to FP64 rounding because K_o^T = K_{-o} and R~ = U~; checked at
+ * precompute).  Same layouts and rules as kifmm_m2l_apply. */
+int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nrhs,
+                            const float* pbar_down, float* qbar_up, float beta, void* stream);
+
+/* Uncompressed M2L (Eq. eq-m2l), the baseline the compression is compared
+ * with:  p_down = beta * p_down + s_l sum_{s in I^t} K_{t-s} q^s  with the
+ * FP32 unit-level K_o (formed on first use; 316 n^2 floats of device
+ * memory).  Always FP32 CUDA-core arithmetic, accumulated with atomic adds
+ * (summation order not fixed).  Same layouts and rules. */
+int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs,
+                          const float* q_up, float* p_down, float beta, void* stream);
+
+/* Synchronise `stream` and report device-side failures of earlier applies
+ * on this plan: KIFMM_ERR_TIMEOUT when a bounded wait inside the
+ * tensor-core kernel ran out (results of that apply are invalid; the flag
+ * is cleared), KIFMM_ERR_CUDA on an asynchronous CUDA error. */
+int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
+
+/* ---- host-side introspection (no GPU needed) ----------------------------- */
+
+/* Run the FP64 precompute of kifmm_m2l_precompute on the host only and copy
+ * out its results.  n and r are returned in *n, *r (either may be NULL).
+ * sigma: [n] singular values of K_fat, descending (or NULL);
+ * U: [n][r] row-major retained left basis U~ (or NULL);
+ * C: [316][r][r] row-major unit-level cores K~_o (or NULL).
+ * Call once with the arrays NULL to learn n and r. */
+int kifmm_m2l_factors_host(const kifmm_m2l_params* params, int* n, int* r,
+                           double* sigma, double* U, double* C);
+
+/* Interaction-list pairs of a box set on the host (Sec. 2.1): for every
+ * target t and source s in I^t, one entry (t, s, offset index of t - s).
+ * Entries are sorted by offset index, then target.  Call with
+ * targets == NULL to get the count in *n_pairs; then with arrays of that
+ * length.  Same box rules as kifmm_m2l_set_level. */
+int kifmm_m2l_pairs_host(int level, int n_boxes, const int32_t* box_ijk, int64_t* n_pairs,
+                         int32_t* targets, int32_t* sources, int32_t* offsets);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* kifmm_m2l_last_error(void);
+
+/* Library version string. */
+const char* kifmm_m2l_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIFMM_M2L_H */

@@ -1,0 +1,10 @@
+"""GB300-native SVD-compressed KIFMM M2L translation (arXiv 1211.2517).
+
+The translation p^{t,d} = U~ s_l sum_{s in I^t} K~_{t-s} R~^T q^{s,u} runs
+in hand-written sm_103a kernels behind the C ABI of include/kifmm_m2l.h
+(libkifmm_m2l.so, built in-tree by ``paper_1211_2517_gb300.build``).
+"""
+from ._lib import EXPORTED, KifmmError, lib  # noqa: F401
+from .m2l import M2LPlan, factors_host, pairs_host, surface_count  # noqa: F401
+
+__all__ = ["M2LPlan", "factors_host", "pairs_host", "surface_count", "KifmmError", "lib", "EXPORTED"]

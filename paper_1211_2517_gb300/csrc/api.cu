@@ -1,0 +1,636 @@
+// C ABI of the SVD-compressed M2L (include/kifmm_m2l.h): plan object,
+// per-level interaction state, scratch management and the apply paths.
+//
+// Data layout in device memory (n surface points, r rank, rp = r rounded
+// up to 16, B boxes of a level, R = nrhs):
+//   Rt   [rp][n]   FP32   R~^T, rows r..rp-1 zero            (V^T compression)
+//   U    [n][rp]   FP32   U~, columns r..rp-1 zero           (U expansion)
+//   C    [316][rp][rp] FP32  K~_o, zero-padded               (FP32 core)
+//   Cb   [pieces][316][rp][rp] BF16 split of C              (tensor-core core)
+//   K    [316][n][n] FP32 unit-level K_o (dense baseline, on first use)
+//   per level: pairs grouped by offset (src, dst int32 [P]) for the forward
+//   map and for the adjoint (roles swapped, offset reversed), a tile table
+//   per nrhs, and scratch q~ / p~ FP32 [B*R][rp] plus BF16 pieces of q~
+//   [pieces][B*R + 1][rp] whose last row is zero.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "kifmm_internal.h"
+
+using namespace kifmm;
+
+namespace {
+
+constexpr int kTileRows = 128;
+
+#define KIFMM_CUDA_TRY(expr)                                                                        \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) {                                                                    \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                          \
+            return _e == cudaErrorMemoryAllocation ? KIFMM_ERR_OOM : KIFMM_ERR_CUDA;               \
+        }                                                                                           \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T* ptr = nullptr;
+    size_t count = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        count = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= count && ptr) return cudaSuccess;
+        release();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
+        if (e == cudaSuccess) count = n;
+        else ptr = nullptr;
+        return e;
+    }
+    cudaError_t upload(const T* h, size_t n) {
+        cudaError_t e = ensure(n);
+        if (e != cudaSuccess || n == 0) return e;
+        return cudaMemcpy(ptr, h, n * sizeof(T), cudaMemcpyHostToDevice);
+    }
+};
+
+struct PairSet {
+    DevBuf<int> src, dst;
+    std::vector<int64_t> off_begin;  // [317] prefix by offset
+    std::map<int, std::unique_ptr<DevBuf<Tile>>> tiles;  // per nrhs
+    std::map<int, int> n_tiles;
+};
+
+struct LevelState {
+    int level = 0, n_boxes = 0;
+    double r0 = 1.0;
+    int64_t n_pairs = 0;
+    PairSet fwd, adj;
+};
+
+}  // namespace
+
+struct kifmm_m2l_plan_s {
+    kifmm_m2l_params prm{};
+    int device = 0, num_sms = 0;
+    int n = 0, r = 0, rp = 0;
+    int pieces = 0;   // BF16 pieces of the tensor-core modes
+    int products = 0;
+    double sym_err = 0;
+    std::vector<double> sigma;
+    int n_pad = 0;    // n rounded up to 16 (K of the compression, N of the expansion)
+    int core_hilo = 0;
+    DevBuf<float> C, K;
+    DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
+    DevBuf<int> err_flag;
+    std::map<std::pair<int, int>, std::unique_ptr<LevelState>> levels;
+    // scratch shared by all levels (apply calls on one plan are serialised)
+    DevBuf<float> qt, pt;
+    DevBuf<__nv_bfloat16> qb;
+};
+
+namespace {
+
+int pieces_for(int precision) {
+    switch (precision) {
+        case KIFMM_PREC_BF16: return 1;
+        case KIFMM_PREC_SPLIT3: return 2;
+        case KIFMM_PREC_SPLIT6: return 3;
+        default: return 0;
+    }
+}
+int products_for(int precision) {
+    switch (precision) {
+        case KIFMM_PREC_BF16: return 1;
+        case KIFMM_PREC_SPLIT3: return 3;
+        case KIFMM_PREC_SPLIT6: return 6;
+        default: return 0;
+    }
+}
+
+// host split of FP64 into BF16 pieces (round to nearest even at each step)
+uint16_t bf16_bits_rn(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+float bf16_to_float(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+int build_pairset(const std::vector<int32_t>& tgt, const std::vector<int32_t>& src,
+                  const std::vector<int32_t>& off, PairSet& ps) {
+    ps.off_begin.assign(kOffsets + 1, 0);
+    for (int32_t k : off) ps.off_begin[k + 1]++;
+    for (int k = 0; k < kOffsets; ++k) ps.off_begin[k + 1] += ps.off_begin[k];
+    ps.tiles.clear();
+    ps.n_tiles.clear();
+    KIFMM_CUDA_TRY(ps.src.upload(src.data(), src.size()));
+    KIFMM_CUDA_TRY(ps.dst.upload(tgt.data(), tgt.size()));
+    return KIFMM_OK;
+}
+
+int get_tiles(PairSet& ps, int nrhs, const Tile** out, int* n_out) {
+    auto it = ps.tiles.find(nrhs);
+    if (it == ps.tiles.end()) {
+        std::vector<Tile> h;
+        for (int k = 0; k < kOffsets; ++k) {
+            const int64_t np = ps.off_begin[k + 1] - ps.off_begin[k];
+            const int64_t rows = np * nrhs;
+            for (int64_t r0 = 0; r0 < rows; r0 += kTileRows) {
+                Tile t;
+                t.k = k;
+                t.pair_begin = (int)ps.off_begin[k];
+                t.row0 = (int)r0;
+                t.nrows = (int)std::min<int64_t>(kTileRows, rows - r0);
+                h.push_back(t);
+            }
+        }
+        auto buf = std::make_unique<DevBuf<Tile>>();
+        KIFMM_CUDA_TRY(buf->upload(h.data(), h.size()));
+        ps.n_tiles[nrhs] = (int)h.size();
+        it = ps.tiles.emplace(nrhs, std::move(buf)).first;
+    }
+    *out = it->second->ptr;
+    *n_out = ps.n_tiles[nrhs];
+    return KIFMM_OK;
+}
+
+int check_device(kifmm_m2l_plan plan) {
+    int dev = -1;
+    KIFMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) {
+        set_error("the current CUDA device differs from the plan's device");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    return KIFMM_OK;
+}
+
+LevelState* find_level(kifmm_m2l_plan plan, int instance, int level) {
+    auto it = plan->levels.find({instance, level});
+    return it == plan->levels.end() ? nullptr : it->second.get();
+}
+
+// N per work item of the compression / expansion GEMMs: <= 96, so that the
+// per-K-chunk partial sums of a row fit in registers and four accumulator
+// slots (two partials, two lo) fit in the 512 TMEM columns.
+int chunk_for(int ndim) {
+    const int parts = (ndim + 95) / 96;
+    return ((ndim + parts - 1) / parts + 15) / 16 * 16;
+}
+
+// Shared body of apply / apply_adjoint: x_in -> y_out through
+//   xt = W_in x ; yt = sum_pairs core xt ; y = beta y + s_l W_out yt
+int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* x_in, float* y_out,
+                     float beta, void* stream, bool adjoint) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    LevelState* ls = find_level(plan, instance, level);
+    if (!ls) {
+        set_error("level not registered: call kifmm_m2l_set_level first");
+        return KIFMM_ERR_STATE;
+    }
+    if (nrhs < 1 || (ls->n_boxes > 0 && (!x_in || !y_out))) {
+        set_error("invalid nrhs or NULL density pointer");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(x_in) & 15) || (reinterpret_cast<uintptr_t>(y_out) & 15)) {
+        set_error("density pointers must be 16-byte aligned");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    if (ls->n_boxes == 0) return KIFMM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = plan->n, rp = plan->rp;
+    const long rows = (long)ls->n_boxes * nrhs;
+    if (rows + 1 > (long)INT32_MAX / 2) {
+        set_error("too many box rows");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    const float scale = (float)std::ldexp(1.0 / ls->r0, level);  // (r0 / 2^l)^-1
+    const bool fp32_core = plan->prm.precision == KIFMM_PREC_FP32;
+    const long piece_stride = (rows + 1) * rp;
+    KIFMM_CUDA_TRY(plan->pt.ensure((size_t)rows * rp));
+    if (fp32_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
+    else KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
+
+    // 1. compression  q~ = R~^T q  (adjoint: U~^T pbar; R~ = U~, so one factor
+    //    serves both directions), written as the core's operand; p~ = 0
+    {
+        UmmaArgs a{};
+        a.Af = x_in;
+        a.lda = n;
+        a.k_valid = n;
+        a.m_rows = (int)rows;
+        a.kdim = plan->n_pad;
+        a.B = plan->Rtb.ptr;
+        a.b_groups = 1;
+        a.ndim = rp;
+        a.n_chunk = chunk_for(rp);
+        a.ldd = rp;
+        a.alpha = 1.0f;
+        a.Dp = fp32_core ? nullptr : plan->qb.ptr;
+        a.dp_piece_stride = piece_stride;
+        a.dp_pieces = fp32_core ? 0 : plan->pieces;
+        a.Df = fp32_core ? plan->qt.ptr : nullptr;
+        a.Z = plan->pt.ptr;
+        a.n_products = 6;
+        a.hilo = 1;
+        a.error_flag = plan->err_flag.ptr;
+        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_SPLIT, a, plan->num_sms, s));
+    }
+
+    // 2. core over offset-grouped pairs
+    PairSet& ps = adjoint ? ls->adj : ls->fwd;
+    const Tile* tiles = nullptr;
+    int n_tiles = 0;
+    st = get_tiles(ps, nrhs, &tiles, &n_tiles);
+    if (st != KIFMM_OK) return st;
+    if (fp32_core) {
+        KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp, tiles,
+                                              n_tiles, ps.src.ptr, ps.dst.ptr, nrhs, 1.0f, s));
+    } else {
+        for (int pc = 0; pc < plan->pieces; ++pc)
+            KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
+                                           rp * sizeof(__nv_bfloat16), s));
+        UmmaArgs a{};
+        a.A = plan->qb.ptr;
+        a.a_piece_stride = piece_stride;
+        a.kdim = rp;
+        a.B = plan->Cb.ptr;
+        a.b_groups = kOffsets;
+        a.ndim = rp;
+        a.n_chunk = (plan->core_hilo && plan->products > 1 && rp > 256) ? (rp / 2 + 15) / 16 * 16 : rp;
+        a.tiles = tiles;
+        a.n_tiles = n_tiles;
+        a.src = ps.src.ptr;
+        a.dst = ps.dst.ptr;
+        a.nrhs = nrhs;
+        a.zero_row = (int)rows;
+        a.D = plan->pt.ptr;
+        a.ldd = rp;
+        a.n_products = plan->products;
+        a.hilo = plan->core_hilo;
+        a.error_flag = plan->err_flag.ptr;
+        KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+    }
+
+    // 3. expansion  y = beta y + s_l U~ p~   (adjoint: R~ q~bar; R~ = U~)
+    {
+        UmmaArgs a{};
+        a.Af = plan->pt.ptr;
+        a.lda = rp;
+        a.k_valid = rp;
+        a.m_rows = (int)rows;
+        a.kdim = rp;
+        a.B = plan->Ub.ptr;
+        a.b_groups = 1;
+        a.ndim = plan->n_pad;
+        a.n_chunk = chunk_for(plan->n_pad);
+        a.D = y_out;
+        a.ldd = n;
+        a.alpha = scale;
+        a.beta = beta;
+        a.n_valid = n;
+        a.n_products = 6;
+        a.hilo = 1;
+        a.error_flag = plan->err_flag.ptr;
+        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_STORE, a, plan->num_sms, s));
+    }
+    return KIFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kifmm_m2l_last_error(void) { return kifmm::last_error(); }
+
+const char* kifmm_m2l_version(void) { return "kifmm_m2l 0.1 (sm_103a)"; }
+
+int kifmm_m2l_factors_host(const kifmm_m2l_params* params, int* n, int* r, double* sigma, double* U, double* C) {
+    int st = check_params(params);
+    if (st != KIFMM_OK) return st;
+    Factors f;
+    st = compute_factors(*params, f);
+    if (st != KIFMM_OK) return st;
+    if (n) *n = f.n;
+    if (r) *r = f.r;
+    if (sigma) std::memcpy(sigma, f.sigma.data(), sizeof(double) * f.n);
+    if (U) std::memcpy(U, f.U.data(), sizeof(double) * f.U.size());
+    if (C) std::memcpy(C, f.C.data(), sizeof(double) * f.C.size());
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_pairs_host(int level, int n_boxes, const int32_t* box_ijk, int64_t* n_pairs, int32_t* targets,
+                         int32_t* sources, int32_t* offsets) {
+    if (!n_pairs) {
+        set_error("n_pairs is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    std::vector<int32_t> tg, sr, of;
+    int st;
+    try {
+        st = build_pairs(level, n_boxes, box_ijk, tg, sr, of);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    if (st != KIFMM_OK) return st;
+    if (targets) {
+        if (!sources || !offsets) {
+            set_error("targets, sources and offsets must all be given");
+            return KIFMM_ERR_INVALID_ARG;
+        }
+        std::memcpy(targets, tg.data(), tg.size() * 4);
+        std::memcpy(sources, sr.data(), sr.size() * 4);
+        std::memcpy(offsets, of.data(), of.size() * 4);
+    }
+    *n_pairs = (int64_t)tg.size();
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out) {
+    if (!out) {
+        set_error("out is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int st = check_params(params);
+    if (st != KIFMM_OK) return st;
+    std::unique_ptr<kifmm_m2l_plan_s> plan;
+    try {
+        plan.reset(new kifmm_m2l_plan_s());
+        plan->prm = *params;
+        Factors f;
+        st = compute_factors(*params, f);
+        if (st != KIFMM_OK) return st;
+        if (f.sym_err > 1e-10) {
+            set_error("K~_o^T = K~_{-o} does not hold (relative error " + std::to_string(f.sym_err) + ")");
+            return KIFMM_ERR_UNSUPPORTED;
+        }
+        KIFMM_CUDA_TRY(cudaGetDevice(&plan->device));
+        KIFMM_CUDA_TRY(cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device));
+        const int n = f.n, r = f.r, rp = (r + 15) / 16 * 16;
+        plan->n = n;
+        plan->r = r;
+        plan->rp = rp;
+        plan->sym_err = f.sym_err;
+        plan->sigma = f.sigma;
+        plan->pieces = pieces_for(params->precision);
+        plan->products = products_for(params->precision);
+        {
+            int major = 0, minor = 0;
+            KIFMM_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, plan->device));
+            KIFMM_CUDA_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, plan->device));
+            if (major != 10 || minor != 3) {
+                set_error("this library's tcgen05 kernels need an sm_103 (GB300) device");
+                return KIFMM_ERR_UNSUPPORTED;
+            }
+        }
+        const int np = (n + 15) / 16 * 16;
+        plan->n_pad = np;
+        std::vector<float> h_c((size_t)kOffsets * rp * rp, 0.f);
+        for (int k = 0; k < kOffsets; ++k)
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b)
+                    h_c[((size_t)k * rp + a) * rp + b] = (float)f.C[((size_t)k * r + a) * r + b];
+        KIFMM_CUDA_TRY(plan->C.upload(h_c.data(), h_c.size()));
+        // 3-piece BF16 splits of the FP64 factors: piece j = RN(x - earlier pieces)
+        auto split_upload = [&](DevBuf<__nv_bfloat16>& dst, size_t per, auto value_at) -> int {
+            std::vector<uint16_t> h(per * 3, 0);
+            for (size_t e = 0; e < per; ++e) {
+                double v = value_at(e);
+                if (v == 0.0) continue;
+                for (int pc = 0; pc < 3; ++pc) {
+                    const uint16_t b = bf16_bits_rn((float)v);
+                    h[pc * per + e] = b;
+                    v -= (double)bf16_to_float(b);
+                }
+            }
+            KIFMM_CUDA_TRY(dst.ensure(h.size()));
+            KIFMM_CUDA_TRY(cudaMemcpy(dst.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
+            return KIFMM_OK;
+        };
+        // K~_o as [316][rp][rp]
+        st = split_upload(plan->Cb, (size_t)kOffsets * rp * rp, [&](size_t e) -> double {
+            const size_t k = e / ((size_t)rp * rp), a = (e / rp) % rp, b = e % rp;
+            return (a < (size_t)r && b < (size_t)r) ? f.C[(k * r + a) * r + b] : 0.0;
+        });
+        if (st != KIFMM_OK) return st;
+        // R~^T as [rp][np]: row a = column a of R~ (= U~)
+        st = split_upload(plan->Rtb, (size_t)rp * np, [&](size_t e) -> double {
+            const size_t a = e / np, i = e % np;
+            return (a < (size_t)r && i < (size_t)n) ? f.U[i * r + a] : 0.0;
+        });
+        if (st != KIFMM_OK) return st;
+        // U~ as [np][rp]
+        st = split_upload(plan->Ub, (size_t)np * rp, [&](size_t e) -> double {
+            const size_t i = e / rp, a = e % rp;
+            return (a < (size_t)r && i < (size_t)n) ? f.U[i * r + a] : 0.0;
+        });
+        if (st != KIFMM_OK) return st;
+        // SPLIT6 keeps the (0,0) product in its own accumulator: the tensor
+        // core's accumulation error grows with the number of MMA steps that
+        // round at the full magnitude, and the 5 small products would
+        // otherwise add 5 such steps per K step.
+        plan->core_hilo = params->precision == KIFMM_PREC_SPLIT6 ? 1 : 0;
+        KIFMM_CUDA_TRY(plan->err_flag.ensure(1));
+        KIFMM_CUDA_TRY(cudaMemset(plan->err_flag.ptr, 0, sizeof(int)));
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    *out = plan.release();
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_destroy(kifmm_m2l_plan plan) {
+    delete plan;
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (r) *r = plan->r;
+    if (r_pad) *r_pad = plan->rp;
+    if (n) *n = plan->n;
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth, int n_boxes,
+                        const int32_t* box_ijk) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (instance < 0 || !(root_halfwidth > 0) || !std::isfinite(root_halfwidth)) {
+        set_error("instance must be >= 0 and root_halfwidth > 0");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    try {
+        std::vector<int32_t> tg, sr, of;
+        st = build_pairs(level, n_boxes, box_ijk, tg, sr, of);
+        if (st != KIFMM_OK) return st;
+        auto ls = std::make_unique<LevelState>();
+        ls->level = level;
+        ls->n_boxes = n_boxes;
+        ls->r0 = root_halfwidth;
+        ls->n_pairs = (int64_t)tg.size();
+        st = build_pairset(tg, sr, of, ls->fwd);
+        if (st != KIFMM_OK) return st;
+        // adjoint: target' = s, source' = t, offset' = -o; regroup by offset'
+        int offs[kOffsets][3];
+        offsets316(offs);
+        std::vector<int> neg(kOffsets);
+        for (int k = 0; k < kOffsets; ++k) neg[k] = offset_index(-offs[k][0], -offs[k][1], -offs[k][2]);
+        std::vector<int32_t> atg(tg.size()), asr(tg.size()), aof(tg.size());
+        // regroup by reversed offset, each group sorted by its new target
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> grp(kOffsets);
+        for (size_t i = 0; i < tg.size(); ++i) grp[neg[of[i]]].push_back({sr[i], tg[i]});
+        size_t w = 0;
+        for (int k = 0; k < kOffsets; ++k) {
+            std::sort(grp[k].begin(), grp[k].end());
+            for (auto& ts : grp[k]) {
+                atg[w] = ts.first;
+                asr[w] = ts.second;
+                aof[w] = k;
+                ++w;
+            }
+        }
+        st = build_pairset(atg, asr, aof, ls->adj);
+        if (st != KIFMM_OK) return st;
+        plan->levels[{instance, level}] = std::move(ls);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    KIFMM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int flag = 0;
+    KIFMM_CUDA_TRY(cudaMemcpy(&flag, plan->err_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        KIFMM_CUDA_TRY(cudaMemset(plan->err_flag.ptr, 0, sizeof(int)));
+        set_error("a bounded wait inside the tensor-core kernel timed out; results are invalid");
+        return KIFMM_ERR_TIMEOUT;
+    }
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_level_pairs(kifmm_m2l_plan plan, int instance, int level, int64_t* n_pairs) {
+    if (!plan || !n_pairs) {
+        set_error("plan or n_pairs is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    LevelState* ls = find_level(plan, instance, level);
+    if (!ls) {
+        set_error("level not registered");
+        return KIFMM_ERR_STATE;
+    }
+    *n_pairs = ls->n_pairs;
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_apply(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* q_up, float* p_down,
+                    float beta, void* stream) {
+    return apply_compressed(plan, instance, level, nrhs, q_up, p_down, beta, stream, false);
+}
+
+int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* pbar_down,
+                            float* qbar_up, float beta, void* stream) {
+    return apply_compressed(plan, instance, level, nrhs, pbar_down, qbar_up, beta, stream, true);
+}
+
+int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* q_up, float* p_down,
+                          float beta, void* stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    LevelState* ls = find_level(plan, instance, level);
+    if (!ls) {
+        set_error("level not registered: call kifmm_m2l_set_level first");
+        return KIFMM_ERR_STATE;
+    }
+    if (nrhs < 1 || (ls->n_boxes > 0 && (!q_up || !p_down))) {
+        set_error("invalid nrhs or NULL density pointer");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(q_up) & 15) || (reinterpret_cast<uintptr_t>(p_down) & 15)) {
+        set_error("density pointers must be 16-byte aligned");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    const int n = plan->n;
+    if (!plan->K.ptr) {
+        std::vector<float> hk((size_t)kOffsets * n * n);
+        std::vector<double> kd((size_t)n * n);
+        int offs[kOffsets][3];
+        offsets316(offs);
+        const std::vector<double> u = unit_surface(plan->prm.p);
+        for (int k = 0; k < kOffsets; ++k) {
+            unit_m2l_matrix(plan->prm.p, plan->prm.d, offs[k], u, kd.data());
+            for (size_t i = 0; i < kd.size(); ++i) hk[(size_t)k * n * n + i] = (float)kd[i];
+        }
+        KIFMM_CUDA_TRY(plan->K.upload(hk.data(), hk.size()));
+    }
+    if (ls->n_boxes == 0) return KIFMM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long rows = (long)ls->n_boxes * nrhs;
+    const float scale = (float)std::ldexp(1.0 / ls->r0, level);
+    // p_down = beta p_down + s_l sum K q : scale the old values, then scatter-add
+    if (beta == 0.f) {
+        KIFMM_CUDA_TRY(launch_zero(p_down, rows * n, s));
+    } else if (beta != 1.f) {
+        KIFMM_CUDA_TRY(launch_scale(p_down, rows * n, beta, s));
+    }
+    const Tile* tiles = nullptr;
+    int n_tiles = 0;
+    st = get_tiles(ls->fwd, nrhs, &tiles, &n_tiles);
+    if (st != KIFMM_OK) return st;
+    KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(q_up, n, plan->K.ptr, n, n, p_down, n, tiles, n_tiles, ls->fwd.src.ptr,
+                                          ls->fwd.dst.ptr, nrhs, scale, s));
+    return KIFMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Kernel launch wrappers (device code in kernels_simt.cu, kernels_umma.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace kifmm {
+
+// One tile of an offset-grouped batch: rows [row0, row0 + nrows) of offset
+// k's virtual row list.  Virtual row v maps to pair = pair_begin + v / nrhs,
+// rhs = v % nrhs; the source row is src[pair] * nrhs + rhs and the output
+// row dst[pair] * nrhs + rhs.
+struct Tile {
+    int k;
+    int pair_begin;
+    int row0;
+    int nrows;
+};
+
+// Offset-grouped gather-GEMM-scatter, FP32 CUDA cores:
+// for every tile, D[dst row] += alpha * A[src row] W_k^T with W_k = W + k * N * K.
+cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int N, int K, float* D, int ldd,
+                                   const Tile* tiles, int n_tiles, const int* src, const int* dst, int nrhs,
+                                   float alpha, cudaStream_t stream);
+
+// x (FP32 [rows][cols], ld) -> `pieces` BF16 arrays [rows][cols] (piece stride
+// `piece_stride` elements) with x ~= sum of pieces (round-to-nearest each).
+cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* out, long piece_stride,
+                              int pieces, cudaStream_t stream);
+
+// Zero `count` floats.
+cudaError_t launch_zero(float* x, long count, cudaStream_t stream);
+
+// x *= beta over `count` floats.
+cudaError_t launch_scale(float* x, long count, float beta, cudaStream_t stream);
+
+// tcgen05 (UMMA) split-BF16 GEMM with fused gather / scatter, one kernel
+// template for the three products of the compressed M2L:
+//   core      D[dst row] += A_pieces[src row] K~_o^T          (A_GATHER, E_RED)
+//   compress  Dp = pieces(alpha A_f32 W^T), Z = 0             (A_ROWS,   E_SPLIT)
+//   expand    D = alpha A_f32 W^T + beta D                    (A_ROWS,   E_STORE)
+// B operands are BF16 pieces [pieces][b_groups][ndim][kdim] read by TMA.
+enum UmmaAMode { A_GATHER = 0, A_ROWS = 1 };
+enum UmmaEMode { E_RED = 0, E_STORE = 1, E_SPLIT = 2 };
+
+struct UmmaArgs {
+    // A operand
+    const __nv_bfloat16* A;   // A_GATHER: piece 0 base, [rows][kdim]; piece i at A + i * a_piece_stride
+    long a_piece_stride;      // elements
+    const float* Af;          // A_ROWS: FP32 rows [m_rows][lda]
+    int lda;
+    int k_valid;              // A_ROWS: valid columns of Af (multiple of 4); beyond: zero
+    int m_rows;               // A_ROWS: number of rows
+    int kdim;                 // padded K (multiple of 16)
+    // B operand (TMA)
+    const __nv_bfloat16* B;   // piece 0 base
+    int b_groups;             // 316 offsets (core) or 1
+    int ndim;                 // N rows per group (multiple of 16)
+    int n_chunk;              // N per work item (multiple of 16)
+    // work list (A_GATHER)
+    const Tile* tiles;
+    int n_tiles;
+    const int* src;
+    const int* dst;
+    int nrhs;
+    int zero_row;             // row of the A pieces that is all zero
+    // epilogue
+    float* D;                 // E_RED / E_STORE: FP32 [*][ldd]
+    int ldd;
+    float alpha, beta;
+    int n_valid;              // E_STORE: columns < n_valid are written
+    __nv_bfloat16* Dp;        // E_SPLIT: pieces [piece][m_rows][ldd]
+    long dp_piece_stride;
+    int dp_pieces;
+    float* Df;                // E_SPLIT: optional FP32 copy [m_rows][ldd]
+    float* Z;                 // E_SPLIT: optional buffer [m_rows][ldd] to zero
+    // arithmetic
+    int n_products;           // 1, 3 or 6 piece products
+    int hilo;                 // 1: the (0,0) product accumulates apart from the others
+    int* error_flag;          // device int, set when a bounded wait times out
+};
+cudaError_t launch_umma(int amode, int emode, const UmmaArgs& args, int num_sms, cudaStream_t stream);
+
+}  // namespace kifmm

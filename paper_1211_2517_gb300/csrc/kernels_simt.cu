@@ -1,0 +1,198 @@
+// CUDA-core (SIMT) FP32 kernels of the M2L path.
+//
+//  * pairs_gemm      D[dst row] += alpha A[src row] W_o^T over offset-grouped
+//                    box pairs, a row gather from the sources and an atomic
+//                    scatter-add into the targets: the FP32 core
+//                    sum_o K~_o q~ and the dense baseline sum_o K_o q
+//                    (Eq. eq-m2l).
+//  * split_bf16      FP32 -> sum of BF16 pieces for the tensor-core modes.
+//
+// Tiling: a 256-thread block computes a 128 x 128 output tile in K-steps of
+// 8 staged through shared memory (double-buffered); each thread owns an
+// 8 x 8 register block (8 contiguous rows, two groups of 4 columns).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace kifmm {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
+
+struct RowMapPairs {
+    const int* src;
+    const int* dst;
+    int nrhs, pair_begin, row0, nrows;
+    __device__ __forceinline__ bool valid(int v) const { return v < nrows; }
+    __device__ __forceinline__ long a_row(int v) const {
+        const int g = row0 + v;
+        const int pr = pair_begin + g / nrhs;
+        return (long)src[pr] * nrhs + (g % nrhs);
+    }
+    __device__ __forceinline__ long d_row(int v) const {
+        const int g = row0 + v;
+        const int pr = pair_begin + g / nrhs;
+        return (long)dst[pr] * nrhs + (g % nrhs);
+    }
+};
+
+// Accumulate the 128x128 tile into acc.
+template <class Map>
+__device__ __forceinline__ void tile_product(const float* __restrict__ A, int lda, const float* __restrict__ W, int N,
+                                             int K, int n0, const Map& map, float (&acc)[8][8],
+                                             float (*As)[BK][BM], float (*Ws)[BK][BN]) {
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    // loader coordinates: row lr, k-offset lk (4 floats)
+    const int lr = tid >> 1, lk = (tid & 1) * 4;
+    const bool a_ok = map.valid(lr);
+    const float* a_ptr = a_ok ? A + map.a_row(lr) * (long)lda : A;
+    const bool w_ok = (n0 + lr) < N;
+    const float* w_ptr = W + (long)(w_ok ? n0 + lr : 0) * K;
+
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    auto load = [&](int k0, float4& av, float4& wv) {
+        const int kk = k0 + lk;
+        av = make_float4(0.f, 0.f, 0.f, 0.f);
+        wv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kk < K) {  // K is a multiple of 4
+            if (a_ok) av = *reinterpret_cast<const float4*>(a_ptr + kk);
+            if (w_ok) wv = __ldg(reinterpret_cast<const float4*>(w_ptr + kk));
+        }
+    };
+    auto store = [&](int buf, const float4& av, const float4& wv) {
+        As[buf][lk + 0][lr] = av.x;
+        As[buf][lk + 1][lr] = av.y;
+        As[buf][lk + 2][lr] = av.z;
+        As[buf][lk + 3][lr] = av.w;
+        Ws[buf][lk + 0][lr] = wv.x;
+        Ws[buf][lk + 1][lr] = wv.y;
+        Ws[buf][lk + 2][lr] = wv.z;
+        Ws[buf][lk + 3][lr] = wv.w;
+    };
+
+    float4 av, wv;
+    load(0, av, wv);
+    store(0, av, wv);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        const bool more = k0 + BK < K;
+        if (more) load(k0 + BK, av, wv);
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8 + 4]);
+            const float4 w0 = *reinterpret_cast<const float4*>(&Ws[buf][k][tx * 4]);
+            const float4 w1 = *reinterpret_cast<const float4*>(&Ws[buf][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+        }
+        if (more) {
+            store(buf ^ 1, av, wv);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT) pairs_gemm_kernel(const float* __restrict__ A, int lda,
+                                                        const float* __restrict__ W, int N, int K,
+                                                        float* __restrict__ D, int ldd, const Tile* __restrict__ tiles,
+                                                        const int* __restrict__ src, const int* __restrict__ dst,
+                                                        int nrhs, float alpha) {
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Ws[2][BK][BN];
+    const Tile t = tiles[blockIdx.x];
+    const int n0 = blockIdx.y * BN;
+    RowMapPairs map{src, dst, nrhs, t.pair_begin, t.row0, t.nrows};
+    float acc[8][8];
+    tile_product(A, lda, W + (long)t.k * N * K, N, K, n0, map, acc, As, Ws);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int v = ty * 8 + i;
+        if (!map.valid(v)) continue;
+        float* drow = D + map.d_row(v) * ldd;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (col < N) atomicAdd(drow + col, alpha * acc[i][j]);
+        }
+    }
+}
+
+__global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int cols, int ld,
+                                  __nv_bfloat16* __restrict__ out, long piece_stride, int pieces) {
+    const long total = (long)rows * cols;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long r = e / cols, c = e % cols;
+        float v = x[r * ld + c];
+        for (int p = 0; p < pieces; ++p) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            out[p * piece_stride + e] = h;
+            v -= __bfloat162float(h);  // exact: the residual of a bf16 rounding is representable
+        }
+    }
+}
+
+__global__ void zero_kernel(float4* __restrict__ x, long n4) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n4; e += (long)gridDim.x * blockDim.x)
+        x[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void scale_kernel(float* __restrict__ x, long n, float beta) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) x[e] *= beta;
+}
+
+}  // namespace
+
+cudaError_t launch_scale(float* x, long count, float beta, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    scale_kernel<<<blocks, 256, 0, stream>>>(x, count, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int N, int K, float* D, int ldd,
+                                   const Tile* tiles, int n_tiles, const int* src, const int* dst, int nrhs,
+                                   float alpha, cudaStream_t stream) {
+    if (n_tiles <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid(n_tiles, (N + BN - 1) / BN);
+    pairs_gemm_kernel<<<grid, NT, 0, stream>>>(A, lda, W, N, K, D, ldd, tiles, src, dst, nrhs, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* out, long piece_stride,
+                              int pieces, cudaStream_t stream) {
+    const long total = (long)rows * cols;
+    if (total <= 0) return cudaSuccess;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    split_bf16_kernel<<<blocks, 256, 0, stream>>>(x, rows, cols, ld, out, piece_stride, pieces);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(float* x, long count, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    if ((count & 3) != 0 || (reinterpret_cast<uintptr_t>(x) & 15) != 0)
+        return cudaMemsetAsync(x, 0, count * sizeof(float), stream);
+    long n4 = count / 4;
+    int blocks = (int)((n4 + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    zero_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<float4*>(x), n4);
+    return cudaGetLastError();
+}
+
+}  // namespace kifmm

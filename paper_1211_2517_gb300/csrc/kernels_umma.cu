@@ -1,0 +1,754 @@
+// tcgen05 (5th-generation tensor core) kernels of the compressed M2L.
+//
+// One kernel template computes the three products of Eq. evalcmp1 restricted
+// to M2L, each as a split-BF16 GEMM with FP32 accumulation in tensor memory:
+//
+//   compress  q~ = R~^T q        A = FP32 rows of q, split to BF16 pieces
+//                                in shared memory; output written as the
+//                                BF16 pieces the core consumes (E_SPLIT)
+//   core      p~^t += K~_o q~^s  one dense GEMM per offset o over every box
+//                                pair sharing it: A gathers source rows of
+//                                q~, B = K~_o, each output row is reduced
+//                                into its target's p~ row (E_RED)
+//   expand    p = s_l U~ p~ (+ beta p)                            (E_STORE)
+//
+// Split precision: x = x_0 + x_1 + x_2 with BF16 pieces; a product keeps
+// the piece products (i, j) of order <= 2^-16 (6 of them for 3 pieces, 3
+// for 2, 1 for 1).  With `hilo`, the (0,0) product accumulates in its own
+// TMEM accumulator and the small ones in another, so the large terms are
+// rounded once per 16-element MMA step instead of once per product.
+//
+// Warp roles of a persistent CTA (one per SM, 288 threads):
+//   warps 0-3  epilogue: TMEM -> registers -> per-warp shared-memory
+//              transpose -> coalesced 16-byte global reductions / stores
+//   warps 4-7  producers: A tiles into 64B-swizzled shared memory (cp.async
+//              gather of BF16 rows, or FP32 loads split in registers);
+//              one thread also TMA-loads the B tiles
+//   warp 8     TMEM allocation and the single MMA-issuing thread
+// Stages cycle through full/empty mbarriers; two TMEM accumulator slots
+// (when they fit in 512 columns) overlap the epilogue of one work item
+// with the MMAs of the next.
+//
+// Every mbarrier wait is bounded (about two seconds of %globaltimer); on
+// timeout the kernel raises a device error flag, every role stops, copies in
+// flight are waited for (bounded), and TMEM is freed before exit.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+#include "kifmm_m2l.h"
+
+namespace kifmm {
+
+namespace {
+
+constexpr int kEpiWarps = 4, kProdWarps = 4;
+constexpr int kThreads = (kEpiWarps + kProdWarps + 1) * 32;  // 288
+constexpr int kTileM = 128;
+constexpr int kChunk = 32;              // K elements per stage (64 bytes of BF16: SWIZZLE_64B rows)
+constexpr int kRowBytes = kChunk * 2;   // 64
+constexpr int kCBoxRows = 64;           // rows per TMA box of K~_o
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+struct Smem {
+    // barriers live at the start of dynamic shared memory
+    uint64_t full[8];
+    uint64_t empty[8];
+    uint64_t tmem_full[2];   // whole-item accumulator slots (core), lo slots (rows modes)
+    uint64_t tmem_empty[2];
+    uint64_t part_full[2];   // rows modes: per K-chunk partial of the (0,0) product
+    uint64_t part_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false on timeout / abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Smem* sm, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (sm->abort_flag) return false;
+        if (global_ns() - t0 > kWaitNs) {
+            sm->abort_flag = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart (SBO), version 1 (bits 46-47), layout type 4 (bits 61-63).
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                  // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;         // SBO
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128.
+__device__ __forceinline__ uint32_t umma_idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void red_add_v4(float* addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// Byte offset of 16-byte chunk c (0..3) of row m in a 64B-swizzled tile whose
+// base is 512-byte aligned: bits [4,6) ^= bits [7,9).
+__device__ __forceinline__ uint32_t swz64(int m, int c) {
+    const uint32_t o = (uint32_t)m * kRowBytes + (uint32_t)c * 16;
+    return o ^ (((o >> 7) & 3u) << 4);
+}
+
+struct Layout {
+    int stages, na, nc, c_rows_alloc, n_acc, acc_cols, n_items, n_chunks, kc_count;
+    uint32_t a_bytes, c_bytes, stage_bytes, trans_off;
+};
+
+// Product table (a piece, b piece), smallest terms first; (0,0) last.
+__constant__ int8_t kProd[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+
+constexpr int kTransStride = 33;  // floats per row of the epilogue transpose buffer
+constexpr int kMaxRowsChunk = 96; // N per work item of the rows modes (partial sums live in registers)
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// split x into `np` BF16 pieces (round to nearest at each step)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 (&p)[3], int np) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i < np) {
+            p[i] = __float2bfloat16_rn(x);
+            x -= __bfloat162float(p[i]);
+        } else {
+            p[i] = __float2bfloat16_rn(0.f);
+        }
+    }
+}
+
+template <int AMODE, int EMODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    umma_kernel(const __grid_constant__ CUtensorMap bmap, const UmmaArgs args, const Layout L) {
+    extern __shared__ __align__(1024) uint8_t smem_dyn[];
+    uint8_t* smem_raw = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+    Smem* sm = reinterpret_cast<Smem*>(smem_raw);
+    uint8_t* stage_base = smem_raw + 1024;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int S = L.stages;
+    const int p0 = 6 - args.n_products;  // first entry of kProd used
+    const int KC = L.kc_count;
+    const int n_chunks = L.n_chunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&sm->full[s], kProdWarps * 32 + 1);
+            mbar_init(&sm->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&sm->tmem_full[a], 1);
+            mbar_init(&sm->tmem_empty[a], kEpiWarps * 32);
+            mbar_init(&sm->part_full[a], 1);
+            mbar_init(&sm->part_empty[a], kEpiWarps * 32);
+        }
+        mbar_init(&sm->drain, 1);
+        sm->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kEpiWarps + kProdWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(&sm->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+
+    auto a_smem = [&](int s, int piece) -> uint32_t {
+        return smem_u32(stage_base + (size_t)s * L.stage_bytes + (size_t)piece * L.a_bytes);
+    };
+    auto c_smem = [&](int s, int piece) -> uint32_t {
+        return smem_u32(stage_base + (size_t)s * L.stage_bytes + (size_t)L.na * L.a_bytes +
+                        (size_t)piece * L.c_bytes);
+    };
+    // work item -> (tile or row tile, N chunk)
+    auto item_tile = [&](int item) { return item / n_chunks; };
+    auto item_n0 = [&](int item) { return (item % n_chunks) * args.n_chunk; };
+    auto item_nthis = [&](int item) { return min(args.n_chunk, args.ndim - item_n0(item)); };
+
+    if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
+        // ================= producers =================
+        const int v = threadIdx.x - kEpiWarps * 32;  // 0..127
+        const bool tma_thread = (v == 0);
+        int it = 0;
+        bool ok = true;
+        auto issue_b = [&](int s, int item, int kc) {
+            int group = 0;
+            if (AMODE == A_GATHER) group = args.tiles[item_tile(item)].k;
+            mbar_arrive_expect_tx(&sm->full[s], (uint32_t)L.nc * L.c_rows_alloc * kRowBytes);
+            for (int pc = 0; pc < L.nc; ++pc) {
+                const int row_base = (pc * args.b_groups + group) * args.ndim + item_n0(item);
+                for (int rb = 0; rb < L.c_rows_alloc; rb += kCBoxRows)
+                    tma_load_2d(c_smem(s, pc) + rb * kRowBytes, &bmap, kc * kChunk, row_base + rb, &sm->full[s]);
+            }
+        };
+        if (AMODE == A_GATHER) {
+            // thread v copies 16-byte chunk (v % 4) of rows v/4 + 32 i, i = 0..3:
+            // one warp instruction covers 8 rows x 64 contiguous bytes
+            const int cch = v % 4;
+            for (int item = blockIdx.x; item < L.n_items && ok; item += gridDim.x) {
+                const Tile t = args.tiles[item_tile(item)];
+                long srow[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = v / 4 + 32 * i;
+                    srow[i] = args.zero_row;
+                    if (r < t.nrows) {
+                        const int g = t.row0 + r;
+                        const int pr = t.pair_begin + g / args.nrhs;
+                        srow[i] = (long)args.src[pr] * args.nrhs + (g % args.nrhs);
+                    }
+                }
+                for (int kc = 0; kc < KC; ++kc, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (!mbar_wait(&sm->empty[s], ph ^ 1u, sm, args.error_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const int col = kc * kChunk + cch * 8;
+                    const uint32_t bytes = col < args.kdim ? 16u : 0u;
+                    const int colc = col < args.kdim ? col : 0;
+                    for (int pc = 0; pc < L.na; ++pc) {
+                        const __nv_bfloat16* base = args.A + pc * args.a_piece_stride + colc;
+                        const uint32_t sbase = a_smem(s, pc);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            cp_async16(sbase + swz64(v / 4 + 32 * i, cch), base + srow[i] * args.kdim, bytes);
+                    }
+                    cp_async_commit();
+                    if (tma_thread) issue_b(s, item, kc);
+                    if (it > 0) {
+                        cp_async_wait_1();
+                        fence_proxy_async();
+                        mbar_arrive(&sm->full[(it - 1) % S]);
+                    }
+                }
+            }
+            cp_async_wait_0();
+            fence_proxy_async();
+            if (it > 0 && ok) mbar_arrive(&sm->full[(it - 1) % S]);
+        } else {
+            // FP32 rows: thread v loads float4 f = v + 128 i (i = 0..7) of the
+            // 128 x 32 tile, row f / 8, columns 4 (f % 8) .. +3 (a warp reads
+            // 4 rows x 128 contiguous bytes), splits them into BF16 pieces and
+            // stores them swizzled.
+            float4 buf[8];
+            auto load = [&](int item, int kc) {
+                const int m0 = item_tile(item) * kTileM;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int f = v + 128 * i;
+                    const int row = m0 + f / 8, col = kc * kChunk + 4 * (f % 8);
+                    buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (row < args.m_rows && col < args.k_valid)
+                        buf[i] = __ldg(reinterpret_cast<const float4*>(args.Af + (long)row * args.lda + col));
+                }
+            };
+            int item = blockIdx.x, kc = 0;
+            if (item < L.n_items) load(item, 0);
+            while (item < L.n_items && ok) {
+                const int s = it % S;
+                const uint32_t ph = (uint32_t)(it / S) & 1u;
+                if (!mbar_wait(&sm->empty[s], ph ^ 1u, sm, args.error_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (tma_thread) issue_b(s, item, kc);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int f = v + 128 * i;
+                    const int row = f / 8, c4 = f % 8;
+                    __nv_bfloat16 pc0[3], pc1[3], pc2[3], pc3[3];
+                    split3(buf[i].x, pc0, L.na);
+                    split3(buf[i].y, pc1, L.na);
+                    split3(buf[i].z, pc2, L.na);
+                    split3(buf[i].w, pc3, L.na);
+                    const uint32_t off = swz64(row, c4 >> 1) + (c4 & 1) * 8;
+#pragma unroll
+                    for (int pc = 0; pc < 3; ++pc) {
+                        if (pc >= L.na) break;
+                        const uint32_t lo = pack_bf16x2(pc0[pc], pc1[pc]), hi = pack_bf16x2(pc2[pc], pc3[pc]);
+                        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_smem(s, pc) + off), "r"(lo), "r"(hi)
+                                     : "memory");
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(&sm->full[s]);
+                ++it;
+                if (++kc == KC) {
+                    kc = 0;
+                    item += gridDim.x;
+                }
+                if (item < L.n_items) load(item, kc);  // in flight while waiting for the next slot
+            }
+        }
+        if (!ok && tma_thread) {
+            const unsigned long long t0 = global_ns();
+            while (global_ns() - t0 < 1000000ull) {
+            }
+        }
+    } else if (warp == kEpiWarps + kProdWarps) {
+        // ================= MMA issuer =================
+        // Core (A_GATHER): one accumulator slot per work item (hi and, with
+        // hilo, lo side by side), double-buffered when two fit.
+        // Rows modes: the (0,0) product of every K-chunk goes to one of two
+        // ping-pong partial slots that the epilogue drains into FP32
+        // registers (so no accumulator chain is longer than one K-chunk);
+        // the small products accumulate over the item in a lo slot.
+        if (lane == 0) {
+            int it = 0, tcount = 0, pcount = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < L.n_items && ok; item += gridDim.x, ++tcount) {
+                const int acc = tcount % L.n_acc;
+                const uint32_t aph = (uint32_t)(tcount / L.n_acc) & 1u;
+                if (!mbar_wait(&sm->tmem_empty[acc], aph ^ 1u, sm, args.error_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int nthis = item_nthis(item);
+                const int nA = nthis <= 256 ? nthis : ((nthis / 2 + 15) / 16) * 16;
+                const int nB = nthis - nA;
+                const uint32_t idA = umma_idesc_bf16(nA), idB = nB > 0 ? umma_idesc_bf16(nB) : 0u;
+                uint32_t d_hi, d_lo;
+                if (AMODE == A_ROWS) {
+                    // columns: part[0], part[1], lo[0], lo[1], each n_chunk wide
+                    d_lo = tmem + (uint32_t)((2 + acc) * args.n_chunk);
+                    d_hi = d_lo;  // set per K-chunk
+                } else {
+                    d_hi = tmem + (uint32_t)(acc * L.acc_cols);
+                    d_lo = args.hilo ? d_hi + (uint32_t)args.n_chunk : d_hi;
+                }
+                bool first_hi = true, first_lo = true;
+                for (int kc = 0; kc < KC; ++kc, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    int ps = 0;
+                    if (AMODE == A_ROWS) {
+                        ps = pcount % 2;
+                        const uint32_t pph = (uint32_t)(pcount / 2) & 1u;
+                        if (!mbar_wait(&sm->part_empty[ps], pph ^ 1u, sm, args.error_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        d_hi = tmem + (uint32_t)(ps * args.n_chunk);
+                        first_hi = true;
+                    }
+                    if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int ksteps = min(kChunk, args.kdim - kc * kChunk) / 16;
+                    for (int pi = p0; pi < 6; ++pi) {
+                        const bool big = kProd[pi][0] == 0 && kProd[pi][1] == 0;
+                        const bool to_hi = big || !(args.hilo || AMODE == A_ROWS);
+                        const uint32_t d = to_hi ? d_hi : d_lo;
+                        const uint32_t abase = a_smem(s, kProd[pi][0]);
+                        const uint32_t cbase = c_smem(s, kProd[pi][1]);
+                        for (int ks = 0; ks < ksteps; ++ks) {
+                            bool& first = to_hi ? first_hi : first_lo;
+                            const uint64_t ad = umma_desc_sw64(abase + ks * 32);
+                            umma_bf16(d, ad, umma_desc_sw64(cbase + ks * 32), idA, first ? 0u : 1u);
+                            if (nB > 0)
+                                umma_bf16(d + (uint32_t)nA, ad, umma_desc_sw64(cbase + (uint32_t)nA * kRowBytes + ks * 32),
+                                          idB, first ? 0u : 1u);
+                            first = false;
+                        }
+                    }
+                    umma_commit(&sm->empty[s]);
+                    if (AMODE == A_ROWS) {
+                        umma_commit(&sm->part_full[ps]);
+                        ++pcount;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&sm->tmem_full[acc]);
+            }
+            umma_commit(&sm->drain);
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&sm->drain, 0u) && global_ns() - t0 < kWaitNs) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ================= epilogue =================
+        float* trans = reinterpret_cast<float*>(smem_raw + L.trans_off) + warp * 32 * kTransStride;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const bool has_lo = args.hilo && args.n_products > 1;
+        int tcount = 0, pcount = 0;
+        for (int item = blockIdx.x; item < L.n_items; item += gridDim.x, ++tcount) {
+            const int acc = tcount % L.n_acc;
+            const uint32_t aph = (uint32_t)(tcount / L.n_acc) & 1u;
+            const int n0 = item_n0(item), nthis = item_nthis(item);
+            // this lane's output row (tile row warp*32 + lane); -1 = none
+            long orow = -1;
+            if (AMODE == A_GATHER) {
+                const Tile t = args.tiles[item_tile(item)];
+                const int r = warp * 32 + lane;
+                if (r < t.nrows) {
+                    const int g = t.row0 + r;
+                    const int pr = t.pair_begin + g / args.nrhs;
+                    orow = (long)args.dst[pr] * args.nrhs + (g % args.nrhs);
+                }
+            } else {
+                const long r = (long)item_tile(item) * kTileM + warp * 32 + lane;
+                if (r < args.m_rows) orow = r;
+            }
+            const uint32_t col_hi = (uint32_t)(acc * L.acc_cols);
+            const uint32_t col_lo = col_hi + (uint32_t)args.n_chunk;
+            // rows modes: sum the per-K-chunk partials of the (0,0) product in
+            // registers (round to nearest), then add the lo slot
+            float sums[kMaxRowsChunk];
+            if (AMODE == A_ROWS) {
+#pragma unroll
+                for (int j = 0; j < kMaxRowsChunk; ++j) sums[j] = 0.f;
+                bool got_all = true;
+                for (int kc = 0; kc < KC; ++kc) {
+                    const int ps = pcount % 2;
+                    const uint32_t pph = (uint32_t)(pcount / 2) & 1u;
+                    const bool gp = mbar_wait(&sm->part_full[ps], pph, sm, args.error_flag);
+                    if (!__all_sync(0xffffffffu, gp)) {
+                        got_all = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t pcol = (uint32_t)(ps * args.n_chunk);
+#pragma unroll
+                    for (int c = 0; c < kMaxRowsChunk; c += 32) {
+                        if (c >= nthis) break;
+                        uint32_t r[32];
+                        if (c + 32 <= nthis)
+                            tmem_ld32(tmem + lane_base + pcol + (uint32_t)c, r);
+                        else
+                            tmem_ld16(tmem + lane_base + pcol + (uint32_t)c, r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c + j < nthis) sums[c + j] += __uint_as_float(r[j]);
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&sm->part_empty[ps]);
+                    ++pcount;
+                }
+                if (!got_all) break;
+            }
+            // the whole item (lo slot, or the core's accumulator) is complete
+            const bool got = mbar_wait(&sm->tmem_full[acc], aph, sm, args.error_flag);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            const uint32_t col_lo_rows = (uint32_t)((2 + acc) * args.n_chunk);
+            for (int c = 0; c < nthis; c += 32) {
+                uint32_t r[32];
+                const bool full32 = c + 32 <= nthis;
+                float val[32];
+                if (AMODE == A_ROWS) {
+                    if (full32)
+                        tmem_ld32(tmem + lane_base + col_lo_rows + (uint32_t)c, r);
+                    else
+                        tmem_ld16(tmem + lane_base + col_lo_rows + (uint32_t)c, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        // sums[] is indexed by a loop-invariant offset c (0, 32, 64)
+                        float sv = 0.f;
+#pragma unroll
+                        for (int cc = 0; cc < kMaxRowsChunk; cc += 32)
+                            if (cc == c && cc + j < kMaxRowsChunk) sv = sums[cc + j];
+                        val[j] = sv + __uint_as_float(r[j]);
+                    }
+                } else {
+                    if (full32)
+                        tmem_ld32(tmem + lane_base + col_hi + (uint32_t)c, r);
+                    else
+                        tmem_ld16(tmem + lane_base + col_hi + (uint32_t)c, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) val[j] = __uint_as_float(r[j]);
+                    if (has_lo) {
+                        if (full32)
+                            tmem_ld32(tmem + lane_base + col_lo + (uint32_t)c, r);
+                        else
+                            tmem_ld16(tmem + lane_base + col_lo + (uint32_t)c, r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) val[j] += __uint_as_float(r[j]);
+                    }
+                }
+                // transpose through shared memory: lane -> row, then 8 lanes per row
+#pragma unroll
+                for (int j = 0; j < 32; ++j) trans[lane * kTransStride + j] = val[j];
+                __syncwarp();
+                const int ncols = full32 ? 32 : 16;
+                const int c4 = lane % 8;
+#pragma unroll
+                for (int pass = 0; pass < 8; ++pass) {
+                    const int rr = pass * 4 + lane / 8;
+                    const long grow = __shfl_sync(0xffffffffu, orow, rr);
+                    if (grow < 0 || 4 * c4 >= ncols) continue;
+                    const float* tp = trans + rr * kTransStride + 4 * c4;
+                    float4 x = make_float4(tp[0], tp[1], tp[2], tp[3]);
+                    const int col = n0 + c + 4 * c4;
+                    if (EMODE == E_RED) {
+                        red_add_v4(args.D + grow * args.ldd + col, __float_as_uint(x.x), __float_as_uint(x.y),
+                                   __float_as_uint(x.z), __float_as_uint(x.w));
+                    } else if (EMODE == E_STORE) {
+                        if (col < args.n_valid) {
+                            float4* dp = reinterpret_cast<float4*>(args.D + grow * args.ldd + col);
+                            float4 y = make_float4(args.alpha * x.x, args.alpha * x.y, args.alpha * x.z,
+                                                   args.alpha * x.w);
+                            if (args.beta != 0.f) {
+                                const float4 o = *dp;
+                                y.x = fmaf(args.beta, o.x, y.x);
+                                y.y = fmaf(args.beta, o.y, y.y);
+                                y.z = fmaf(args.beta, o.z, y.z);
+                                y.w = fmaf(args.beta, o.w, y.w);
+                            }
+                            *dp = y;
+                        }
+                    } else {  // E_SPLIT
+                        x.x *= args.alpha;
+                        x.y *= args.alpha;
+                        x.z *= args.alpha;
+                        x.w *= args.alpha;
+                        if (args.Df)
+                            *reinterpret_cast<float4*>(args.Df + grow * args.ldd + col) = x;
+                        if (args.Z)
+                            *reinterpret_cast<float4*>(args.Z + grow * args.ldd + col) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        __nv_bfloat16 q0[3], q1[3], q2[3], q3[3];
+                        split3(x.x, q0, args.dp_pieces);
+                        split3(x.y, q1, args.dp_pieces);
+                        split3(x.z, q2, args.dp_pieces);
+                        split3(x.w, q3, args.dp_pieces);
+#pragma unroll
+                        for (int pc = 0; pc < 3; ++pc) {
+                            if (pc >= args.dp_pieces) break;
+                            uint2 pk = make_uint2(pack_bf16x2(q0[pc], q1[pc]), pack_bf16x2(q2[pc], q3[pc]));
+                            *reinterpret_cast<uint2*>(args.Dp + pc * args.dp_piece_stride + grow * args.ldd + col) = pk;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            mbar_arrive(&sm->tmem_empty[acc]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kEpiWarps + kProdWarps) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+template <int AM, int EM>
+cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L, size_t smem, int grid,
+                     cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(umma_kernel<AM, EM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    umma_kernel<AM, EM><<<grid, kThreads, smem, stream>>>(bmap, a, L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cudaStream_t stream) {
+    if (a.kdim % 16 != 0 || a.kdim <= 0 || a.ndim % 16 != 0 || a.ndim < 16 || a.n_chunk % 16 != 0 ||
+        a.n_chunk < 16 || a.n_chunk > 512)
+        return cudaErrorInvalidValue;
+    if (a.n_products != 1 && a.n_products != 3 && a.n_products != 6) return cudaErrorInvalidValue;
+    const bool gather = amode == A_GATHER;
+    if (!((gather && emode == E_RED) || (!gather && (emode == E_STORE || emode == E_SPLIT))))
+        return cudaErrorInvalidValue;
+    if (!gather && (a.k_valid % 4 != 0 || a.lda % 4 != 0 || a.k_valid > a.kdim)) return cudaErrorInvalidValue;
+    if (a.ldd % 4 != 0) return cudaErrorInvalidValue;
+    EncodeTiledFn encode = get_encode_fn();
+    if (!encode) return cudaErrorNotSupported;
+
+    Layout L{};
+    L.na = a.n_products == 1 ? 1 : (a.n_products == 3 ? 2 : 3);
+    L.nc = L.na;
+    L.n_chunks = (a.ndim + a.n_chunk - 1) / a.n_chunk;
+    L.kc_count = (a.kdim + kChunk - 1) / kChunk;
+    L.c_rows_alloc = (a.n_chunk + kCBoxRows - 1) / kCBoxRows * kCBoxRows;
+    L.a_bytes = kTileM * kRowBytes;
+    L.c_bytes = (uint32_t)L.c_rows_alloc * kRowBytes;
+    L.stage_bytes = (uint32_t)L.na * L.a_bytes + (uint32_t)L.nc * L.c_bytes;
+    if (gather) {
+        L.acc_cols = a.n_chunk * ((a.hilo && a.n_products > 1) ? 2 : 1);
+        if (L.acc_cols > 512) return cudaErrorInvalidValue;
+        L.n_acc = 2 * L.acc_cols <= 512 ? 2 : 1;
+    } else {
+        // two partial slots + two lo slots, partial sums of <= 96 columns in registers
+        if (a.n_chunk > kMaxRowsChunk) return cudaErrorInvalidValue;
+        L.acc_cols = a.n_chunk;
+        L.n_acc = 2;
+    }
+    const long row_tiles = gather ? a.n_tiles : ((long)a.m_rows + kTileM - 1) / kTileM;
+    if (row_tiles * L.n_chunks > INT32_MAX) return cudaErrorInvalidValue;
+    L.n_items = (int)(row_tiles * L.n_chunks);
+    if (L.n_items <= 0) return cudaSuccess;
+
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const uint32_t trans_bytes = kEpiWarps * 32 * kTransStride * 4;
+    const int avail = max_smem - 2048 - (int)trans_bytes;
+    L.stages = avail / (int)L.stage_bytes;
+    if (L.stages > 8) L.stages = 8;
+    if (L.stages < 2) return cudaErrorInvalidConfiguration;
+    L.trans_off = 1024 + (uint32_t)L.stages * L.stage_bytes;
+    const size_t smem = 1024 + (size_t)L.trans_off + trans_bytes;
+
+    // B pieces viewed as a 2D tensor [pieces * b_groups * ndim rows][kdim]
+    CUtensorMap bmap;
+    const cuuint64_t rows_total = (cuuint64_t)L.nc * a.b_groups * a.ndim;
+    const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
+    const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)kCBoxRows};
+    const cuuint32_t estride[2] = {1, 1};
+    CUresult cr = encode(&bmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim, gstride,
+                         box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+    const int grid = num_sms < L.n_items ? num_sms : L.n_items;
+    if (gather) return launch_t<A_GATHER, E_RED>(bmap, a, L, smem, grid, stream);
+    if (emode == E_STORE) return launch_t<A_ROWS, E_STORE>(bmap, a, L, smem, grid, stream);
+    return launch_t<A_ROWS, E_SPLIT>(bmap, a, L, smem, grid, stream);
+}
+
+}  // namespace kifmm

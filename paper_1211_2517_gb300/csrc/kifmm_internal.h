@@ -1,0 +1,55 @@
+// Internal declarations shared by the host precompute, the plan and the
+// kernels.  Not part of the public ABI (see include/kifmm_m2l.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kifmm_m2l.h"
+
+namespace kifmm {
+
+constexpr int kOffsets = KIFMM_N_OFFSETS;
+
+// Thread-local last-error message behind kifmm_m2l_last_error().
+void set_error(const std::string& msg);
+const char* last_error();
+
+// Number of surface points for p points per edge: 6(p-1)^2 + 2.
+inline int surface_count(int p) { return 6 * (p - 1) * (p - 1) + 2; }
+
+// The 316 offsets o in {-3..3}^3 with max|o_i| >= 2, lexicographic.
+void offsets316(int (*o)[3]);
+// Index of offset o in offsets316(), or -1.
+int offset_index(int ox, int oy, int oz);
+
+// Points of the [-1,1]^3 cube boundary (lexicographic grid order), [n][3].
+std::vector<double> unit_surface(int p);
+
+// Entry (i, j) of the unit-level translation matrix K_o (Sec. 2.2 Eq. eq-m2l,
+// surfaces of Sec. 2.1): G(2 o + (1+d)(u_i - u_j)), G = 1/(4 pi |.|).
+void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>& u, double* K);
+
+// FP64 factors of the stage-1 compression (Sec. 3.1).
+struct Factors {
+    int p = 0, n = 0, r = 0;
+    double d = 0, eps = 0;
+    std::vector<double> sigma;  // [n] singular values of K_fat, descending
+    std::vector<double> U;      // [n][r] row-major, U~ (= R~)
+    std::vector<double> C;      // [316][r][r] row-major, K~_o = U~^T K_o U~
+    double sym_err = 0;         // max |K~_o^T - K~_{-o}| / max |K~|
+};
+
+// Full host precompute, with the optional on-disk cache.  Returns a status.
+int compute_factors(const kifmm_m2l_params& prm, Factors& f);
+
+// Validate a params struct; returns a status and sets the error message.
+int check_params(const kifmm_m2l_params* prm);
+
+// Interaction-list pairs of one level (Sec. 2.1), sorted by (offset, target).
+// Returns a status.
+int build_pairs(int level, int n_boxes, const int32_t* ijk, std::vector<int32_t>& tgt,
+                std::vector<int32_t>& src, std::vector<int32_t>& off);
+
+}  // namespace kifmm

@@ -1,0 +1,553 @@
+// Host FP64 precompute of the SVD-compressed M2L operators (Sec. 3.1).
+//
+//   K_fat = [K_1 ... K_316] = U Sigma [V_1^T ... V_316^T]          (Eq. fat)
+//   U~ = columns of U with sigma_i >= eps sigma_0                    (Eq. eq-cmpM2Ls)
+//   R~ = U~  because K_o^T = K_{-o} (G radial, same surfaces), so
+//        K_thin is a row-block permutation of K_fat^T (Eq. thin) and the
+//        right basis of K_thin spans the left basis of K_fat.
+//   K~_o = U~^T K_o R~
+//
+// The SVD never forms the Gram matrix K_fat K_fat^T: singular values down
+// to 1e-8 sigma_0 would drown in its rounding.  Instead:
+//   1. TSQR: K_fat^T = Q R by Householder reflections, merging one n x n
+//      block K_o^T at a time into a running triangular R (each worker thread
+//      owns a range of offsets; the per-thread R factors are merged last).
+//   2. One-sided Jacobi (Hestenes) on R: R V = W Sigma.  Since
+//      K_fat = R^T Q^T = V Sigma (Q W)^T, the left singular vectors of K_fat
+//      are V, accumulated from plane rotations (orthogonal to rounding).
+//      Pairs are visited in a round-robin tournament so that each round's
+//      n/2 rotations are independent and run in parallel.
+#include <algorithm>
+#include <cerrno>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <thread>
+
+#include "kifmm_internal.h"
+
+namespace kifmm {
+
+namespace {
+thread_local std::string g_last_error;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTieTol = 1e-13;          // equal singular values: within 1e-13 sigma_0
+constexpr unsigned kCacheMagic = 0x4b4d324cu;  // "KM2L"
+constexpr unsigned kCacheVersion = 1;
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error() { return g_last_error.c_str(); }
+
+void offsets316(int (*o)[3]) {
+    int k = 0;
+    for (int x = -3; x <= 3; ++x)
+        for (int y = -3; y <= 3; ++y)
+            for (int z = -3; z <= 3; ++z) {
+                int m = std::max(std::abs(x), std::max(std::abs(y), std::abs(z)));
+                if (m >= 2) {
+                    o[k][0] = x;
+                    o[k][1] = y;
+                    o[k][2] = z;
+                    ++k;
+                }
+            }
+}
+
+namespace {
+struct OffsetTable {
+    int index[7 * 7 * 7];
+    OffsetTable() {
+        int o[kOffsets][3];
+        offsets316(o);
+        for (int i = 0; i < 343; ++i) index[i] = -1;
+        for (int k = 0; k < kOffsets; ++k) index[(o[k][0] + 3) * 49 + (o[k][1] + 3) * 7 + (o[k][2] + 3)] = k;
+    }
+};
+}  // namespace
+
+int offset_index(int ox, int oy, int oz) {
+    static const OffsetTable table;  // initialised once, thread-safe
+    if (ox < -3 || ox > 3 || oy < -3 || oy > 3 || oz < -3 || oz > 3) return -1;
+    return table.index[(ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
+}
+
+std::vector<double> unit_surface(int p) {
+    std::vector<double> u;
+    u.reserve(3 * surface_count(p));
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                int mn = std::min(i, std::min(j, k)), mx = std::max(i, std::max(j, k));
+                if (mn == 0 || mx == p - 1) {
+                    u.push_back(2.0 * i / (p - 1) - 1.0);
+                    u.push_back(2.0 * j / (p - 1) - 1.0);
+                    u.push_back(2.0 * k / (p - 1) - 1.0);
+                }
+            }
+    return u;
+}
+
+void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>& u, double* K) {
+    const int n = surface_count(p);
+    const double s = 1.0 + d;
+    for (int i = 0; i < n; ++i) {
+        const double xi0 = 2.0 * o[0] + s * u[3 * i], xi1 = 2.0 * o[1] + s * u[3 * i + 1],
+                     xi2 = 2.0 * o[2] + s * u[3 * i + 2];
+        for (int j = 0; j < n; ++j) {
+            const double a = xi0 - s * u[3 * j], b = xi1 - s * u[3 * j + 1], c = xi2 - s * u[3 * j + 2];
+            K[(size_t)i * n + j] = 1.0 / (4.0 * kPi * std::sqrt(a * a + b * b + c * c));
+        }
+    }
+}
+
+int check_params(const kifmm_m2l_params* prm) {
+    if (!prm) {
+        set_error("params is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (prm->kernel_id != KIFMM_KERNEL_LAPLACE) {
+        set_error("kernel_id " + std::to_string(prm->kernel_id) + " is not supported (only 0 = Laplace)");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
+    if (prm->p < 2 || prm->p > 12) {
+        set_error("p must be in [2, 12], got " + std::to_string(prm->p));
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (!(prm->d >= 0.0 && prm->d <= 2.0 / 3.0)) {
+        set_error("d must be in [0, 2/3]");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (!(prm->eps <= 0.0 || (prm->eps >= 1e-12 && prm->eps < 1.0)) || std::isnan(prm->eps)) {
+        set_error("eps must be <= 0 (no truncation) or in [1e-12, 1)");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (prm->precision < KIFMM_PREC_FP32 || prm->precision > KIFMM_PREC_SPLIT6) {
+        set_error("precision must be one of KIFMM_PREC_*");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    return KIFMM_OK;
+}
+
+namespace {
+
+// A fixed team of worker threads; run(f) calls f(tid, nthreads) on every
+// member (the caller is member 0) and returns when all are done.
+class ThreadTeam {
+  public:
+    explicit ThreadTeam(int n) : n_(n < 1 ? 1 : n) {
+        for (int t = 1; t < n_; ++t) workers_.emplace_back([this, t] { loop(t); });
+    }
+    ~ThreadTeam() {
+        {
+            std::lock_guard<std::mutex> g(m_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (auto& w : workers_) w.join();
+    }
+    int size() const { return n_; }
+    void run(const std::function<void(int, int)>& f) {
+        {
+            std::lock_guard<std::mutex> g(m_);
+            job_ = &f;
+            pending_ = n_ - 1;
+            ++gen_;
+        }
+        cv_.notify_all();
+        f(0, n_);
+        std::unique_lock<std::mutex> lk(m_);
+        done_.wait(lk, [this] { return pending_ == 0; });
+        job_ = nullptr;
+    }
+
+  private:
+    void loop(int t) {
+        unsigned long seen = 0;
+        while (true) {
+            const std::function<void(int, int)>* job;
+            {
+                std::unique_lock<std::mutex> lk(m_);
+                cv_.wait(lk, [&] { return gen_ != seen; });
+                seen = gen_;
+                if (stop_) return;
+                job = job_;
+            }
+            (*job)(t, n_);
+            {
+                std::lock_guard<std::mutex> g(m_);
+                if (--pending_ == 0) done_.notify_one();
+            }
+        }
+    }
+    int n_;
+    std::vector<std::thread> workers_;
+    std::mutex m_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int, int)>* job_ = nullptr;
+    unsigned long gen_ = 0;
+    int pending_ = 0;
+    bool stop_ = false;
+};
+
+int team_size() {
+    const char* env = std::getenv("KIFMM_M2L_THREADS");
+    int n = env ? std::atoi(env) : (int)std::thread::hardware_concurrency();
+    if (n < 1) n = 1;
+    if (n > 64) n = 64;
+    return n;
+}
+
+// Merge a dense block B (mb x n, column-major) into the upper-triangular R
+// (n x n, column-major): on return R is the triangular factor of [R; B].
+// B is overwritten with Householder vectors.
+void householder_merge(int n, double* R, int mb, double* B) {
+    for (int k = 0; k < n; ++k) {
+        double* bk = B + (size_t)k * mb;
+        double xn2 = 0.0;
+        for (int i = 0; i < mb; ++i) xn2 += bk[i] * bk[i];
+        if (xn2 == 0.0) continue;
+        const double alpha = R[k + (size_t)k * n];
+        const double beta = (alpha >= 0.0 ? -1.0 : 1.0) * std::sqrt(alpha * alpha + xn2);
+        const double tau = (beta - alpha) / beta;
+        const double scale = 1.0 / (alpha - beta);
+        for (int i = 0; i < mb; ++i) bk[i] *= scale;
+        R[k + (size_t)k * n] = beta;
+        for (int c = k + 1; c < n; ++c) {
+            double* bc = B + (size_t)c * mb;
+            double w = R[k + (size_t)c * n];
+            for (int i = 0; i < mb; ++i) w += bk[i] * bc[i];
+            w *= tau;
+            R[k + (size_t)c * n] -= w;
+            for (int i = 0; i < mb; ++i) bc[i] -= w * bk[i];
+        }
+    }
+}
+
+// Triangular factor of K_fat^T (316 n x n).  Returns R, column-major n x n.
+std::vector<double> tsqr_kfat_t(int p, double d, const std::vector<double>& u, ThreadTeam& team) {
+    const int n = surface_count(p);
+    int offs[kOffsets][3];
+    offsets316(offs);
+    const int nthreads = team.size();
+    std::vector<std::vector<double>> Rt(nthreads, std::vector<double>((size_t)n * n, 0.0));
+    team.run([&](int tid, int) {
+        std::vector<double> K((size_t)n * n), B((size_t)n * n);
+        const int lo = (int)((long)kOffsets * tid / nthreads), hi = (int)((long)kOffsets * (tid + 1) / nthreads);
+        for (int k = lo; k < hi; ++k) {
+            unit_m2l_matrix(p, d, offs[k], u, K.data());
+            // block of K_fat^T: rows j (source points), columns i; B(j,i) = K_o[i][j]
+            // column-major B: column i contiguous over j -> B[i*n + j] = K[i*n + j]
+            std::copy(K.begin(), K.end(), B.begin());
+            householder_merge(n, Rt[tid].data(), n, B.data());
+        }
+    });
+    std::vector<double> R = Rt[0];
+    for (int t = 1; t < nthreads; ++t) householder_merge(n, R.data(), n, Rt[t].data());
+    return R;
+}
+
+// One-sided Jacobi on A (n x n column-major, n even).  On return V holds
+// the right singular vectors (column-major) and sig the singular values,
+// both sorted by descending singular value.
+void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& sig, ThreadTeam& team) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i + (size_t)i * n] = 1.0;
+    const double tol = 1e-15;
+    // round-robin tournament: player 0 fixed, others rotate
+    std::vector<int> ring(n);
+    std::iota(ring.begin(), ring.end(), 0);
+    std::vector<long> rot_count(team.size());
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        long rotations = 0;
+        std::fill(rot_count.begin(), rot_count.end(), 0L);
+        for (int round = 0; round < n - 1; ++round) {
+          team.run([&](int tid, int nt) {
+            for (int m = tid; m < n / 2; m += nt) {
+                int a = ring[m], b = ring[n - 1 - m];
+                if (a > b) std::swap(a, b);
+                double* ap = A.data() + (size_t)a * n;
+                double* aq = A.data() + (size_t)b * n;
+                double alpha = 0, beta = 0, gamma = 0;
+                for (int i = 0; i < n; ++i) {
+                    alpha += ap[i] * ap[i];
+                    beta += aq[i] * aq[i];
+                    gamma += ap[i] * aq[i];
+                }
+                if (gamma == 0.0 || std::fabs(gamma) <= tol * std::sqrt(alpha * beta)) continue;
+                const double zeta = (beta - alpha) / (2.0 * gamma);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                for (int i = 0; i < n; ++i) {
+                    const double x = ap[i], y = aq[i];
+                    ap[i] = c * x - s * y;
+                    aq[i] = s * x + c * y;
+                }
+                double* vp = V.data() + (size_t)a * n;
+                double* vq = V.data() + (size_t)b * n;
+                for (int i = 0; i < n; ++i) {
+                    const double x = vp[i], y = vq[i];
+                    vp[i] = c * x - s * y;
+                    vq[i] = s * x + c * y;
+                }
+                ++rot_count[tid];
+            }
+          });
+            // rotate positions 1..n-1
+            int last = ring[n - 1];
+            for (int i = n - 1; i > 1; --i) ring[i] = ring[i - 1];
+            ring[1] = last;
+        }
+        for (long c : rot_count) rotations += c;
+        if (rotations == 0) break;
+    }
+    std::vector<double> s(n);
+    for (int j = 0; j < n; ++j) {
+        double acc = 0;
+        const double* aj = A.data() + (size_t)j * n;
+        for (int i = 0; i < n; ++i) acc += aj[i] * aj[i];
+        s[j] = std::sqrt(acc);
+    }
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return s[x] > s[y]; });
+    std::vector<double> Vs((size_t)n * n);
+    sig.resize(n);
+    for (int j = 0; j < n; ++j) {
+        sig[j] = s[ord[j]];
+        std::copy(V.begin() + (size_t)ord[j] * n, V.begin() + (size_t)(ord[j] + 1) * n, Vs.begin() + (size_t)j * n);
+    }
+    V.swap(Vs);
+}
+
+int truncation_rank(const std::vector<double>& sig, double eps) {
+    const int n = (int)sig.size();
+    if (eps <= 0) return n;
+    int r = 0;
+    while (r < n && sig[r] >= eps * sig[0]) ++r;
+    while (r > 0 && r < n && sig[r - 1] - sig[r] <= kTieTol * sig[0]) ++r;
+    return r;
+}
+
+std::string cache_path(const kifmm_m2l_params& prm) {
+    const char* dir = std::getenv("KIFMM_M2L_CACHE");
+    if (!dir || !*dir) return std::string();
+    char name[256];
+    std::snprintf(name, sizeof(name), "/kifmm_m2l_v%u_k%d_p%d_d%.17g_eps%.17g.bin", kCacheVersion, prm.kernel_id,
+                  prm.p, prm.d, prm.eps);
+    return std::string(dir) + name;
+}
+
+bool load_cache(const std::string& path, const kifmm_m2l_params& prm, Factors& f) {
+    if (path.empty()) return false;
+    FILE* fp = std::fopen(path.c_str(), "rb");
+    if (!fp) return false;
+    unsigned hdr[2];
+    int dims[4];
+    double pd[2];
+    bool ok = std::fread(hdr, sizeof(hdr), 1, fp) == 1 && hdr[0] == kCacheMagic && hdr[1] == kCacheVersion &&
+              std::fread(dims, sizeof(dims), 1, fp) == 1 && std::fread(pd, sizeof(pd), 1, fp) == 1 &&
+              dims[0] == prm.kernel_id && dims[1] == prm.p && pd[0] == prm.d && pd[1] == prm.eps;
+    if (ok) {
+        f.p = dims[1];
+        f.n = surface_count(f.p);
+        f.r = dims[2];
+        ok = dims[3] == f.n && f.r >= 1 && f.r <= f.n;
+    }
+    if (ok) {
+        f.d = prm.d;
+        f.eps = prm.eps;
+        f.sigma.resize(f.n);
+        f.U.resize((size_t)f.n * f.r);
+        f.C.resize((size_t)kOffsets * f.r * f.r);
+        ok = std::fread(f.sigma.data(), sizeof(double), f.n, fp) == (size_t)f.n &&
+             std::fread(f.U.data(), sizeof(double), f.U.size(), fp) == f.U.size() &&
+             std::fread(f.C.data(), sizeof(double), f.C.size(), fp) == f.C.size() &&
+             std::fread(&f.sym_err, sizeof(double), 1, fp) == 1;
+    }
+    std::fclose(fp);
+    return ok;
+}
+
+void store_cache(const std::string& path, const kifmm_m2l_params& prm, const Factors& f) {
+    if (path.empty()) return;
+    std::string tmp = path + ".tmp" + std::to_string((long)std::rand());
+    FILE* fp = std::fopen(tmp.c_str(), "wb");
+    if (!fp) return;
+    unsigned hdr[2] = {kCacheMagic, kCacheVersion};
+    int dims[4] = {prm.kernel_id, prm.p, f.r, f.n};
+    double pd[2] = {prm.d, prm.eps};
+    bool ok = std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 && std::fwrite(dims, sizeof(dims), 1, fp) == 1 &&
+              std::fwrite(pd, sizeof(pd), 1, fp) == 1 &&
+              std::fwrite(f.sigma.data(), sizeof(double), f.n, fp) == (size_t)f.n &&
+              std::fwrite(f.U.data(), sizeof(double), f.U.size(), fp) == f.U.size() &&
+              std::fwrite(f.C.data(), sizeof(double), f.C.size(), fp) == f.C.size() &&
+              std::fwrite(&f.sym_err, sizeof(double), 1, fp) == 1;
+    ok = (std::fclose(fp) == 0) && ok;
+    if (ok)
+        std::rename(tmp.c_str(), path.c_str());
+    else
+        std::remove(tmp.c_str());
+}
+
+}  // namespace
+
+int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
+    int st = check_params(&prm);
+    if (st != KIFMM_OK) return st;
+    const std::string cpath = cache_path(prm);
+    if (load_cache(cpath, prm, f)) return KIFMM_OK;
+
+    const int p = prm.p, n = surface_count(p);
+    const std::vector<double> u = unit_surface(p);
+    try {
+        ThreadTeam team(team_size());
+        std::vector<double> R = tsqr_kfat_t(p, prm.d, u, team);
+        // zero the strict lower triangle (Householder vectors are not stored in R)
+        for (int c = 0; c < n; ++c)
+            for (int i = c + 1; i < n; ++i) R[i + (size_t)c * n] = 0.0;
+        std::vector<double> V, sig;
+        jacobi_svd(n, R, V, sig, team);
+        const int r = truncation_rank(sig, prm.eps);
+
+        f.p = p;
+        f.n = n;
+        f.r = r;
+        f.d = prm.d;
+        f.eps = prm.eps;
+        f.sigma = sig;
+        f.U.assign((size_t)n * r, 0.0);
+        for (int j = 0; j < r; ++j) {
+            // sign rule: the largest-magnitude entry of each column is positive
+            const double* vj = V.data() + (size_t)j * n;
+            int imax = 0;
+            for (int i = 1; i < n; ++i)
+                if (std::fabs(vj[i]) > std::fabs(vj[imax])) imax = i;
+            const double sgn = vj[imax] < 0 ? -1.0 : 1.0;
+            for (int i = 0; i < n; ++i) f.U[(size_t)i * r + j] = sgn * vj[i];
+        }
+
+        // cores K~_o = U~^T K_o U~
+        int offs[kOffsets][3];
+        offsets316(offs);
+        f.C.assign((size_t)kOffsets * r * r, 0.0);
+        team.run([&](int tid, int nt) {
+            std::vector<double> K((size_t)n * n), T((size_t)n * r);
+            for (int k = tid; k < kOffsets; k += nt) {
+                unit_m2l_matrix(p, prm.d, offs[k], u, K.data());
+                // T = K_o U~  (n x r)
+                std::fill(T.begin(), T.end(), 0.0);
+                for (int i = 0; i < n; ++i) {
+                    double* ti = T.data() + (size_t)i * r;
+                    const double* ki = K.data() + (size_t)i * n;
+                    for (int j = 0; j < n; ++j) {
+                        const double kij = ki[j];
+                        const double* uj = f.U.data() + (size_t)j * r;
+                        for (int b = 0; b < r; ++b) ti[b] += kij * uj[b];
+                    }
+                }
+                // C = U~^T T  (r x r)
+                double* ck = f.C.data() + (size_t)k * r * r;
+                for (int i = 0; i < n; ++i) {
+                    const double* ui = f.U.data() + (size_t)i * r;
+                    const double* ti = T.data() + (size_t)i * r;
+                    for (int a = 0; a < r; ++a) {
+                        const double uia = ui[a];
+                        double* ca = ck + (size_t)a * r;
+                        for (int b = 0; b < r; ++b) ca[b] += uia * ti[b];
+                    }
+                }
+            }
+        });
+        // symmetry K~_o^T = K~_{-o}
+        double cmax = 0, dmax = 0;
+        for (int k = 0; k < kOffsets; ++k) {
+            const int km = offset_index(-offs[k][0], -offs[k][1], -offs[k][2]);
+            const double* ck = f.C.data() + (size_t)k * r * r;
+            const double* cm = f.C.data() + (size_t)km * r * r;
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b) {
+                    cmax = std::max(cmax, std::fabs(ck[(size_t)a * r + b]));
+                    dmax = std::max(dmax, std::fabs(ck[(size_t)a * r + b] - cm[(size_t)b * r + a]));
+                }
+        }
+        f.sym_err = cmax > 0 ? dmax / cmax : 0.0;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed in the FP64 precompute");
+        return KIFMM_ERR_OOM;
+    }
+    store_cache(cpath, prm, f);
+    return KIFMM_OK;
+}
+
+int build_pairs(int level, int n_boxes, const int32_t* ijk, std::vector<int32_t>& tgt, std::vector<int32_t>& src,
+                std::vector<int32_t>& off) {
+    tgt.clear();
+    src.clear();
+    off.clear();
+    if (level < 0 || level > 20 || n_boxes < 0 || (n_boxes > 0 && !ijk)) {
+        set_error("invalid level / n_boxes / box_ijk");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    const int64_t m = int64_t(1) << level;
+    std::vector<std::pair<int64_t, int32_t>> keys(n_boxes);
+    for (int b = 0; b < n_boxes; ++b) {
+        const int64_t x = ijk[3 * b], y = ijk[3 * b + 1], z = ijk[3 * b + 2];
+        if (x < 0 || y < 0 || z < 0 || x >= m || y >= m || z >= m) {
+            set_error("box " + std::to_string(b) + " has coordinates outside [0, 2^level)");
+            return KIFMM_ERR_INVALID_ARG;
+        }
+        keys[b] = {(x << 42) | (y << 21) | z, b};
+    }
+    std::sort(keys.begin(), keys.end());
+    for (int b = 1; b < n_boxes; ++b)
+        if (keys[b].first == keys[b - 1].first) {
+            set_error("duplicate box coordinates");
+            return KIFMM_ERR_INVALID_ARG;
+        }
+    auto find = [&](int64_t x, int64_t y, int64_t z) -> int32_t {
+        if (x < 0 || y < 0 || z < 0 || x >= m || y >= m || z >= m) return -1;
+        const int64_t key = (x << 42) | (y << 21) | z;
+        auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key, (int32_t)-1));
+        return (it != keys.end() && it->first == key) ? it->second : -1;
+    };
+    // per offset buckets (offset-major order), each bucket in target order
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> bucket(kOffsets);
+    for (int t = 0; t < n_boxes; ++t) {
+        const int64_t tx = ijk[3 * t], ty = ijk[3 * t + 1], tz = ijk[3 * t + 2];
+        const int64_t px = tx >> 1, py = ty >> 1, pz = tz >> 1;
+        // children of the parent's near-field boxes (Sec. 2.1), minus t's near field
+        for (int64_t sx = 2 * px - 2; sx <= 2 * px + 3; ++sx)
+            for (int64_t sy = 2 * py - 2; sy <= 2 * py + 3; ++sy)
+                for (int64_t sz = 2 * pz - 2; sz <= 2 * pz + 3; ++sz) {
+                    const int64_t ox = tx - sx, oy = ty - sy, oz = tz - sz;
+                    if (std::max(std::llabs(ox), std::max(std::llabs(oy), std::llabs(oz))) <= 1) continue;
+                    const int32_t s = find(sx, sy, sz);
+                    if (s < 0) continue;
+                    bucket[offset_index((int)ox, (int)oy, (int)oz)].push_back({t, s});
+                }
+    }
+    size_t total = 0;
+    for (auto& b : bucket) total += b.size();
+    tgt.reserve(total);
+    src.reserve(total);
+    off.reserve(total);
+    for (int k = 0; k < kOffsets; ++k)
+        for (auto& ts : bucket[k]) {
+            tgt.push_back(ts.first);
+            src.push_back(ts.second);
+            off.push_back(k);
+        }
+    return KIFMM_OK;
+}
+
+}  // namespace kifmm

@@ -1,0 +1,157 @@
+"""Python face of the SVD-compressed M2L library (thin marshalling layer).
+
+Every step of the translation runs in libkifmm_m2l.so; this module turns
+torch tensors and NumPy arrays into pointers and sizes.  PyTorch is used
+for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import PREC, Params, call, lib
+
+
+def _params(p: int, eps: float, d: float, precision: str, kernel_id: int = 0) -> Params:
+    if precision not in PREC:
+        raise ValueError(f"precision must be one of {sorted(PREC)}")
+    return Params(kernel_id, int(p), float(eps), float(d), PREC[precision])
+
+
+def surface_count(p: int) -> int:
+    """Equivalent / check points per surface: 6(p-1)^2 + 2."""
+    return 6 * (p - 1) ** 2 + 2
+
+
+def factors_host(p: int, eps: float, d: float = 0.1):
+    """Run the library's FP64 precompute on the host.
+
+    Returns (sigma [n], U [n, r], C [316, r, r]) as float64 arrays.
+    """
+    prm = _params(p, eps, d, "fp32")
+    n, r = ctypes.c_int(0), ctypes.c_int(0)
+    call("kifmm_m2l_factors_host", ctypes.byref(prm), ctypes.byref(n), ctypes.byref(r), None, None, None)
+    sigma = np.empty(n.value)
+    U = np.empty((n.value, r.value))
+    C = np.empty((_lib.N_OFFSETS, r.value, r.value))
+    call("kifmm_m2l_factors_host", ctypes.byref(prm), ctypes.byref(n), ctypes.byref(r),
+         sigma.ctypes.data, U.ctypes.data, C.ctypes.data)
+    return sigma, U, C
+
+
+def pairs_host(level: int, box_ijk):
+    """Interaction-list pairs built by the library on the host.
+
+    Returns (targets, sources, offset_index) int32 arrays sorted by offset
+    then target.
+    """
+    box = np.ascontiguousarray(box_ijk, dtype=np.int32).reshape(-1, 3)
+    cnt = ctypes.c_int64(0)
+    call("kifmm_m2l_pairs_host", int(level), box.shape[0], box.ctypes.data, ctypes.byref(cnt), None, None, None)
+    tg = np.empty(cnt.value, np.int32)
+    sr = np.empty(cnt.value, np.int32)
+    of = np.empty(cnt.value, np.int32)
+    call("kifmm_m2l_pairs_host", int(level), box.shape[0], box.ctypes.data, ctypes.byref(cnt),
+         tg.ctypes.data, sr.ctypes.data, of.ctypes.data)
+    return tg, sr, of
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_tensor(x, name, shape):
+    import torch
+
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+
+
+class M2LPlan:
+    """A precomputed compressed M2L operator plus registered octree levels.
+
+    ``precision``: "fp32" (CUDA cores), "bf16", "split3" or "split6"
+    (tcgen05 tensor cores; split6 keeps FP32-level accuracy).
+    """
+
+    def __init__(self, p: int, eps: float, d: float = 0.1, precision: str = "split6", kernel_id: int = 0):
+        self.p, self.eps, self.d, self.precision = int(p), float(eps), float(d), precision
+        self._h = ctypes.c_void_p(None)
+        prm = _params(p, eps, d, precision, kernel_id)
+        call("kifmm_m2l_precompute", ctypes.byref(prm), ctypes.byref(self._h))
+        r, rp, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        call("kifmm_m2l_plan_rank", self._h, ctypes.byref(r), ctypes.byref(rp), ctypes.byref(n))
+        self.r, self.r_pad, self.n = r.value, rp.value, n.value
+        self._levels = {}
+
+    # -- lifetime -------------------------------------------------------
+    def close(self) -> None:
+        if self._h:
+            lib().kifmm_m2l_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- levels ---------------------------------------------------------
+    def set_level(self, level: int, box_ijk, root_halfwidth: float, instance: int = 0) -> int:
+        """Register the boxes of one level; returns the number of M2L pairs."""
+        box = np.ascontiguousarray(box_ijk, dtype=np.int32).reshape(-1, 3)
+        call("kifmm_m2l_set_level", self._h, int(instance), int(level), float(root_halfwidth), box.shape[0],
+             box.ctypes.data)
+        cnt = ctypes.c_int64(0)
+        call("kifmm_m2l_level_pairs", self._h, int(instance), int(level), ctypes.byref(cnt))
+        self._levels[(instance, level)] = box.shape[0]
+        return cnt.value
+
+    def n_boxes(self, level: int, instance: int = 0) -> int:
+        return self._levels[(instance, level)]
+
+    # -- translation ----------------------------------------------------
+    def _run(self, fname, x, level, instance, out, beta, stream):
+        import torch
+
+        if (instance, level) not in self._levels:
+            cnt = ctypes.c_int64(0)  # the library reports the unregistered level
+            call("kifmm_m2l_level_pairs", self._h, int(instance), int(level), ctypes.byref(cnt))
+        nb = self._levels[(instance, level)]
+        squeeze = x.dim() == 2
+        nrhs = 1 if squeeze else x.shape[1]
+        shape = (nb, self.n) if squeeze else (nb, nrhs, self.n)
+        _check_tensor(x, "input", shape)
+        if out is None:
+            out = torch.empty(shape, device=x.device, dtype=torch.float32)
+            beta = 0.0
+        _check_tensor(out, "out", shape)
+        call(fname, self._h, int(instance), int(level), int(nrhs), ctypes.c_void_p(x.data_ptr()),
+             ctypes.c_void_p(out.data_ptr()), float(beta), _stream_handle(stream))
+        return out
+
+    def apply(self, q_up, level: int, instance: int = 0, out=None, beta: float = 0.0, stream=None):
+        """Compressed M2L: out = beta*out + U~ s_l sum K~ R~^T q_up."""
+        return self._run("kifmm_m2l_apply", q_up, level, instance, out, beta, stream)
+
+    def apply_adjoint(self, pbar, level: int, instance: int = 0, out=None, beta: float = 0.0, stream=None):
+        """Transpose of ``apply``: out = beta*out + R~ s_l sum K~^T U~^T pbar."""
+        return self._run("kifmm_m2l_apply_adjoint", pbar, level, instance, out, beta, stream)
+
+    def apply_dense(self, q_up, level: int, instance: int = 0, out=None, beta: float = 0.0, stream=None):
+        """Uncompressed FP32 M2L (the baseline)."""
+        return self._run("kifmm_m2l_apply_dense", q_up, level, instance, out, beta, stream)
+
+    def sync(self, stream=None) -> None:
+        """Synchronise the stream and raise on device-side failures."""
+        call("kifmm_m2l_sync", self._h, _stream_handle(stream))

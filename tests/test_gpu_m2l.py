@@ -1,0 +1,236 @@
+"""GPU parity of the compressed M2L (and its adjoint and dense baseline)
+against the FP64 oracle, called through the C ABI.
+
+Tolerances (relative L2 over all outputs of a level):
+  fp32, split6 : 1e-6  (the gate; an FP32 pipeline lands at ~5e-7 because
+                 V^T compression, core sums and U expansion each round)
+  split3       : 3e-5  (2-piece BF16 split keeps ~16 significand bits)
+  bf16         : 1e-2  (8 significand bits)
+The oracle runs at the same eps, so both sides truncate at the same rank
+and only rounding differs.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import geometry as geo
+from oracle import m2l as om
+from oracle import upward
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-6, "split6": 1e-6, "split3": 3e-5, "bf16": 1e-2}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    os.environ.setdefault("KIFMM_M2L_CACHE", tempfile.mkdtemp(prefix="kifmm_cache_"))
+    from paper_1211_2517_gb300 import build
+
+    build.build()
+    import paper_1211_2517_gb300 as pkg
+
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def cube():
+    """Uniform cube, 16384 points, depth 3, p = 6, eps = 1e-8, S2M/M2M inputs."""
+    wl = synth.workload("cube16k_p6")
+    qup = upward.upward_pass(wl.tree, wl.points, wl.p, wl.d, wl.densities)
+    return wl, {l: qup[l].astype(np.float32) for l in (2, 3)}
+
+
+@pytest.fixture(scope="module")
+def sphere_small():
+    """Sphere, 60000 points, depth 4, p = 8, eps = 1e-7 (random densities, 3 rhs)."""
+    pts = synth.points_sphere(60_000, 7)
+    tree = synth.build_tree(pts, 4)
+    qs = {l: synth.random_box_densities(tree.levels[l].shape[0], 3, 296, 100 + l) for l in (2, 3, 4)}
+    return tree, qs
+
+
+def make_plan(g, p, eps, precision, tree, levels):
+    plan = g.M2LPlan(p, eps, 0.1, precision)
+    for l in levels:
+        plan.set_level(l, tree.levels[l], tree.r0)
+    return plan
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split6", "split3", "bf16"])
+def test_compressed_parity_cube(g, oracle_factors, cube, precision):
+    wl, qup = cube
+    f = oracle_factors(wl.p, wl.d, wl.eps)
+    plan = make_plan(g, wl.p, wl.eps, precision, wl.tree, (2, 3))
+    assert plan.r == f.r
+    for l in (2, 3):
+        box = wl.tree.levels[l]
+        ref = om.m2l_svd(box, l, wl.tree.r0, f, qup[l].astype(np.float64))
+        out = plan.apply(torch.from_numpy(qup[l]).cuda(), l)
+        plan.sync()
+        err = rel(out.cpu().numpy(), ref)
+        print(f"cube p=6 level {l} {precision}: rel L2 {err:.3e}")
+        assert err <= TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split6", "split3"])
+def test_compressed_parity_multi_rhs(g, oracle_factors, sphere_small, precision):
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, precision, tree, (2, 3, 4))
+    for l in (2, 3, 4):
+        ref = om.m2l_svd(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64))
+        out = plan.apply(torch.from_numpy(qs[l]).cuda(), l)
+        plan.sync()
+        err = rel(out.cpu().numpy(), ref)
+        print(f"sphere p=8 level {l} nrhs=3 {precision}: rel L2 {err:.3e}")
+        assert err <= TOL[precision], err
+
+
+def test_dense_parity(g, cube):
+    wl, qup = cube
+    K = om.unit_m2l_matrices(wl.p, wl.d)
+    plan = make_plan(g, wl.p, wl.eps, "fp32", wl.tree, (2, 3))
+    for l in (2, 3):
+        ref = om.m2l_dense_unit(wl.tree.levels[l], l, wl.tree.r0, K, qup[l].astype(np.float64))
+        out = plan.apply_dense(torch.from_numpy(qup[l]).cuda(), l)
+        plan.sync()
+        err = rel(out.cpu().numpy(), ref)
+        print(f"dense p=6 level {l}: rel L2 {err:.3e}")
+        assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split6"])
+def test_adjoint_parity_and_dot_product(g, oracle_factors, sphere_small, precision):
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, precision, tree, (3, 4))
+    rng = np.random.default_rng(9)
+    for l in (3, 4):
+        y = rng.standard_normal(qs[l].shape).astype(np.float32)
+        ref = om.m2l_svd_adjoint(tree.levels[l], l, tree.r0, f, y.astype(np.float64))
+        x = torch.from_numpy(qs[l]).cuda()
+        yt = torch.from_numpy(y).cuda()
+        aty = plan.apply_adjoint(yt, l)
+        ax = plan.apply(x, l)
+        plan.sync()
+        err = rel(aty.cpu().numpy(), ref)
+        print(f"adjoint level {l} {precision}: rel L2 {err:.3e}")
+        assert err <= TOL[precision], err
+        lhs = float((ax.double() * yt.double()).sum())
+        rhs = float((x.double() * aty.double()).sum())
+        assert abs(lhs - rhs) <= 1e-5 * ax.double().norm().item() * yt.double().norm().item()
+
+
+def test_beta_accumulates(g, cube):
+    wl, qup = cube
+    plan = make_plan(g, wl.p, wl.eps, "split6", wl.tree, (3,))
+    x = torch.from_numpy(qup[3]).cuda()
+    base = plan.apply(x, 3)
+    prev = torch.randn_like(base)
+    out = prev.clone()
+    plan.apply(x, 3, out=out, beta=0.5)
+    plan.sync()
+    torch.testing.assert_close(out, 0.5 * prev + base, rtol=1e-5, atol=1e-5 * base.abs().max().item())
+    dense = plan.apply_dense(x, 3)
+    out2 = prev.clone()
+    plan.apply_dense(x, 3, out=out2, beta=1.0)
+    plan.sync()
+    torch.testing.assert_close(out2, prev + dense, rtol=1e-5, atol=1e-5 * dense.abs().max().item())
+
+
+def test_edge_cases(g):
+    from paper_1211_2517_gb300._lib import KifmmError
+
+    plan = g.M2LPlan(4, 1e-4, 0.1, "split6")
+    n = plan.n
+    # empty level
+    plan.set_level(2, np.zeros((0, 3), np.int32), 1.0)
+    out = plan.apply(torch.zeros((0, n), device="cuda"), 2)
+    assert out.shape == (0, n)
+    # a single box has no interaction partners: output zero
+    plan.set_level(3, np.array([[3, 4, 5]]), 1.0)
+    out = plan.apply(torch.randn(1, n, device="cuda"), 3)
+    plan.sync()
+    assert torch.count_nonzero(out).item() == 0
+    # apply before set_level
+    with pytest.raises(KifmmError):
+        plan.apply(torch.zeros((4, n), device="cuda"), 5)
+    # wrong shape is caught before the call
+    with pytest.raises(ValueError):
+        plan.apply(torch.zeros((2, n), device="cuda"), 3)
+
+
+def test_autograd_central_differences(g, oracle_factors):
+    """Loss 0.5 ||A q - phi||^2 w.r.t. the densities q (sphere, p = 8)."""
+    from paper_1211_2517_gb300.autograd import m2l
+
+    pts = synth.points_sphere(80_000, 21)
+    tree = synth.build_tree(pts, 4)
+    l = 4
+    plan = make_plan(g, 8, 1e-7, "split6", tree, (l,))
+    nb = tree.levels[l].shape[0]
+    rng = np.random.default_rng(22)
+    q = torch.from_numpy(rng.standard_normal((nb, 296)).astype(np.float32)).cuda().requires_grad_(True)
+    phi = torch.from_numpy(rng.standard_normal((nb, 296)).astype(np.float32)).cuda()
+
+    def loss(x):
+        return 0.5 * ((m2l(x, plan, l).double() - phi.double()) ** 2).sum()
+
+    L = loss(q)
+    L.backward()
+    grad = q.grad.double()
+    # against the oracle's transpose product A^T (A q - phi)
+    f = oracle_factors(8, 0.1, 1e-7)
+    box = tree.levels[l]
+    qn = q.detach().cpu().numpy().astype(np.float64)
+    resid = om.m2l_svd(box, l, tree.r0, f, qn) - phi.cpu().numpy()
+    gref = om.m2l_svd_adjoint(box, l, tree.r0, f, resid)
+    assert rel(grad.cpu().numpy(), gref) < 1e-5
+    # Central differences, h = 1e-3, along seeded directions v = g/rms(g) + z/2
+    # (z ~ N(0,1)): O(1) entries survive FP32 rounding of q + h v, and the
+    # gradient component keeps <grad L, v> well above the rounding noise of
+    # the FP32 forward (the loss is quadratic: only rounding separates them).
+    h = 1e-3
+    gdir = grad.float() / grad.float().pow(2).mean().sqrt()
+    for j in range(8):
+        z = torch.from_numpy(rng.standard_normal((nb, 296)).astype(np.float32)).cuda()
+        v = gdir + 0.5 * z
+        with torch.no_grad():
+            lp = float(loss(q + h * v))
+            lm = float(loss(q - h * v))
+        fd = (lp - lm) / (2 * h)
+        an = float((grad * v.double()).sum())
+        assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)
+
+
+def test_full_size_sphere_sampled(g, oracle_factors):
+    """The 2M-point sphere at depth 6, p = 8, eps = 1e-7 (the benchmark
+    workload, split6), every level, on sampled targets the oracle computes
+    one by one."""
+    wl = synth.workload("sphere2m_p8")
+    tree = wl.tree
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, "split6", tree, range(2, 7))
+    rng = np.random.default_rng(5)
+    for l in range(2, 7):
+        nb = tree.levels[l].shape[0]
+        q = synth.random_box_densities(nb, 1, 296, 300 + l)[:, 0, :]
+        out = plan.apply(torch.from_numpy(q).cuda(), l)
+        plan.sync()
+        tg = np.sort(rng.choice(nb, size=min(24, nb), replace=False))
+        ref = om.m2l_svd_targets(tree.levels[l], l, tree.r0, f, q.astype(np.float64), tg)[:, 0, :]
+        err = rel(out.cpu().numpy()[tg], ref)
+        print(f"sphere2m level {l}: sampled rel L2 {err:.3e}")
+        assert err <= 1e-6, err
