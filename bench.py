@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the SVD-compressed M2L translation on GB300.
+
+One step = one compressed M2L apply (V^T compression, offset-grouped core
+products over the interaction lists, U expansion) over every level 2..6 of
+the synthetic 2,097,152-point sphere workload (depth 6, p = 8, n = 296,
+eps = 1e-7, d = 0.1, one right-hand side), i.e. 1,158,296 box-pair
+translations.  Inputs are resident in HBM when the timed region starts and
+L2 is flushed (a 256 MB write) before every timed step.
+
+Prints ONE JSON line (rank 0).  Besides the throughput it reports the
+tensor roofline of the core kernel (tracing with CUDA events), an end-to-end
+number through the public API with pinned host buffers, the plain FP32
+dense M2L on the same GPU, the adjoint, SM clocks sampled during the timed
+region, and the FP64 oracle timed on the host cores (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica
+of the workload (weak scaling: the M2L of independent FMM instances needs
+no data exchange) and the slowest rank's time is reported.
+``--impl reference`` times the FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "M2L box-pair translations/s and % tensor roofline vs dense M2L, rel err ≤1e-6"
+UNIT = "box-pair translations/s"
+WORKLOAD = "sphere2m_p8"
+LEVELS = range(2, 7)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def workload_desc(pairs, r, r_pad, precision):
+    return {
+        "workload": "sphere2m_p8: 2,097,152 points uniform on the unit sphere (normalised Gaussian, seed 0), "
+                    "uniform octree depth 6 with empty boxes skipped, levels 2-6, p=8 (n=296), eps=1e-7, d=0.1, "
+                    "Laplace 1/(4 pi r), 1 right-hand side, upward-equivalent densities N(0,1)",
+        "pairs_per_step": pairs,
+        "rank_r": r,
+        "r_pad": r_pad,
+        "precision": precision,
+        "l2": "flushed before every timed step (256 MB write)",
+        "scaling_units": "independent replicas, one per GPU",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, n = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0] and parts[0] not in self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            n += 1
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+_ORACLE_FACTORS = {}
+
+
+def oracle_sample(wl, seconds_budget):
+    """Time the FP64 oracle's compressed M2L on a bounded slice of the
+    workload (its precompute, like the library's, is not timed); returns
+    (pairs, seconds, description)."""
+    import numpy as np
+
+    import synth
+    from oracle import geometry as geo
+    from oracle import m2l as om
+
+    key = (wl.p, wl.d, wl.eps)
+    if key not in _ORACLE_FACTORS:
+        _ORACLE_FACTORS[key] = om.svd_factors(wl.p, wl.d, wl.eps)
+    f = _ORACLE_FACTORS[key]
+    done_pairs, spent, parts = 0, 0.0, []
+    for level in LEVELS:
+        box = wl.tree.levels[level]
+        tg, sr, ok = geo.interaction_lists(box)
+        q = synth.random_box_densities(box.shape[0], 1, f.U.shape[0], 1000 + level)[:, 0].astype(np.float64)
+        # whole level if the budget allows, else the first targets that fit
+        est = tg.size / 1.5e5
+        if spent + est > seconds_budget and done_pairs > 0:
+            frac = max(0.0, (seconds_budget - spent) / est)
+            if frac < 0.02:
+                break
+            nt = max(1, int(frac * box.shape[0]))
+            sel = tg < nt
+            tg, sr, ok = tg[sel], sr[sel], ok[sel]
+            parts.append(f"level {level}: targets 0..{nt - 1} ({tg.size} pairs)")
+        else:
+            parts.append(f"level {level}: all {tg.size} pairs")
+        t0 = time.perf_counter()
+        om.m2l_svd(box, level, wl.tree.r0, f, q, (tg, sr, ok))
+        spent += time.perf_counter() - t0
+        done_pairs += tg.size
+        if spent > seconds_budget:
+            break
+    return done_pairs, spent, "oracle.m2l.m2l_svd (NumPy FP64, BLAS) on " + "; ".join(parts)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import synth
+
+    wl = synth.workload(WORKLOAD)
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(wl, budget)
+    pairs = secs = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        p, s, desc = oracle_sample(wl, budget)
+        pairs += p
+        secs += s
+    value = pairs / secs
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(None, None, None, "fp64 oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_umma.cu",):
+        h.update(open(os.path.join(ROOT, "paper_1211_2517_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per core launch from the committed ncu summary, when it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "m2l_core_sphere2m_p8_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_step_core")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import numpy as np
+
+    import synth
+    from paper_1211_2517_gb300 import M2LPlan
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    peak_src = "measured" if "bf16_tflops" in peaks else "fallback"
+
+    wl = synth.workload(WORKLOAD, seed=rank)
+    tree = wl.tree
+    plan = M2LPlan(wl.p, wl.eps, wl.d, args.precision)
+    pairs = {}
+    for l in LEVELS:
+        pairs[l] = plan.set_level(l, tree.levels[l], tree.r0)
+    total_pairs = sum(pairs.values())
+    n, r, rp = plan.n, plan.r, plan.r_pad
+    q = {l: torch.from_numpy(synth.random_box_densities(tree.levels[l].shape[0], 1, n, 100 + l)[:, 0]).to(dev)
+         for l in LEVELS}
+    out = {l: torch.empty_like(q[l]) for l in LEVELS}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(fn=plan.apply, src=q, dst=out):
+        for l in LEVELS:
+            fn(src[l], l, out=dst[l])
+
+    def timed(fn_step, k):
+        evs = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn_step()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+
+    # ---- timed region --------------------------------------------------
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", ""))
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total_ms = timed(step, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    plan.sync()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    units = torch.tensor([float(total_pairs)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(units, op=torch.distributed.ReduceOp.SUM)
+    max_ms = float(t.item())
+    job_pairs = float(units.item())
+    value = job_pairs * args.steps / (max_ms / 1e3)
+    launches_per_step = 3 * len(list(LEVELS))
+
+    # ---- roofline of the core kernel (traced pass, same conditions) -----
+    k_prof = min(args.steps, 20)
+    plan.profile(True)
+    timed(step, k_prof)
+    stage_ms, traced = plan.profile_read()
+    plan.profile(False)
+    core_ms = stage_ms["core"] / k_prof
+    flops_step = 2.0 * r * r * total_pairs
+    achieved = flops_step / (core_ms / 1e3) / 1e12
+    issued = {"split6": 6, "split3": 3, "bf16": 1}.get(args.precision, 0) * 2.0 * rp * rp * total_pairs
+    traffic = recorded_traffic()
+    roofline = {
+        "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+        "frac": achieved / bf16_peak, "traffic": traffic,
+        "kernel": "umma_kernel<A_GATHER,E_RED> (offset-grouped core)",
+        "algorithmic_flops_per_step": flops_step,
+        "flops_per_unit": f"2 r^2 = {2 * r * r} per box pair (r = {r})",
+        "launches_per_step": len(list(LEVELS)),
+        "core_ms_per_step": core_ms,
+        "stage_ms_per_step": {k: v / k_prof for k, v in stage_ms.items()},
+        "issued_tensor_tflops": issued / (core_ms / 1e3) / 1e12 if issued else None,
+        "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
+    }
+
+    # ---- end to end through the public API with pinned host buffers ---
+    hq = {l: q[l].cpu().pin_memory() for l in LEVELS}
+    hp = {l: torch.empty_like(hq[l]).pin_memory() for l in LEVELS}
+    dq = {l: torch.empty_like(q[l]) for l in LEVELS}
+
+    def e2e_step():
+        for l in LEVELS:
+            dq[l].copy_(hq[l], non_blocking=True)
+        for l in LEVELS:
+            plan.apply(dq[l], l, out=out[l])
+        for l in LEVELS:
+            hp[l].copy_(out[l], non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    k_e2e = min(args.steps, 50)
+    e2e_ms = timed(e2e_step, k_e2e)
+    h2d = sum(x.numel() * 4 for x in hq.values())
+    e2e_value = total_pairs * k_e2e / (e2e_ms / 1e3)
+    te = torch.tensor([e2e_value], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MIN)
+        te *= world
+    e2e = {"value": float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
+
+    # ---- adjoint and the plain FP32 dense M2L on the same GPU -----------
+    k_small = min(args.steps, 10)
+    step(plan.apply_adjoint)
+    adj_ms = timed(lambda: step(plan.apply_adjoint), k_small)
+    step(plan.apply_dense)
+    dense_ms = timed(lambda: step(plan.apply_dense), max(2, min(k_small, 5)))
+    dense_value = total_pairs * max(2, min(k_small, 5)) / (dense_ms / 1e3)
+    per_gpu_value = total_pairs * args.steps / (total_ms / 1e3)
+    plan.sync()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": workload_desc(total_pairs, r, rp, args.precision),
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "dense_fp32_baseline": {"value": dense_value, "unit": UNIT,
+                                "speedup_compressed_over_dense": per_gpu_value / dense_value},
+        "adjoint": {"value": total_pairs * k_small / (adj_ms / 1e3), "unit": UNIT},
+        "parity": "tests/test_gpu_m2l.py: split6 and fp32 within 1e-6 relative L2 of the FP64 oracle",
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cp, cs, cdesc = oracle_sample(wl, 20.0)
+        line["cpu_baseline"] = {"value": cp / cs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": cdesc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("split6", "split3", "bf16", "fp32"), default="split6")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -157,6 +157,21 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
  * is cleared), KIFMM_ERR_CUDA on an asynchronous CUDA error. */
 int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
 
+/* ---- tracing ------------------------------------------------------------ */
+
+/* Per-stage timing (enable != 0 turns it on, 0 off; off by default).  While
+ * on, every apply / apply_adjoint records CUDA events on the caller's
+ * stream around its compression, core and expansion kernels.  Recording
+ * costs a few microseconds per stage; leave it off for throughput runs. */
+int kifmm_m2l_profile_enable(kifmm_m2l_plan plan, int enable);
+
+/* Read and clear the stage times recorded since the last read: waits for
+ * the recorded events, writes ms[0..2] = summed milliseconds of the
+ * compression, core and expansion kernels, and *launches = the number of
+ * this library's kernel launches inside those intervals.  Either output
+ * may be NULL. */
+int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
+
 /* ---- host-side introspection (no GPU needed) ----------------------------- */
 
 /* Run the FP64 precompute of kifmm_m2l_precompute on the host only and copy

@@ -172,7 +172,7 @@ def m2l_dense_unit(box_ijk, level: int, r0: float, K: np.ndarray, q_up) -> np.nd
     out = np.zeros_like(q)
     for k in np.unique(ok):
         sel = ok == k
-        out[tg[sel]] += np.einsum("ij,brj->bri", K[k], q[sr[sel]])
+        out[tg[sel]] += q[sr[sel]] @ K[k].T
     out *= level_scale(level, r0)
     return out[:, 0, :] if squeeze else out
 
@@ -190,7 +190,7 @@ def m2l_svd(box_ijk, level: int, r0: float, f: SvdFactors, q_up, lists=None) -> 
     pt = np.zeros(q.shape[:2] + (f.r,))
     for k in np.unique(ok):
         sel = ok == k
-        pt[tg[sel]] += np.einsum("ab,nrb->nra", f.C[k], qt[sr[sel]])
+        pt[tg[sel]] += qt[sr[sel]] @ f.C[k].T          # K~_o q~ for every pair of offset o
     pt *= level_scale(level, r0)
     out = pt @ f.U.T
     return out[:, 0, :] if squeeze else out
@@ -204,7 +204,7 @@ def m2l_svd_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, pbar, lists=N
     qt = np.zeros(pb.shape[:2] + (f.r,))
     for k in np.unique(ok):
         sel = ok == k
-        qt[sr[sel]] += np.einsum("ab,nra->nrb", f.C[k], pt[tg[sel]])
+        qt[sr[sel]] += pt[tg[sel]] @ f.C[k]            # K~_o^T p~bar
     qt *= level_scale(level, r0)
     out = qt @ f.R.T
     return out[:, 0, :] if squeeze else out

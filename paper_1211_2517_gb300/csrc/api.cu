@@ -102,6 +102,32 @@ struct kifmm_m2l_plan_s {
     DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
     DevBuf<int> err_flag;
     std::map<std::pair<int, int>, std::unique_ptr<LevelState>> levels;
+    // tracing: (stage, start, stop) event triples recorded by applies
+    bool profile = false;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t traced_launches = 0;
+    cudaEvent_t get_event() {
+        if (!event_pool.empty()) {
+            cudaEvent_t e = event_pool.back();
+            event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ~kifmm_m2l_plan_s() {
+        for (auto& r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : event_pool) cudaEventDestroy(e);
+    }
     // scratch shared by all levels (apply calls on one plan are serialised)
     DevBuf<float> qt, pt;
     DevBuf<__nv_bfloat16> qb;
@@ -203,6 +229,29 @@ int chunk_for(int ndim) {
     return ((ndim + parts - 1) / parts + 15) / 16 * 16;
 }
 
+// Records a (start, stop) event pair around one stage when tracing is on.
+struct StageTimer {
+    kifmm_m2l_plan plan;
+    cudaStream_t s;
+    int stage;
+    int launches;
+    cudaEvent_t a = nullptr;
+    StageTimer(kifmm_m2l_plan p, cudaStream_t st, int stg, int nl) : plan(p), s(st), stage(stg), launches(nl) {
+        if (plan->profile) {
+            a = plan->get_event();
+            cudaEventRecord(a, s);
+        }
+    }
+    ~StageTimer() {
+        if (plan->profile && a) {
+            cudaEvent_t b = plan->get_event();
+            cudaEventRecord(b, s);
+            plan->recs.push_back({stage, a, b});
+            plan->traced_launches += launches;
+        }
+    }
+};
+
 // Shared body of apply / apply_adjoint: x_in -> y_out through
 //   xt = W_in x ; yt = sum_pairs core xt ; y = beta y + s_l W_out yt
 int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* x_in, float* y_out,
@@ -244,6 +293,7 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
     // 1. compression  q~ = R~^T q  (adjoint: U~^T pbar; R~ = U~, so one factor
     //    serves both directions), written as the core's operand; p~ = 0
     {
+        StageTimer timer(plan, s, 0, 1);
         UmmaArgs a{};
         a.Af = x_in;
         a.lda = n;
@@ -274,6 +324,7 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
     st = get_tiles(ps, nrhs, &tiles, &n_tiles);
     if (st != KIFMM_OK) return st;
     if (fp32_core) {
+        StageTimer timer(plan, s, 1, 1);
         KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp, tiles,
                                               n_tiles, ps.src.ptr, ps.dst.ptr, nrhs, 1.0f, s));
     } else {
@@ -299,11 +350,13 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
         a.n_products = plan->products;
         a.hilo = plan->core_hilo;
         a.error_flag = plan->err_flag.ptr;
+        StageTimer timer(plan, s, 1, 1);
         KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     }
 
     // 3. expansion  y = beta y + s_l U~ p~   (adjoint: R~ q~bar; R~ = U~)
     {
+        StageTimer timer(plan, s, 2, 1);
         UmmaArgs a{};
         a.Af = plan->pt.ptr;
         a.lda = rp;
@@ -554,6 +607,42 @@ int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream) {
         return KIFMM_ERR_TIMEOUT;
     }
     return KIFMM_OK;
+}
+
+int kifmm_m2l_profile_enable(kifmm_m2l_plan plan, int enable) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    plan->profile = enable != 0;
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    double acc[3] = {0, 0, 0};
+    int status = KIFMM_OK;
+    for (auto& r : plan->recs) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && status == KIFMM_OK) {
+            set_error(std::string("cudaEventElapsedTime: ") + cudaGetErrorString(e));
+            status = KIFMM_ERR_CUDA;
+        }
+        acc[r.stage] += t;
+        plan->event_pool.push_back(r.a);
+        plan->event_pool.push_back(r.b);
+    }
+    plan->recs.clear();
+    if (ms)
+        for (int i = 0; i < 3; ++i) ms[i] = acc[i];
+    if (launches) *launches = plan->traced_launches;
+    plan->traced_launches = 0;
+    return status;
 }
 
 int kifmm_m2l_level_pairs(kifmm_m2l_plan plan, int instance, int level, int64_t* n_pairs) {

@@ -152,6 +152,17 @@ class M2LPlan:
         """Uncompressed FP32 M2L (the baseline)."""
         return self._run("kifmm_m2l_apply_dense", q_up, level, instance, out, beta, stream)
 
+    def profile(self, enable: bool = True) -> None:
+        """Turn per-stage CUDA-event tracing on or off."""
+        call("kifmm_m2l_profile_enable", self._h, 1 if enable else 0)
+
+    def profile_read(self):
+        """Stage times since the last read: ({'compress','core','expand': ms}, launches)."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int64(0)
+        call("kifmm_m2l_profile_read", self._h, ms, ctypes.byref(n))
+        return {"compress": ms[0], "core": ms[1], "expand": ms[2]}, n.value
+
     def sync(self, stream=None) -> None:
         """Synchronise the stream and raise on device-side failures."""
         call("kifmm_m2l_sync", self._h, _stream_handle(stream))
