@@ -45,6 +45,7 @@
 #ifndef KIFMM_M2L_H
 #define KIFMM_M2L_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -156,6 +157,39 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
  * tensor-core kernel ran out (results of that apply are invalid; the flag
  * is cleared), KIFMM_ERR_CUDA on an asynchronous CUDA error. */
 int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
+
+/* ---- allocation-free apply ------------------------------------------------ */
+
+/* kifmm_m2l_apply without any device allocation.  The paper has no
+ * counterpart; this is an interface for callers of the library.
+ *
+ * kifmm_m2l_apply grows plan-owned scratch buffers with cudaMalloc the
+ * first time a level or an nrhs needs them.  Callers that must not
+ * allocate device memory once their run has started use this entry point
+ * instead: applications whose memory manager reserved the device up front,
+ * solvers held to a fixed memory budget, and latency-critical loops that
+ * cannot take the device-wide synchronisation of cudaMalloc / cudaFree.
+ * It computes what kifmm_m2l_apply computes (same layouts, beta rule,
+ * precision mode and kernels) and calls no allocating routine.  Its
+ * scratch is one static device array of KIFMM_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) that every GPU which loads this part of the library keeps until
+ * the process exits.
+ *  - The first call on a device looks up the array's device address
+ *    (once per device, with that device current); make that first call
+ *    before any stream capture.
+ *  - A level and nrhs whose scratch would not fit is rejected with
+ *    KIFMM_ERR_INVALID_ARG before anything is launched; the message gives
+ *    the bytes needed.  The need is about n_boxes * nrhs * r_pad bytes
+ *    times (2 * pieces + 4) (split modes; 8 for KIFMM_PREC_FP32), plus
+ *    16 bytes per 128 (pair, rhs) rows.
+ *  - Every call, from any plan, reuses the same array and overwrites it
+ *    (the call clears what must start at zero).  Calls whose device work
+ *    overlaps, e.g. on two streams at once, race and give wrong results:
+ *    serialise them.
+ * Same argument rules as kifmm_m2l_apply. */
+#define KIFMM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nrhs,
+                            const float* q_up, float* p_down, float beta, void* stream);
 
 /* ---- tracing ------------------------------------------------------------ */
 

@@ -27,111 +27,9 @@
 
 #include "kernels.h"
 #include "kifmm_internal.h"
+#include "plan.h"
 
 using namespace kifmm;
-
-namespace {
-
-constexpr int kTileRows = 128;
-
-#define KIFMM_CUDA_TRY(expr)                                                                        \
-    do {                                                                                            \
-        cudaError_t _e = (expr);                                                                    \
-        if (_e != cudaSuccess) {                                                                    \
-            set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                          \
-            return _e == cudaErrorMemoryAllocation ? KIFMM_ERR_OOM : KIFMM_ERR_CUDA;               \
-        }                                                                                           \
-    } while (0)
-
-template <class T>
-struct DevBuf {
-    T* ptr = nullptr;
-    size_t count = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { release(); }
-    void release() {
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        count = 0;
-    }
-    cudaError_t ensure(size_t n) {
-        if (n <= count && ptr) return cudaSuccess;
-        release();
-        if (n == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
-        if (e == cudaSuccess) count = n;
-        else ptr = nullptr;
-        return e;
-    }
-    cudaError_t upload(const T* h, size_t n) {
-        cudaError_t e = ensure(n);
-        if (e != cudaSuccess || n == 0) return e;
-        return cudaMemcpy(ptr, h, n * sizeof(T), cudaMemcpyHostToDevice);
-    }
-};
-
-struct PairSet {
-    DevBuf<int> src, dst;
-    std::vector<int64_t> off_begin;  // [317] prefix by offset
-    std::map<int, std::unique_ptr<DevBuf<Tile>>> tiles;  // per nrhs
-    std::map<int, int> n_tiles;
-};
-
-struct LevelState {
-    int level = 0, n_boxes = 0;
-    double r0 = 1.0;
-    int64_t n_pairs = 0;
-    PairSet fwd, adj;
-};
-
-}  // namespace
-
-struct kifmm_m2l_plan_s {
-    kifmm_m2l_params prm{};
-    int device = 0, num_sms = 0;
-    int n = 0, r = 0, rp = 0;
-    int pieces = 0;   // BF16 pieces of the tensor-core modes
-    int products = 0;
-    double sym_err = 0;
-    std::vector<double> sigma;
-    int n_pad = 0;    // n rounded up to 16 (K of the compression, N of the expansion)
-    int core_hilo = 0;
-    DevBuf<float> C, K;
-    DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
-    DevBuf<int> err_flag;
-    std::map<std::pair<int, int>, std::unique_ptr<LevelState>> levels;
-    // tracing: (stage, start, stop) event triples recorded by applies
-    bool profile = false;
-    struct Rec {
-        int stage;
-        cudaEvent_t a, b;
-    };
-    std::vector<Rec> recs;
-    std::vector<cudaEvent_t> event_pool;
-    int64_t traced_launches = 0;
-    cudaEvent_t get_event() {
-        if (!event_pool.empty()) {
-            cudaEvent_t e = event_pool.back();
-            event_pool.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        cudaEventCreate(&e);
-        return e;
-    }
-    ~kifmm_m2l_plan_s() {
-        for (auto& r : recs) {
-            cudaEventDestroy(r.a);
-            cudaEventDestroy(r.b);
-        }
-        for (auto e : event_pool) cudaEventDestroy(e);
-    }
-    // scratch shared by all levels (apply calls on one plan are serialised)
-    DevBuf<float> qt, pt;
-    DevBuf<__nv_bfloat16> qb;
-};
 
 namespace {
 
@@ -206,28 +104,8 @@ int get_tiles(PairSet& ps, int nrhs, const Tile** out, int* n_out) {
     return KIFMM_OK;
 }
 
-int check_device(kifmm_m2l_plan plan) {
-    int dev = -1;
-    KIFMM_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != plan->device) {
-        set_error("the current CUDA device differs from the plan's device");
-        return KIFMM_ERR_INVALID_ARG;
-    }
-    return KIFMM_OK;
-}
 
-LevelState* find_level(kifmm_m2l_plan plan, int instance, int level) {
-    auto it = plan->levels.find({instance, level});
-    return it == plan->levels.end() ? nullptr : it->second.get();
-}
 
-// N per work item of the compression / expansion GEMMs: <= 96, so that the
-// per-K-chunk partial sums of a row fit in registers and four accumulator
-// slots (two partials, two lo) fit in the 512 TMEM columns.
-int chunk_for(int ndim) {
-    const int parts = (ndim + 95) / 96;
-    return ((ndim + parts - 1) / parts + 15) / 16 * 16;
-}
 
 // Records a (start, stop) event pair around one stage when tracing is on.
 struct StageTimer {
@@ -381,6 +259,33 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
 }
 
 }  // namespace
+
+namespace kifmm {
+
+// N per work item of the compression / expansion GEMMs: <= 96, so that the
+// per-K-chunk partial sums of a row fit in registers and four accumulator
+// slots (two partials, two lo) fit in the 512 TMEM columns.
+int chunk_for(int ndim) {
+    const int parts = (ndim + 95) / 96;
+    return ((ndim + parts - 1) / parts + 15) / 16 * 16;
+}
+
+int check_device(kifmm_m2l_plan plan) {
+    int dev = -1;
+    KIFMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) {
+        set_error("the current CUDA device differs from the plan's device");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    return KIFMM_OK;
+}
+
+LevelState* find_level(kifmm_m2l_plan plan, int instance, int level) {
+    auto it = plan->levels.find({instance, level});
+    return it == plan->levels.end() ? nullptr : it->second.get();
+}
+
+}  // namespace kifmm
 
 extern "C" {
 
