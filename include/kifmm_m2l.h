@@ -144,6 +144,23 @@ int kifmm_m2l_apply(kifmm_m2l_plan plan, int instance, int level, int nrhs,
 int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                             const float* pbar_down, float* qbar_up, float beta, void* stream);
 
+/* Compressed M2L of the consecutive registered levels level_lo..level_hi
+ * of one instance as one batch (Step 3.1 over the downward pass's M2L
+ * levels): the same result as kifmm_m2l_apply on each level, in three
+ * kernel launches for all levels together (compression of every row, one
+ * core over the levels' pairs merged by offset, expansion of every row).
+ * q_up and p_down hold the levels' arrays back to back in level order:
+ * [n_boxes(level_lo)][nrhs][n], then level_lo + 1, ...  DEVICE float32.
+ * 0 <= level_lo <= level_hi < level_lo + 32; the merged pair list is built
+ * on the first call for (instance, level_lo, level_hi) and rebuilt after a
+ * kifmm_m2l_set_level of any of these levels. */
+int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                           const float* q_up, float* p_down, float beta, void* stream);
+
+/* Adjoint of kifmm_m2l_apply_levels (see kifmm_m2l_apply_adjoint). */
+int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                                   const float* pbar_down, float* qbar_up, float beta, void* stream);
+
 /* Uncompressed M2L (Eq. eq-m2l), the baseline the compression is compared
  * with:  p_down = beta * p_down + s_l sum_{s in I^t} K_{t-s} q^s  with the
  * FP32 unit-level K_o (formed on first use; 316 n^2 floats of device
@@ -181,7 +198,7 @@ int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
  *    KIFMM_ERR_INVALID_ARG before anything is launched; the message gives
  *    the bytes needed.  The need is about n_boxes * nrhs * r_pad bytes
  *    times (2 * pieces + 4) (split modes; 8 for KIFMM_PREC_FP32), plus
- *    16 bytes per 128 (pair, rhs) rows.
+ *    about 1 KB per 128 (pair, rhs) rows (tile and row tables).
  *  - Every call, from any plan, reuses the same array and overwrites it
  *    (the call clears what must start at zero).  Calls whose device work
  *    overlaps, e.g. on two streams at once, race and give wrong results:

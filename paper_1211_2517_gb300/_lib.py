@@ -29,7 +29,7 @@ N_OFFSETS = 316
 EXPORTED = (
     "kifmm_m2l_precompute", "kifmm_m2l_destroy", "kifmm_m2l_plan_rank", "kifmm_m2l_set_level",
     "kifmm_m2l_level_pairs", "kifmm_m2l_apply", "kifmm_m2l_apply_adjoint", "kifmm_m2l_apply_dense",
-    "kifmm_m2l_apply_noalloc",
+    "kifmm_m2l_apply_noalloc", "kifmm_m2l_apply_levels", "kifmm_m2l_apply_levels_adjoint",
     "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error",
     "kifmm_m2l_version",
 )
@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_apply_adjoint": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_dense": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_noalloc": [vp, i32, i32, i32, vp, vp, f32, vp],
+        "kifmm_m2l_apply_levels": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
+        "kifmm_m2l_apply_levels_adjoint": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_sync": [vp, vp],
         "kifmm_m2l_profile_enable": [vp, i32],
         "kifmm_m2l_profile_read": [vp, ctypes.POINTER(ctypes.c_double), pi64],

@@ -71,16 +71,17 @@ int build_pairset(const std::vector<int32_t>& tgt, const std::vector<int32_t>& s
     ps.off_begin.assign(kOffsets + 1, 0);
     for (int32_t k : off) ps.off_begin[k + 1]++;
     for (int k = 0; k < kOffsets; ++k) ps.off_begin[k + 1] += ps.off_begin[k];
-    ps.tiles.clear();
-    ps.n_tiles.clear();
+    ps.tilesets.clear();
     KIFMM_CUDA_TRY(ps.src.upload(src.data(), src.size()));
     KIFMM_CUDA_TRY(ps.dst.upload(tgt.data(), tgt.size()));
+    ps.h_src = src;
+    ps.h_dst = tgt;
     return KIFMM_OK;
 }
 
-int get_tiles(PairSet& ps, int nrhs, const Tile** out, int* n_out) {
-    auto it = ps.tiles.find(nrhs);
-    if (it == ps.tiles.end()) {
+int get_tiles(PairSet& ps, int nrhs, TileSet** out) {
+    auto it = ps.tilesets.find(nrhs);
+    if (it == ps.tilesets.end()) {
         std::vector<Tile> h;
         for (int k = 0; k < kOffsets; ++k) {
             const int64_t np = ps.off_begin[k + 1] - ps.off_begin[k];
@@ -94,18 +95,14 @@ int get_tiles(PairSet& ps, int nrhs, const Tile** out, int* n_out) {
                 h.push_back(t);
             }
         }
-        auto buf = std::make_unique<DevBuf<Tile>>();
-        KIFMM_CUDA_TRY(buf->upload(h.data(), h.size()));
-        ps.n_tiles[nrhs] = (int)h.size();
-        it = ps.tiles.emplace(nrhs, std::move(buf)).first;
+        auto ts = std::make_unique<TileSet>();
+        int st = make_tileset(h, ps.h_src, ps.h_dst, nrhs, *ts);
+        if (st != KIFMM_OK) return st;
+        it = ps.tilesets.emplace(nrhs, std::move(ts)).first;
     }
-    *out = it->second->ptr;
-    *n_out = ps.n_tiles[nrhs];
+    *out = it->second.get();
     return KIFMM_OK;
 }
-
-
-
 
 // Records a (start, stop) event pair around one stage when tracing is on.
 struct StageTimer {
@@ -197,14 +194,13 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
 
     // 2. core over offset-grouped pairs
     PairSet& ps = adjoint ? ls->adj : ls->fwd;
-    const Tile* tiles = nullptr;
-    int n_tiles = 0;
-    st = get_tiles(ps, nrhs, &tiles, &n_tiles);
+    TileSet* ts = nullptr;
+    st = get_tiles(ps, nrhs, &ts);
     if (st != KIFMM_OK) return st;
     if (fp32_core) {
         StageTimer timer(plan, s, 1, 1);
-        KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp, tiles,
-                                              n_tiles, ps.src.ptr, ps.dst.ptr, nrhs, 1.0f, s));
+        KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp,
+                                              ts->tiles.ptr, ts->n_tiles, ps.src.ptr, ps.dst.ptr, nrhs, 1.0f, s));
     } else {
         for (int pc = 0; pc < plan->pieces; ++pc)
             KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
@@ -216,13 +212,14 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
         a.B = plan->Cb.ptr;
         a.b_groups = kOffsets;
         a.ndim = rp;
-        a.n_chunk = (plan->core_hilo && plan->products > 1 && rp > 256) ? (rp / 2 + 15) / 16 * 16 : rp;
-        a.tiles = tiles;
-        a.n_tiles = n_tiles;
-        a.src = ps.src.ptr;
-        a.dst = ps.dst.ptr;
+        a.n_chunk = core_chunk(plan);
+        a.row_src = ts->row_src.ptr;
+        a.row_dst = ts->row_dst.ptr;
+        a.tile_k = ts->tile_k.ptr;
+        a.n_tiles = ts->n_tiles;
         a.nrhs = nrhs;
         a.zero_row = (int)rows;
+        a.level_scale[0] = 1.0f;  // the level scale is applied by the expansion
         a.D = plan->pt.ptr;
         a.ldd = rp;
         a.n_products = plan->products;
@@ -258,16 +255,219 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
     return KIFMM_OK;
 }
 
+
+// Merged pairs of levels lo..hi (forward or adjoint), built on first use.
+int get_multi(kifmm_m2l_plan plan, int instance, int lo, int hi, bool adjoint, MultiState** out) {
+    const auto key = std::make_tuple(instance, lo, hi, adjoint ? 1 : 0);
+    auto it = plan->multi.find(key);
+    if (it != plan->multi.end()) {
+        *out = it->second.get();
+        return KIFMM_OK;
+    }
+    auto ms = std::make_unique<MultiState>();
+    std::vector<int64_t> box_off(hi - lo + 1);
+    std::vector<PairSet*> sets(hi - lo + 1);
+    for (int l = lo; l <= hi; ++l) {
+        LevelState* ls = find_level(plan, instance, l);
+        box_off[l - lo] = ms->total_boxes;
+        ms->total_boxes += ls->n_boxes;
+        sets[l - lo] = adjoint ? &ls->adj : &ls->fwd;
+    }
+    std::vector<int32_t> src, dst;
+    for (int k = 0; k < kOffsets; ++k)
+        for (int li = 0; li <= hi - lo; ++li) {
+            PairSet& ps = *sets[li];
+            const int64_t b = ps.off_begin[k], e = ps.off_begin[k + 1];
+            if (e == b) continue;
+            ms->groups.push_back({k, li, (int64_t)src.size(), e - b});
+            for (int64_t i = b; i < e; ++i) {
+                src.push_back((int32_t)(ps.h_src[i] + box_off[li]));
+                dst.push_back((int32_t)(ps.h_dst[i] + box_off[li]));
+            }
+        }
+    KIFMM_CUDA_TRY(ms->src.upload(src.data(), src.size()));
+    KIFMM_CUDA_TRY(ms->dst.upload(dst.data(), dst.size()));
+    ms->h_src.swap(src);
+    ms->h_dst.swap(dst);
+    *out = ms.get();
+    plan->multi[key] = std::move(ms);
+    return KIFMM_OK;
+}
+
+int get_multi_tiles(MultiState& ms, int nrhs, TileSet** out) {
+    auto it = ms.tilesets.find(nrhs);
+    if (it == ms.tilesets.end()) {
+        std::vector<Tile> h;
+        for (const auto& g : ms.groups) {
+            const int64_t rows = g.count * nrhs;
+            for (int64_t r0 = 0; r0 < rows; r0 += kTileRows)
+                h.push_back({g.k | (g.level_idx << 16), (int)g.begin, (int)r0,
+                             (int)std::min<int64_t>(kTileRows, rows - r0)});
+        }
+        auto ts = std::make_unique<TileSet>();
+        int st = make_tileset(h, ms.h_src, ms.h_dst, nrhs, *ts);
+        if (st != KIFMM_OK) return st;
+        it = ms.tilesets.emplace(nrhs, std::move(ts)).first;
+    }
+    *out = it->second.get();
+    return KIFMM_OK;
+}
+
+// Levels lo..hi of one instance in three launches: compression of all their
+// rows, one core over the merged offset-ordered tiles (each tile scaled by
+// its level's s_l), expansion of all rows.
+int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, const float* x_in, float* y_out,
+                 float beta, void* stream, bool adjoint) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (lo < 0 || hi < lo || hi - lo >= 32) {
+        set_error("need 0 <= level_lo <= level_hi < level_lo + 32");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    for (int l = lo; l <= hi; ++l)
+        if (!find_level(plan, instance, l)) {
+            set_error("level " + std::to_string(l) + " not registered: call kifmm_m2l_set_level first");
+            return KIFMM_ERR_STATE;
+        }
+    if (nrhs < 1) {
+        set_error("nrhs must be >= 1");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(x_in) & 15) || (reinterpret_cast<uintptr_t>(y_out) & 15)) {
+        set_error("density pointers must be 16-byte aligned");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    MultiState* ms = nullptr;
+    st = get_multi(plan, instance, lo, hi, adjoint, &ms);
+    if (st != KIFMM_OK) return st;
+    if (ms->total_boxes == 0) return KIFMM_OK;
+    if (!x_in || !y_out) {
+        set_error("NULL density pointer");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = plan->n, rp = plan->rp;
+    const long rows = (long)ms->total_boxes * nrhs;
+    if (rows + 1 > (long)INT32_MAX / 2) {
+        set_error("too many box rows");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    const bool fp32_core = plan->prm.precision == KIFMM_PREC_FP32;
+    const long piece_stride = (rows + 1) * rp;
+    KIFMM_CUDA_TRY(plan->pt.ensure((size_t)rows * rp));
+    if (fp32_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
+    else KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
+    TileSet* ts = nullptr;
+    st = get_multi_tiles(*ms, nrhs, &ts);
+    if (st != KIFMM_OK) return st;
+    {
+        StageTimer timer(plan, s, 0, 1);
+        UmmaArgs a{};
+        a.Af = x_in;
+        a.lda = n;
+        a.k_valid = n;
+        a.m_rows = (int)rows;
+        a.kdim = plan->n_pad;
+        a.B = plan->Rtb.ptr;
+        a.b_groups = 1;
+        a.ndim = rp;
+        a.n_chunk = chunk_for(rp);
+        a.ldd = rp;
+        a.alpha = 1.0f;
+        a.Dp = fp32_core ? nullptr : plan->qb.ptr;
+        a.dp_piece_stride = piece_stride;
+        a.dp_pieces = fp32_core ? 0 : plan->pieces;
+        a.Df = fp32_core ? plan->qt.ptr : nullptr;
+        a.Z = plan->pt.ptr;
+        a.n_products = 6;
+        a.hilo = 1;
+        a.error_flag = plan->err_flag.ptr;
+        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_SPLIT, a, plan->num_sms, s));
+    }
+    ScaleTable scales{};
+    for (int l = lo; l <= hi; ++l) {
+        const LevelState* ls = find_level(plan, instance, l);
+        scales.s[l - lo] = (float)std::ldexp(1.0 / ls->r0, l);
+    }
+    if (fp32_core) {
+        StageTimer timer(plan, s, 1, 1);
+        KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp, ts->tiles.ptr,
+                                              ts->n_tiles, ms->src.ptr, ms->dst.ptr, nrhs, scales, s));
+    } else {
+        for (int pc = 0; pc < plan->pieces; ++pc)
+            KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
+                                           rp * sizeof(__nv_bfloat16), s));
+        UmmaArgs a{};
+        a.A = plan->qb.ptr;
+        a.a_piece_stride = piece_stride;
+        a.kdim = rp;
+        a.B = plan->Cb.ptr;
+        a.b_groups = kOffsets;
+        a.ndim = rp;
+        a.n_chunk = core_chunk(plan);
+        a.row_src = ts->row_src.ptr;
+        a.row_dst = ts->row_dst.ptr;
+        a.tile_k = ts->tile_k.ptr;
+        a.n_tiles = ts->n_tiles;
+        a.nrhs = nrhs;
+        a.zero_row = (int)rows;
+        for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i];
+        a.D = plan->pt.ptr;
+        a.ldd = rp;
+        a.n_products = plan->products;
+        a.hilo = plan->core_hilo;
+        a.error_flag = plan->err_flag.ptr;
+        StageTimer timer(plan, s, 1, 1);
+        KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+    }
+    {
+        StageTimer timer(plan, s, 2, 1);
+        UmmaArgs a{};
+        a.Af = plan->pt.ptr;
+        a.lda = rp;
+        a.k_valid = rp;
+        a.m_rows = (int)rows;
+        a.kdim = rp;
+        a.B = plan->Ub.ptr;
+        a.b_groups = 1;
+        a.ndim = plan->n_pad;
+        a.n_chunk = chunk_for(plan->n_pad);
+        a.D = y_out;
+        a.ldd = n;
+        a.alpha = 1.0f;
+        a.beta = beta;
+        a.n_valid = n;
+        a.n_products = 6;
+        a.hilo = 1;
+        a.error_flag = plan->err_flag.ptr;
+        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_STORE, a, plan->num_sms, s));
+    }
+    return KIFMM_OK;
+}
+
 }  // namespace
 
 namespace kifmm {
 
-// N per work item of the compression / expansion GEMMs: <= 96, so that the
-// per-K-chunk partial sums of a row fit in registers and four accumulator
-// slots (two partials, two lo) fit in the 512 TMEM columns.
+// N per work item of the compression / expansion GEMMs: <= 64, so that the
+// partial sums of a row fit in registers next to a loaded TMEM chunk, and
+// four accumulator slots (two partials, two lo) fit in the TMEM columns.
 int chunk_for(int ndim) {
-    const int parts = (ndim + 95) / 96;
+    const int parts = (ndim + 63) / 64;
     return ((ndim + parts - 1) / parts + 15) / 16 * 16;
+}
+
+int core_chunk(kifmm_m2l_plan plan) {
+    const int rp = plan->rp;
+    // hi and lo side by side must fit the 512 TMEM columns (one slot); a
+    // split of N would gather every A row once per part, which costs more
+    // than the lost overlap of epilogue and MMA
+    if (plan->core_hilo && plan->products > 1 && 2 * rp > 512) return (rp / 2 + 15) / 16 * 16;
+    return rp;
 }
 
 int check_device(kifmm_m2l_plan plan) {
@@ -277,6 +477,29 @@ int check_device(kifmm_m2l_plan plan) {
         set_error("the current CUDA device differs from the plan's device");
         return KIFMM_ERR_INVALID_ARG;
     }
+    return KIFMM_OK;
+}
+
+int make_tileset(const std::vector<Tile>& tiles, const std::vector<int32_t>& src, const std::vector<int32_t>& dst,
+                 int nrhs, TileSet& out) {
+    const size_t nt = tiles.size();
+    std::vector<int> rs(nt * kTileRows, -1), rd(nt * kTileRows, -1), tk(nt);
+    for (size_t t = 0; t < nt; ++t) {
+        const Tile& tl = tiles[t];
+        tk[t] = tl.k;
+        for (int r = 0; r < tl.nrows; ++r) {
+            const int64_t g = (int64_t)tl.row0 + r;
+            const int64_t pr = tl.pair_begin + g / nrhs;
+            const int64_t rhs = g % nrhs;
+            rs[t * kTileRows + r] = (int)(src[pr] * (int64_t)nrhs + rhs);
+            rd[t * kTileRows + r] = (int)(dst[pr] * (int64_t)nrhs + rhs);
+        }
+    }
+    KIFMM_CUDA_TRY(out.tiles.upload(tiles.data(), nt));
+    KIFMM_CUDA_TRY(out.row_src.upload(rs.data(), rs.size()));
+    KIFMM_CUDA_TRY(out.row_dst.upload(rd.data(), rd.size()));
+    KIFMM_CUDA_TRY(out.tile_k.upload(tk.data(), tk.size()));
+    out.n_tiles = (int)nt;
     return KIFMM_OK;
 }
 
@@ -491,6 +714,13 @@ int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double roo
         st = build_pairset(atg, asr, aof, ls->adj);
         if (st != KIFMM_OK) return st;
         plan->levels[{instance, level}] = std::move(ls);
+        for (auto it = plan->multi.begin(); it != plan->multi.end();) {
+            const auto& key = it->first;
+            if (std::get<0>(key) == instance && std::get<1>(key) <= level && level <= std::get<2>(key))
+                it = plan->multi.erase(it);
+            else
+                ++it;
+        }
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed");
         return KIFMM_ERR_OOM;
@@ -574,6 +804,16 @@ int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nr
     return apply_compressed(plan, instance, level, nrhs, pbar_down, qbar_up, beta, stream, true);
 }
 
+int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                           const float* q_up, float* p_down, float beta, void* stream) {
+    return apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, beta, stream, false);
+}
+
+int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                                   const float* pbar_down, float* qbar_up, float beta, void* stream) {
+    return apply_levels(plan, instance, level_lo, level_hi, nrhs, pbar_down, qbar_up, beta, stream, true);
+}
+
 int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* q_up, float* p_down,
                           float beta, void* stream) {
     if (!plan) {
@@ -618,12 +858,11 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
     } else if (beta != 1.f) {
         KIFMM_CUDA_TRY(launch_scale(p_down, rows * n, beta, s));
     }
-    const Tile* tiles = nullptr;
-    int n_tiles = 0;
-    st = get_tiles(ls->fwd, nrhs, &tiles, &n_tiles);
+    TileSet* ts = nullptr;
+    st = get_tiles(ls->fwd, nrhs, &ts);
     if (st != KIFMM_OK) return st;
-    KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(q_up, n, plan->K.ptr, n, n, p_down, n, tiles, n_tiles, ls->fwd.src.ptr,
-                                          ls->fwd.dst.ptr, nrhs, scale, s));
+    KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(q_up, n, plan->K.ptr, n, n, p_down, n, ts->tiles.ptr, ts->n_tiles,
+                                          ls->fwd.src.ptr, ls->fwd.dst.ptr, nrhs, scale, s));
     return KIFMM_OK;
 }
 

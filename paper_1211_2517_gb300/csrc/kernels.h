@@ -8,7 +8,8 @@
 namespace kifmm {
 
 // One tile of an offset-grouped batch: rows [row0, row0 + nrows) of offset
-// k's virtual row list.  Virtual row v maps to pair = pair_begin + v / nrhs,
+// (k & 0xFFFF)'s virtual row list; k >> 16 selects a level scale of the
+// tensor-core core (0 for single-level batches).  Virtual row v maps to pair = pair_begin + v / nrhs,
 // rhs = v % nrhs; the source row is src[pair] * nrhs + rhs and the output
 // row dst[pair] * nrhs + rhs.
 struct Tile {
@@ -18,8 +19,17 @@ struct Tile {
     int nrows;
 };
 
+// Factor applied to a tile's output, selected by tile.k >> 16.
+struct ScaleTable {
+    float s[32];
+};
+
 // Offset-grouped gather-GEMM-scatter, FP32 CUDA cores:
-// for every tile, D[dst row] += alpha * A[src row] W_k^T with W_k = W + k * N * K.
+// for every tile, D[dst row] += alpha * A[src row] W_k^T with W_k = W + k * N * K
+// (k = tile.k & 0xFFFF; alpha = scales.s[tile.k >> 16], or the scalar).
+cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int N, int K, float* D, int ldd,
+                                   const Tile* tiles, int n_tiles, const int* src, const int* dst, int nrhs,
+                                   const ScaleTable& scales, cudaStream_t stream);
 cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int N, int K, float* D, int ldd,
                                    const Tile* tiles, int n_tiles, const int* src, const int* dst, int nrhs,
                                    float alpha, cudaStream_t stream);
@@ -58,13 +68,16 @@ struct UmmaArgs {
     int b_groups;             // 316 offsets (core) or 1
     int ndim;                 // N rows per group (multiple of 16)
     int n_chunk;              // N per work item (multiple of 16)
-    // work list (A_GATHER)
-    const Tile* tiles;
+    // work list (A_GATHER): per tile t, 128 A rows row_src[128 t + i] and
+    // output rows row_dst[128 t + i] (-1: none), and tile_k[t] = offset |
+    // (level index << 16)
+    const int* row_src;
+    const int* row_dst;
+    const int* tile_k;
     int n_tiles;
-    const int* src;
-    const int* dst;
     int nrhs;
     int zero_row;             // row of the A pieces that is all zero
+    float level_scale[32];    // E_RED: factor applied to a tile's output, by tile.k >> 16
     // epilogue
     float* D;                 // E_RED / E_STORE: FP32 [*][ldd]
     int ldd;

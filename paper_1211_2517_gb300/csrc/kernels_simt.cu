@@ -110,14 +110,15 @@ __global__ void __launch_bounds__(NT) pairs_gemm_kernel(const float* __restrict_
                                                         const float* __restrict__ W, int N, int K,
                                                         float* __restrict__ D, int ldd, const Tile* __restrict__ tiles,
                                                         const int* __restrict__ src, const int* __restrict__ dst,
-                                                        int nrhs, float alpha) {
+                                                        int nrhs, const ScaleTable scales) {
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Ws[2][BK][BN];
     const Tile t = tiles[blockIdx.x];
     const int n0 = blockIdx.y * BN;
     RowMapPairs map{src, dst, nrhs, t.pair_begin, t.row0, t.nrows};
     float acc[8][8];
-    tile_product(A, lda, W + (long)t.k * N * K, N, K, n0, map, acc, As, Ws);
+    tile_product(A, lda, W + (long)(t.k & 0xFFFF) * N * K, N, K, n0, map, acc, As, Ws);
+    const float alpha = scales.s[(t.k >> 16) & 31];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -167,11 +168,19 @@ cudaError_t launch_scale(float* x, long count, float beta, cudaStream_t stream) 
 
 cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int N, int K, float* D, int ldd,
                                    const Tile* tiles, int n_tiles, const int* src, const int* dst, int nrhs,
-                                   float alpha, cudaStream_t stream) {
+                                   const ScaleTable& scales, cudaStream_t stream) {
     if (n_tiles <= 0 || N <= 0) return cudaSuccess;
     dim3 grid(n_tiles, (N + BN - 1) / BN);
-    pairs_gemm_kernel<<<grid, NT, 0, stream>>>(A, lda, W, N, K, D, ldd, tiles, src, dst, nrhs, alpha);
+    pairs_gemm_kernel<<<grid, NT, 0, stream>>>(A, lda, W, N, K, D, ldd, tiles, src, dst, nrhs, scales);
     return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int N, int K, float* D, int ldd,
+                                   const Tile* tiles, int n_tiles, const int* src, const int* dst, int nrhs,
+                                   float alpha, cudaStream_t stream) {
+    ScaleTable sc{};
+    sc.s[0] = alpha;
+    return launch_pairs_gemm_fp32(A, lda, W, N, K, D, ldd, tiles, n_tiles, src, dst, nrhs, sc, stream);
 }
 
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* out, long piece_stride,

@@ -22,8 +22,9 @@
 //   warps 0-3  epilogue: TMEM -> registers -> per-warp shared-memory
 //              transpose -> coalesced 16-byte global reductions / stores
 //   warps 4-7  producers: A tiles into 64B-swizzled shared memory (cp.async
-//              gather of BF16 rows, or FP32 loads split in registers);
-//              one thread also TMA-loads the B tiles
+//              gather of BF16 rows, each stage owned by one warp; or FP32
+//              loads split in registers); a producer thread also TMA-loads
+//              the B tiles
 //   warp 8     TMEM allocation and the single MMA-issuing thread
 // Stages cycle through full/empty mbarriers; two TMEM accumulator slots
 // (when they fit in 512 columns) overlap the epilogue of one work item
@@ -37,6 +38,8 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "kernels.h"
 #include "kifmm_m2l.h"
@@ -122,6 +125,18 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// wait until at most n (1..7) groups are pending
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+    switch (n) {
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+    }
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
@@ -202,14 +217,16 @@ __device__ __forceinline__ uint32_t swz64(int m, int c) {
 
 struct Layout {
     int stages, na, nc, c_rows_alloc, n_acc, acc_cols, n_items, n_chunks, kc_count;
+    int prod_warps;  // A_GATHER: producer warps in use; divides `stages`
     uint32_t a_bytes, c_bytes, stage_bytes, trans_off;
 };
 
 // Product table (a piece, b piece), smallest terms first; (0,0) last.
 __constant__ int8_t kProd[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
 
-constexpr int kTransStride = 33;  // floats per row of the epilogue transpose buffer
-constexpr int kMaxRowsChunk = 96; // N per work item of the rows modes (partial sums live in registers)
+constexpr int kTransStride = 36;  // floats per row of the epilogue transpose buffer (16-byte rows, no bank conflicts)
+constexpr int kMaxRowsChunk = 64; // N per work item of the rows modes (partial sums live in registers)
+constexpr int kPartChunks = 2;    // rows modes: K-chunks per drained partial of the (0,0) product
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -243,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&sm->full[s], kProdWarps * 32 + 1);
+            mbar_init(&sm->full[s], (AMODE == A_GATHER ? 32 : kProdWarps * 32) + 1);
             mbar_init(&sm->empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -282,12 +299,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
         // ================= producers =================
         const int v = threadIdx.x - kEpiWarps * 32;  // 0..127
-        const bool tma_thread = (v == 0);
+        const bool tma_thread = AMODE == A_GATHER ? (lane == 0) : (v == 0);
         int it = 0;
         bool ok = true;
+        int group = 0;  // B group (offset) of the current item, A_GATHER only
         auto issue_b = [&](int s, int item, int kc) {
-            int group = 0;
-            if (AMODE == A_GATHER) group = args.tiles[item_tile(item)].k;
             mbar_arrive_expect_tx(&sm->full[s], (uint32_t)L.nc * L.c_rows_alloc * kRowBytes);
             for (int pc = 0; pc < L.nc; ++pc) {
                 const int row_base = (pc * args.b_groups + group) * args.ndim + item_n0(item);
@@ -296,23 +312,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         if (AMODE == A_GATHER) {
-            // thread v copies 16-byte chunk (v % 4) of rows v/4 + 32 i, i = 0..3:
-            // one warp instruction covers 8 rows x 64 contiguous bytes
-            const int cch = v % 4;
+            // Stage it belongs to producer warp it % P (P = L.prod_warps divides
+            // the number of slots S, so every slot has exactly one producer
+            // warp: its barriers see one waiter and one arriver, in order).
+            // That warp gathers all 128 rows of the stage (lane l copies
+            // 16-byte chunk l % 4 of rows l / 4 + 8 i: one instruction covers
+            // 8 rows x 64 contiguous bytes), waits for its own copies only and
+            // arrives; P warps keep P stages in flight independently.
+            const int P = L.prod_warps;
+            const int pw = warp - kEpiWarps, cch = lane % 4, rl = lane / 4;
+            int srow[16];
             for (int item = blockIdx.x; item < L.n_items && ok; item += gridDim.x) {
-                const Tile t = args.tiles[item_tile(item)];
-                long srow[4];
+                const int t = item_tile(item);
+                // does this warp own any stage of this item?
+                const int first_own = (pw - it % P + P) % P;
+                if (pw < P && first_own < KC) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = v / 4 + 32 * i;
-                    srow[i] = args.zero_row;
-                    if (r < t.nrows) {
-                        const int g = t.row0 + r;
-                        const int pr = t.pair_begin + g / args.nrhs;
-                        srow[i] = (long)args.src[pr] * args.nrhs + (g % args.nrhs);
+                    for (int i = 0; i < 16; ++i) {
+                        const int x = __ldg(args.row_src + (long)t * kTileM + rl + 8 * i);
+                        srow[i] = x < 0 ? args.zero_row : x;
                     }
+                    group = __ldg(args.tile_k + t) & 0xFFFF;
                 }
                 for (int kc = 0; kc < KC; ++kc, ++it) {
+                    if (it % P != pw) continue;
                     const int s = it % S;
                     const uint32_t ph = (uint32_t)(it / S) & 1u;
                     if (!mbar_wait(&sm->empty[s], ph ^ 1u, sm, args.error_flag)) {
@@ -326,21 +349,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const __nv_bfloat16* base = args.A + pc * args.a_piece_stride + colc;
                         const uint32_t sbase = a_smem(s, pc);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            cp_async16(sbase + swz64(v / 4 + 32 * i, cch), base + srow[i] * args.kdim, bytes);
+                        for (int i = 0; i < 16; ++i)
+                            cp_async16(sbase + swz64(rl + 8 * i, cch), base + (long)srow[i] * args.kdim, bytes);
                     }
                     cp_async_commit();
-                    if (tma_thread) issue_b(s, item, kc);
-                    if (it > 0) {
-                        cp_async_wait_1();
-                        fence_proxy_async();
-                        mbar_arrive(&sm->full[(it - 1) % S]);
-                    }
+                    if (lane == 0) issue_b(s, item, kc);
+                    cp_async_wait_0();
+                    fence_proxy_async();
+                    mbar_arrive(&sm->full[s]);
                 }
             }
             cp_async_wait_0();
-            fence_proxy_async();
-            if (it > 0 && ok) mbar_arrive(&sm->full[(it - 1) % S]);
         } else {
             // FP32 rows: thread v loads float4 f = v + 128 i (i = 0..7) of the
             // 128 x 32 tile, row f / 8, columns 4 (f % 8) .. +3 (a warp reads
@@ -405,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ================= MMA issuer =================
         // Core (A_GATHER): one accumulator slot per work item (hi and, with
         // hilo, lo side by side), double-buffered when two fit.
-        // Rows modes: the (0,0) product of every K-chunk goes to one of two
-        // ping-pong partial slots that the epilogue drains into FP32
-        // registers (so no accumulator chain is longer than one K-chunk);
+        // Rows modes: the (0,0) product of every kPartChunks K-chunks goes to
+        // one of two ping-pong partial slots that the epilogue drains into
+        // FP32 registers (no accumulator chain is longer than 4 MMA steps);
         // the small products accumulate over the item in a lo slot.
         if (lane == 0) {
             int it = 0, tcount = 0, pcount = 0;
@@ -434,11 +453,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     d_lo = args.hilo ? d_hi + (uint32_t)args.n_chunk : d_hi;
                 }
                 bool first_hi = true, first_lo = true;
+                int ps = 0;
                 for (int kc = 0; kc < KC; ++kc, ++it) {
                     const int s = it % S;
                     const uint32_t ph = (uint32_t)(it / S) & 1u;
-                    int ps = 0;
-                    if (AMODE == A_ROWS) {
+                    if (AMODE == A_ROWS && kc % kPartChunks == 0) {
                         ps = pcount % 2;
                         const uint32_t pph = (uint32_t)(pcount / 2) & 1u;
                         if (!mbar_wait(&sm->part_empty[ps], pph ^ 1u, sm, args.error_flag)) {
@@ -471,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     umma_commit(&sm->empty[s]);
-                    if (AMODE == A_ROWS) {
+                    if (AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) {
                         umma_commit(&sm->part_full[ps]);
                         ++pcount;
                     }
@@ -491,19 +510,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         const bool has_lo = args.hilo && args.n_products > 1;
         int tcount = 0, pcount = 0;
+        int e_nxt_row = -1, e_nxt_k = 0;
+        if (AMODE == A_GATHER && blockIdx.x < L.n_items) {
+            const int t0 = item_tile(blockIdx.x);
+            e_nxt_row = __ldg(args.row_dst + (long)t0 * kTileM + warp * 32 + lane);
+            e_nxt_k = __ldg(args.tile_k + t0);
+        }
         for (int item = blockIdx.x; item < L.n_items; item += gridDim.x, ++tcount) {
             const int acc = tcount % L.n_acc;
             const uint32_t aph = (uint32_t)(tcount / L.n_acc) & 1u;
             const int n0 = item_n0(item), nthis = item_nthis(item);
             // this lane's output row (tile row warp*32 + lane); -1 = none
             long orow = -1;
+            float oscale = 1.0f;
             if (AMODE == A_GATHER) {
-                const Tile t = args.tiles[item_tile(item)];
-                const int r = warp * 32 + lane;
-                if (r < t.nrows) {
-                    const int g = t.row0 + r;
-                    const int pr = t.pair_begin + g / args.nrhs;
-                    orow = (long)args.dst[pr] * args.nrhs + (g % args.nrhs);
+                orow = e_nxt_row;
+                oscale = args.level_scale[(e_nxt_k >> 16) & 31];
+                if (item + (int)gridDim.x < L.n_items) {  // prefetch the next item's rows
+                    const int tn = item_tile(item + gridDim.x);
+                    e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + warp * 32 + lane);
+                    e_nxt_k = __ldg(args.tile_k + tn);
                 }
             } else {
                 const long r = (long)item_tile(item) * kTileM + warp * 32 + lane;
@@ -518,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < kMaxRowsChunk; ++j) sums[j] = 0.f;
                 bool got_all = true;
-                for (int kc = 0; kc < KC; ++kc) {
+                for (int kc = 0; kc < KC; kc += kPartChunks) {
                     const int ps = pcount % 2;
                     const uint32_t pph = (uint32_t)(pcount / 2) & 1u;
                     const bool gp = mbar_wait(&sm->part_full[ps], pph, sm, args.error_flag);
@@ -552,16 +578,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
             const uint32_t col_lo_rows = (uint32_t)((2 + acc) * args.n_chunk);
+            // output rows of the 8 transpose passes of this lane (pass p
+            // serves tile row 4 p + lane / 8)
+            long prow[8];
+#pragma unroll
+            for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
+            const int c4 = lane % 8;
             for (int c = 0; c < nthis; c += 32) {
-                uint32_t r[32];
+                uint32_t r[32], r2[32];
                 const bool full32 = c + 32 <= nthis;
                 float val[32];
+                // issue the TMEM loads of this chunk together, then wait once
+                const uint32_t a0 = tmem + lane_base + (AMODE == A_ROWS ? col_lo_rows : col_hi) + (uint32_t)c;
+                if (full32) tmem_ld32(a0, r);
+                else tmem_ld16(a0, r);
+                if (AMODE != A_ROWS && has_lo) {
+                    if (full32) tmem_ld32(tmem + lane_base + col_lo + (uint32_t)c, r2);
+                    else tmem_ld16(tmem + lane_base + col_lo + (uint32_t)c, r2);
+                }
+                tmem_wait_ld();
                 if (AMODE == A_ROWS) {
-                    if (full32)
-                        tmem_ld32(tmem + lane_base + col_lo_rows + (uint32_t)c, r);
-                    else
-                        tmem_ld16(tmem + lane_base + col_lo_rows + (uint32_t)c, r);
-                    tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         // sums[] is indexed by a loop-invariant offset c (0, 32, 64)
@@ -572,40 +608,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                         val[j] = sv + __uint_as_float(r[j]);
                     }
                 } else {
-                    if (full32)
-                        tmem_ld32(tmem + lane_base + col_hi + (uint32_t)c, r);
-                    else
-                        tmem_ld16(tmem + lane_base + col_hi + (uint32_t)c, r);
-                    tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) val[j] = __uint_as_float(r[j]);
                     if (has_lo) {
-                        if (full32)
-                            tmem_ld32(tmem + lane_base + col_lo + (uint32_t)c, r);
-                        else
-                            tmem_ld16(tmem + lane_base + col_lo + (uint32_t)c, r);
-                        tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) val[j] += __uint_as_float(r[j]);
+                        for (int j = 0; j < 32; ++j) val[j] += __uint_as_float(r2[j]);
                     }
                 }
-                // transpose through shared memory: lane -> row, then 8 lanes per row
+                // transpose through shared memory: lane -> row (16-byte stores),
+                // then 8 lanes per row (16-byte loads)
 #pragma unroll
-                for (int j = 0; j < 32; ++j) trans[lane * kTransStride + j] = val[j];
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * q) =
+                        make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
                 __syncwarp();
                 const int ncols = full32 ? 32 : 16;
-                const int c4 = lane % 8;
 #pragma unroll
                 for (int pass = 0; pass < 8; ++pass) {
                     const int rr = pass * 4 + lane / 8;
-                    const long grow = __shfl_sync(0xffffffffu, orow, rr);
+                    const long grow = prow[pass];
                     if (grow < 0 || 4 * c4 >= ncols) continue;
-                    const float* tp = trans + rr * kTransStride + 4 * c4;
-                    float4 x = make_float4(tp[0], tp[1], tp[2], tp[3]);
+                    float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
                     const int col = n0 + c + 4 * c4;
                     if (EMODE == E_RED) {
-                        red_add_v4(args.D + grow * args.ldd + col, __float_as_uint(x.x), __float_as_uint(x.y),
-                                   __float_as_uint(x.z), __float_as_uint(x.w));
+                        // one tile = one level: every lane holds the same scale
+                        red_add_v4(args.D + grow * args.ldd + col, __float_as_uint(oscale * x.x),
+                                   __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
+                                   __float_as_uint(oscale * x.w));
                     } else if (EMODE == E_STORE) {
                         if (col < args.n_valid) {
                             float4* dp = reinterpret_cast<float4*>(args.D + grow * args.ldd + col);
@@ -674,11 +703,37 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
+// Host-side state cached across launches (the per-call host work is a
+// visible share of a small level's apply): the largest dynamic shared memory
+// already granted to each kernel instantiation on each device, each device's
+// opt-in limit, and encoded tensor maps of the B operands.
+std::mutex g_cache_mutex;
+int g_smem_granted[3][64] = {};
+int g_max_smem[64] = {};
+struct MapKey {
+    const void* ptr;
+    int rows, kdim;
+    bool operator<(const MapKey& o) const {
+        if (ptr != o.ptr) return ptr < o.ptr;
+        if (rows != o.rows) return rows < o.rows;
+        return kdim < o.kdim;
+    }
+};
+std::map<MapKey, CUtensorMap> g_maps;
+
 template <int AM, int EM>
 cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L, size_t smem, int grid,
-                     cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(umma_kernel<AM, EM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+                     cudaStream_t stream, int dev) {
+    const int inst = AM == A_GATHER ? 0 : (EM == E_STORE ? 1 : 2);
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        if (g_smem_granted[inst][dev] < (int)smem) {
+            cudaError_t e =
+                cudaFuncSetAttribute(umma_kernel<AM, EM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            g_smem_granted[inst][dev] = (int)smem;
+        }
+    }
     umma_kernel<AM, EM><<<grid, kThreads, smem, stream>>>(bmap, a, L);
     return cudaGetLastError();
 }
@@ -723,32 +778,55 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (L.n_items <= 0) return cudaSuccess;
 
     int dev = 0, max_smem = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return ce;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        if (!g_max_smem[dev]) {
+            ce = cudaDeviceGetAttribute(&g_max_smem[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (ce != cudaSuccess) return ce;
+        }
+        max_smem = g_max_smem[dev];
+    }
     const uint32_t trans_bytes = kEpiWarps * 32 * kTransStride * 4;
     const int avail = max_smem - 2048 - (int)trans_bytes;
     L.stages = avail / (int)L.stage_bytes;
     if (L.stages > 8) L.stages = 8;
     if (L.stages < 2) return cudaErrorInvalidConfiguration;
+    // gather mode: each slot is owned by one producer warp
+    L.prod_warps = L.stages >= kProdWarps ? kProdWarps : L.stages;
+    if (gather) L.stages = L.stages / L.prod_warps * L.prod_warps;
     L.trans_off = 1024 + (uint32_t)L.stages * L.stage_bytes;
     const size_t smem = 1024 + (size_t)L.trans_off + trans_bytes;
 
     // B pieces viewed as a 2D tensor [pieces * b_groups * ndim rows][kdim]
     CUtensorMap bmap;
     const cuuint64_t rows_total = (cuuint64_t)L.nc * a.b_groups * a.ndim;
-    const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
-    const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)kCBoxRows};
-    const cuuint32_t estride[2] = {1, 1};
-    CUresult cr = encode(&bmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim, gstride,
-                         box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        const MapKey key{a.B, (int)rows_total, a.kdim};
+        auto it = g_maps.find(key);
+        if (it != g_maps.end()) {
+            bmap = it->second;
+        } else {
+            const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
+            const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
+            const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)kCBoxRows};
+            const cuuint32_t estride[2] = {1, 1};
+            CUresult cr = encode(&bmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim,
+                                 gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            if (g_maps.size() > 256) g_maps.clear();
+            g_maps.emplace(key, bmap);
+        }
+    }
 
     const int grid = num_sms < L.n_items ? num_sms : L.n_items;
-    if (gather) return launch_t<A_GATHER, E_RED>(bmap, a, L, smem, grid, stream);
-    if (emode == E_STORE) return launch_t<A_ROWS, E_STORE>(bmap, a, L, smem, grid, stream);
-    return launch_t<A_ROWS, E_SPLIT>(bmap, a, L, smem, grid, stream);
+    if (gather) return launch_t<A_GATHER, E_RED>(bmap, a, L, smem, grid, stream, dev);
+    if (emode == E_STORE) return launch_t<A_ROWS, E_STORE>(bmap, a, L, smem, grid, stream, dev);
+    return launch_t<A_ROWS, E_SPLIT>(bmap, a, L, smem, grid, stream, dev);
 }
 
 }  // namespace kifmm

@@ -37,24 +37,43 @@ struct TilePrefix {
     int tile_begin[kOffsets + 1];
 };
 
-// Expand the per-offset prefixes into the tile table of the core kernel:
+// Expand the per-offset prefixes into the tile table of the core kernels:
 // tile t belongs to the last offset k with tile_begin[k] <= t (offsets
 // without pairs have no tiles) and covers 128 consecutive (pair, rhs) rows.
-__global__ void build_tiles_kernel(const TilePrefix pre, int nrhs, int n_tiles, Tile* tiles) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+// One thread per (tile, row) also writes the row tables of the tensor-core
+// kernel (source and target row of every tile row, -1 past the tile's end).
+__global__ void build_tiles_kernel(const TilePrefix pre, int nrhs, int n_tiles, const int* src, const int* dst,
+                                   Tile* tiles, int* row_src, int* row_dst, int* tile_k) {
+    const long total = (long)n_tiles * kTileRows;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / kTileRows), r = (int)(e % kTileRows);
         int lo = 0, hi = kOffsets - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
             if (pre.tile_begin[mid] <= t) lo = mid;
             else hi = mid - 1;
         }
-        Tile out;
-        out.k = lo;
-        out.pair_begin = pre.pair_begin[lo];
-        out.row0 = (t - pre.tile_begin[lo]) * kTileRows;
+        const int row0 = (t - pre.tile_begin[lo]) * kTileRows;
         const int rows = (pre.pair_begin[lo + 1] - pre.pair_begin[lo]) * nrhs;
-        out.nrows = rows - out.row0 < kTileRows ? rows - out.row0 : kTileRows;
-        tiles[t] = out;
+        const int nrows = rows - row0 < kTileRows ? rows - row0 : kTileRows;
+        if (r == 0) {
+            Tile out;
+            out.k = lo;
+            out.pair_begin = pre.pair_begin[lo];
+            out.row0 = row0;
+            out.nrows = nrows;
+            tiles[t] = out;
+            tile_k[t] = lo;
+        }
+        int rs = -1, rd = -1;
+        if (r < nrows) {
+            const int g = row0 + r;
+            const int pr = pre.pair_begin[lo] + g / nrhs;
+            rs = src[pr] * nrhs + g % nrhs;
+            rd = dst[pr] * nrhs + g % nrhs;
+        }
+        row_src[e] = rs;
+        row_dst[e] = rd;
     }
 }
 
@@ -125,13 +144,15 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
     pre.pair_begin[kOffsets] = (int)ps.off_begin[kOffsets];
     pre.tile_begin[kOffsets] = (int)n_tiles;
 
-    // scratch layout: [q~ pieces (rows + 1 zero row) | q~ FP32 | p~ FP32 | tiles]
+    // scratch layout: [q~ pieces (rows + 1 zero row) | q~ FP32 | p~ FP32 | tiles | row tables]
     const long piece_stride = (rows + 1) * rp;
     const size_t qb_bytes = fp32_core ? 0 : align256((size_t)piece_stride * plan->pieces * sizeof(__nv_bfloat16));
     const size_t qt_bytes = fp32_core ? align256((size_t)rows * rp * sizeof(float)) : 0;
     const size_t pt_bytes = align256((size_t)rows * rp * sizeof(float));
     const size_t tile_bytes = align256((size_t)n_tiles * sizeof(Tile));
-    const size_t need = qb_bytes + qt_bytes + pt_bytes + tile_bytes;
+    const size_t rowtab_bytes = align256((size_t)n_tiles * kTileRows * sizeof(int));
+    const size_t tk_bytes = align256((size_t)n_tiles * sizeof(int));
+    const size_t need = qb_bytes + qt_bytes + pt_bytes + tile_bytes + 2 * rowtab_bytes + tk_bytes;
     if (need > kScratchBytes || rows + 1 > (long)INT32_MAX / 2) {
         set_error("kifmm_m2l_apply_noalloc: this level with nrhs = " + std::to_string(nrhs) + " needs " +
                   std::to_string(need) + " bytes of scratch; the static scratch holds " +
@@ -142,6 +163,9 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
     float* qt = reinterpret_cast<float*>(base + qb_bytes);
     float* pt = reinterpret_cast<float*>(base + qb_bytes + qt_bytes);
     Tile* tiles = reinterpret_cast<Tile*>(base + qb_bytes + qt_bytes + pt_bytes);
+    int* row_src = reinterpret_cast<int*>(base + qb_bytes + qt_bytes + pt_bytes + tile_bytes);
+    int* row_dst = reinterpret_cast<int*>(base + qb_bytes + qt_bytes + pt_bytes + tile_bytes + rowtab_bytes);
+    int* tile_k = reinterpret_cast<int*>(base + qb_bytes + qt_bytes + pt_bytes + tile_bytes + 2 * rowtab_bytes);
     const float scale = (float)std::ldexp(1.0 / ls->r0, level);
 
     // 1. compression q~ = R~^T q into the scratch, p~ = 0 (the scratch keeps
@@ -172,8 +196,10 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
     }
     // 2. tile table and the core
     if (n_tiles > 0) {
-        const int blocks = (int)((n_tiles + 255) / 256 < 1024 ? (n_tiles + 255) / 256 : 1024);
-        build_tiles_kernel<<<blocks, 256, 0, s>>>(pre, nrhs, (int)n_tiles, tiles);
+        const long work = n_tiles * (long)kTileRows;
+        const int blocks = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
+        build_tiles_kernel<<<blocks, 256, 0, s>>>(pre, nrhs, (int)n_tiles, ps.src.ptr, ps.dst.ptr, tiles, row_src,
+                                                  row_dst, tile_k);
         KIFMM_CUDA_TRY(cudaGetLastError());
     }
     if (fp32_core) {
@@ -189,13 +215,14 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
         a.B = plan->Cb.ptr;
         a.b_groups = kOffsets;
         a.ndim = rp;
-        a.n_chunk = (plan->core_hilo && plan->products > 1 && rp > 256) ? (rp / 2 + 15) / 16 * 16 : rp;
-        a.tiles = tiles;
+        a.n_chunk = core_chunk(plan);
+        a.row_src = row_src;
+        a.row_dst = row_dst;
+        a.tile_k = tile_k;
         a.n_tiles = (int)n_tiles;
-        a.src = ps.src.ptr;
-        a.dst = ps.dst.ptr;
         a.nrhs = nrhs;
         a.zero_row = (int)rows;
+        a.level_scale[0] = 1.0f;  // the level scale is applied by the expansion
         a.D = pt;
         a.ldd = rp;
         a.n_products = plan->products;

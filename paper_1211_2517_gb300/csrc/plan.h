@@ -9,6 +9,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
@@ -56,12 +57,39 @@ struct DevBuf {
     }
 };
 
+// Tiles of 128 (pair, rhs) rows for one nrhs: the tile list (CUDA-core
+// kernel) and the per-row index tables of the tensor-core kernel.
+struct TileSet {
+    DevBuf<Tile> tiles;
+    DevBuf<int> row_src, row_dst, tile_k;
+    int n_tiles = 0;
+};
+
 struct PairSet {
     DevBuf<int> src, dst;
+    std::vector<int32_t> h_src, h_dst;  // host copies (row tables, multi-level batches)
     std::vector<int64_t> off_begin;  // [317] prefix by offset
-    std::map<int, std::unique_ptr<DevBuf<Tile>>> tiles;  // per nrhs
-    std::map<int, int> n_tiles;
+    std::map<int, std::unique_ptr<TileSet>> tilesets;  // per nrhs
 };
+
+// Pairs of several consecutive levels of one instance, merged for a
+// multi-level batch: box indices are offset so that the levels' density
+// arrays sit back to back; groups are ordered by offset, then level.
+struct MultiState {
+    DevBuf<int> src, dst;
+    struct Group {
+        int k, level_idx;
+        int64_t begin, count;
+    };
+    std::vector<Group> groups;
+    std::vector<int32_t> h_src, h_dst;
+    int64_t total_boxes = 0;
+    std::map<int, std::unique_ptr<TileSet>> tilesets;  // per nrhs
+};
+
+// Upload a tile list and build its row tables from host pair arrays.
+int make_tileset(const std::vector<Tile>& tiles, const std::vector<int32_t>& src, const std::vector<int32_t>& dst,
+                 int nrhs, TileSet& out);
 
 struct LevelState {
     int level = 0, n_boxes = 0;
@@ -86,6 +114,8 @@ struct kifmm_m2l_plan_s {
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
     kifmm::DevBuf<int> err_flag;
     std::map<std::pair<int, int>, std::unique_ptr<kifmm::LevelState>> levels;
+    // multi-level batches keyed by (instance, level_lo, level_hi, adjoint)
+    std::map<std::tuple<int, int, int, int>, std::unique_ptr<kifmm::MultiState>> multi;
     // tracing: (stage, start, stop) event triples recorded by applies
     bool profile = false;
     struct Rec {
@@ -126,5 +156,7 @@ LevelState* find_level(kifmm_m2l_plan plan, int instance, int level);
 int check_device(kifmm_m2l_plan plan);
 // N per work item of the compression / expansion GEMMs.
 int chunk_for(int ndim);
+// N per work item of the core GEMM.
+int core_chunk(kifmm_m2l_plan plan);
 
 }  // namespace kifmm

@@ -148,6 +148,31 @@ class M2LPlan:
         """Transpose of ``apply``: out = beta*out + R~ s_l sum K~^T U~^T pbar."""
         return self._run("kifmm_m2l_apply_adjoint", pbar, level, instance, out, beta, stream)
 
+    def apply_levels(self, x_all, level_lo: int, level_hi: int, instance: int = 0, out=None, beta: float = 0.0,
+                     stream=None, adjoint: bool = False):
+        """Levels level_lo..level_hi in one batch; x_all / out hold the
+        levels' [n_boxes, nrhs, n] (or [n_boxes, n]) arrays back to back."""
+        import torch
+
+        for l in range(level_lo, level_hi + 1):
+            if (instance, l) not in self._levels:
+                cnt = ctypes.c_int64(0)
+                call("kifmm_m2l_level_pairs", self._h, int(instance), int(l), ctypes.byref(cnt))
+        nb = sum(self._levels[(instance, l)] for l in range(level_lo, level_hi + 1))
+        squeeze = x_all.dim() == 2
+        nrhs = 1 if squeeze else x_all.shape[1]
+        shape = (nb, self.n) if squeeze else (nb, nrhs, self.n)
+        _check_tensor(x_all, "input", shape)
+        if out is None:
+            out = torch.empty(shape, device=x_all.device, dtype=torch.float32)
+            beta = 0.0
+        _check_tensor(out, "out", shape)
+        fname = "kifmm_m2l_apply_levels_adjoint" if adjoint else "kifmm_m2l_apply_levels"
+        call(fname, self._h, int(instance), int(level_lo), int(level_hi), int(nrhs),
+             ctypes.c_void_p(x_all.data_ptr()), ctypes.c_void_p(out.data_ptr()), float(beta),
+             _stream_handle(stream))
+        return out
+
     def apply_dense(self, q_up, level: int, instance: int = 0, out=None, beta: float = 0.0, stream=None):
         """Uncompressed FP32 M2L (the baseline)."""
         return self._run("kifmm_m2l_apply_dense", q_up, level, instance, out, beta, stream)

@@ -234,3 +234,33 @@ def test_full_size_sphere_sampled(g, oracle_factors):
         err = rel(out.cpu().numpy()[tg], ref)
         print(f"sphere2m level {l}: sampled rel L2 {err:.3e}")
         assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("precision", ["split6", "fp32"])
+def test_levels_batch_parity(g, oracle_factors, sphere_small, precision):
+    """kifmm_m2l_apply_levels (levels 2..4 in one batch, 3 rhs) against the
+    oracle on every level, forward and adjoint."""
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, precision, tree, (2, 3, 4))
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in (2, 3, 4)])).cuda()
+    for adjoint in (False, True):
+        out = plan.apply_levels(x_all, 2, 4, adjoint=adjoint)
+        plan.sync()
+        o = out.cpu().numpy()
+        row = 0
+        for l in (2, 3, 4):
+            nb = tree.levels[l].shape[0]
+            fn = om.m2l_svd_adjoint if adjoint else om.m2l_svd
+            ref = fn(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64))
+            err = rel(o[row:row + nb], ref)
+            print(f"levels batch {precision} adjoint={adjoint} level {l}: rel L2 {err:.3e}")
+            assert err <= TOL[precision], err
+            row += nb
+    # re-registering a level invalidates the merged batch state
+    plan.set_level(3, tree.levels[3], tree.r0)
+    out2 = plan.apply_levels(x_all, 2, 4)
+    plan.sync()
+    ref_all = plan.apply_levels(x_all, 2, 4)
+    plan.sync()
+    assert rel(out2.cpu().numpy(), ref_all.cpu().numpy().astype(np.float64)) < 1e-6
