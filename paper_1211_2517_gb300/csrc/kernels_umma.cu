@@ -18,14 +18,14 @@
 // TMEM accumulator and the small ones in another, so the large terms are
 // rounded once per 16-element MMA step instead of once per product.
 //
-// Warp roles of a persistent CTA (one per SM, 288 threads):
+// Warp roles of a persistent CTA (one per SM, 384 threads):
 //   warps 0-3  epilogue: TMEM -> registers -> per-warp shared-memory
 //              transpose -> coalesced 16-byte global reductions / stores
-//   warps 4-7  producers: A tiles into 64B-swizzled shared memory (cp.async
-//              gather of BF16 rows, each stage owned by one warp; or FP32
-//              loads split in registers); a producer thread also TMA-loads
-//              the B tiles
-//   warp 8     TMEM allocation and the single MMA-issuing thread
+//   warps 4-10 producers: A tiles into 64B-swizzled shared memory (cp.async
+//              gather of BF16 rows, one ring slot per warp; or, in the rows
+//              modes, warps 4-7 load FP32 rows and split them in registers);
+//              a producer thread also TMA-loads the B tiles
+//   warp 11    TMEM allocation and the single MMA-issuing thread
 // Stages cycle through full/empty mbarriers; two TMEM accumulator slots
 // (when they fit in 512 columns) overlap the epilogue of one work item
 // with the MMAs of the next.
@@ -48,11 +48,14 @@ namespace kifmm {
 
 namespace {
 
-constexpr int kEpiWarps = 4, kProdWarps = 4;
-constexpr int kThreads = (kEpiWarps + kProdWarps + 1) * 32;  // 288
+constexpr int kEpiWarps = 4, kProdWarps = 7;
+constexpr int kRowsProdWarps = 4;  // producer warps of the rows modes (128 threads, one per tile row)
+constexpr int kThreads = (kEpiWarps + kProdWarps + 1) * 32;  // 384
 constexpr int kTileM = 128;
-constexpr int kChunk = 32;              // K elements per stage (64 bytes of BF16: SWIZZLE_64B rows)
-constexpr int kRowBytes = kChunk * 2;   // 64
+// K elements per pipeline stage (64-byte rows, 64-byte swizzle).  The
+// templates also support 16 (32-byte rows, 32-byte swizzle); measured on the
+// core, twice the stages of half the size cost more than they hide.
+__host__ __device__ constexpr int chunk_of(int) { return 32; }
 constexpr int kCBoxRows = 64;           // rows per TMA box of K~_o
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -147,15 +150,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major, 64-byte swizzle, 8-row groups
-// 512 bytes apart (SBO), version 1 (bits 46-47), layout type 4 (bits 61-63).
-__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+// UMMA shared-memory descriptor, K-major, rows of CH BF16 elements swizzled
+// over their width: CH = 32 -> 64-byte swizzle (layout type 4), 8-row groups
+// 512 bytes apart; CH = 16 -> 32-byte swizzle (layout type 6), 8-row groups
+// 256 bytes apart.  Version 1 (bits 46-47), layout type in bits 61-63.
+template <int CH>
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;                  // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;         // SBO
-    d |= (uint64_t)1 << 46;                  // descriptor version
-    d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
+    d |= (uint64_t)1 << 16;                        // LBO (unused for swizzled K-major)
+    d |= (uint64_t)((8 * CH * 2) >> 4) << 32;      // SBO: one 8-row group
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)(CH == 32 ? 4 : 6) << 61;       // SWIZZLE_64B / SWIZZLE_32B
     return d;
 }
 
@@ -208,11 +214,13 @@ __device__ __forceinline__ void red_add_v4(float* addr, uint32_t a, uint32_t b, 
                  : "memory");
 }
 
-// Byte offset of 16-byte chunk c (0..3) of row m in a 64B-swizzled tile whose
-// base is 512-byte aligned: bits [4,6) ^= bits [7,9).
-__device__ __forceinline__ uint32_t swz64(int m, int c) {
-    const uint32_t o = (uint32_t)m * kRowBytes + (uint32_t)c * 16;
-    return o ^ (((o >> 7) & 3u) << 4);
+// Byte offset of 16-byte chunk c of row m in a swizzled tile whose base is
+// aligned to the swizzle atom: 64-byte rows (CH = 32): bits [4,6) ^= bits
+// [7,9); 32-byte rows (CH = 16): bit 4 ^= bit 7.
+template <int CH>
+__device__ __forceinline__ uint32_t swz(int m, int c) {
+    const uint32_t o = (uint32_t)m * (CH * 2) + (uint32_t)c * 16;
+    return CH == 32 ? (o ^ (((o >> 7) & 3u) << 4)) : (o ^ (((o >> 7) & 1u) << 4));
 }
 
 struct Layout {
@@ -255,12 +263,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int S = L.stages;
     const int p0 = 6 - args.n_products;  // first entry of kProd used
+    constexpr int CH = chunk_of(AMODE);  // K elements per stage
+    constexpr int RB = CH * 2;           // bytes per shared-memory row
     const int KC = L.kc_count;
     const int n_chunks = L.n_chunks;
+    // Work items of this CTA: every gridDim.x-th item (consecutive CTAs
+    // take consecutive offset-ordered tiles, which share K~_o in L2)
+    const int i_beg = (int)blockIdx.x, i_end = L.n_items, i_step = (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&sm->full[s], (AMODE == A_GATHER ? 32 : kProdWarps * 32) + 1);
+            mbar_init(&sm->full[s], (AMODE == A_GATHER ? 32 : kRowsProdWarps * 32) + 1);
             mbar_init(&sm->empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -304,35 +317,42 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         int group = 0;  // B group (offset) of the current item, A_GATHER only
         auto issue_b = [&](int s, int item, int kc) {
-            mbar_arrive_expect_tx(&sm->full[s], (uint32_t)L.nc * L.c_rows_alloc * kRowBytes);
+            mbar_arrive_expect_tx(&sm->full[s], (uint32_t)L.nc * L.c_rows_alloc * RB);
             for (int pc = 0; pc < L.nc; ++pc) {
                 const int row_base = (pc * args.b_groups + group) * args.ndim + item_n0(item);
                 for (int rb = 0; rb < L.c_rows_alloc; rb += kCBoxRows)
-                    tma_load_2d(c_smem(s, pc) + rb * kRowBytes, &bmap, kc * kChunk, row_base + rb, &sm->full[s]);
+                    tma_load_2d(c_smem(s, pc) + rb * RB, &bmap, kc * CH, row_base + rb, &sm->full[s]);
             }
         };
         if (AMODE == A_GATHER) {
-            // Stage it belongs to producer warp it % P (P = L.prod_warps divides
-            // the number of slots S, so every slot has exactly one producer
-            // warp: its barriers see one waiter and one arriver, in order).
-            // That warp gathers all 128 rows of the stage (lane l copies
-            // 16-byte chunk l % 4 of rows l / 4 + 8 i: one instruction covers
-            // 8 rows x 64 contiguous bytes), waits for its own copies only and
-            // arrives; P warps keep P stages in flight independently.
+            // Stage it belongs to producer warp it % P (P = L.prod_warps = S,
+            // one ring slot per warp: its barriers see one waiter and one
+            // arriver, in order).  That warp gathers all 128 rows of the stage
+            // (lane l copies 16-byte chunk l % CPR of rows l / CPR + RPI i: one
+            // instruction covers RPI rows of CH * 2 contiguous bytes), waits
+            // for its own copies only and arrives; P warps keep P stages in
+            // flight.
             const int P = L.prod_warps;
-            const int pw = warp - kEpiWarps, cch = lane % 4, rl = lane / 4;
-            int srow[16];
-            for (int item = blockIdx.x; item < L.n_items && ok; item += gridDim.x) {
+            constexpr int CPR = CH / 8;          // 16-byte chunks per row and stage
+            constexpr int RPI = 32 / CPR;        // rows per warp instruction
+            constexpr int NR = kTileM / RPI;     // rows per lane
+            const int pw = warp - kEpiWarps, cch = lane % CPR, rl = lane / CPR;
+            // row indices of this and of the next item (prefetched while the
+            // current one streams: no dependent load at an item's start)
+            int srow[NR], nrow[NR], ngroup = 0;
+            auto load_rows = [&](int item) {
                 const int t = item_tile(item);
-                // does this warp own any stage of this item?
-                const int first_own = (pw - it % P + P) % P;
-                if (pw < P && first_own < KC) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int x = __ldg(args.row_src + (long)t * kTileM + rl + 8 * i);
-                        srow[i] = x < 0 ? args.zero_row : x;
-                    }
-                    group = __ldg(args.tile_k + t) & 0xFFFF;
+                for (int i = 0; i < NR; ++i) nrow[i] = __ldg(args.row_src + (long)t * kTileM + rl + RPI * i);
+                ngroup = __ldg(args.tile_k + t) & 0xFFFF;
+            };
+            if (pw < P && i_beg < i_end) load_rows(i_beg);
+            for (int item = i_beg; item < i_end && ok; item += i_step) {
+                if (pw < P) {
+#pragma unroll
+                    for (int i = 0; i < NR; ++i) srow[i] = nrow[i] < 0 ? args.zero_row : nrow[i];
+                    group = ngroup;
+                    if (item + i_step < i_end) load_rows(item + i_step);
                 }
                 for (int kc = 0; kc < KC; ++kc, ++it) {
                     if (it % P != pw) continue;
@@ -342,15 +362,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    const int col = kc * kChunk + cch * 8;
+                    const int col = kc * CH + cch * 8;
                     const uint32_t bytes = col < args.kdim ? 16u : 0u;
                     const int colc = col < args.kdim ? col : 0;
                     for (int pc = 0; pc < L.na; ++pc) {
                         const __nv_bfloat16* base = args.A + pc * args.a_piece_stride + colc;
                         const uint32_t sbase = a_smem(s, pc);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            cp_async16(sbase + swz64(rl + 8 * i, cch), base + (long)srow[i] * args.kdim, bytes);
+                        for (int i = 0; i < NR; ++i)
+                            cp_async16(sbase + swz<CH>(rl + RPI * i, cch), base + (long)srow[i] * args.kdim, bytes);
                     }
                     cp_async_commit();
                     if (lane == 0) issue_b(s, item, kc);
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             cp_async_wait_0();
-        } else {
+        } else if (v < kRowsProdWarps * 32) {
             // FP32 rows: thread v loads float4 f = v + 128 i (i = 0..7) of the
             // 128 x 32 tile, row f / 8, columns 4 (f % 8) .. +3 (a warp reads
             // 4 rows x 128 contiguous bytes), splits them into BF16 pieces and
@@ -371,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int f = v + 128 * i;
-                    const int row = m0 + f / 8, col = kc * kChunk + 4 * (f % 8);
+                    const int row = m0 + f / 8, col = kc * CH + 4 * (f % 8);
                     buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (row < args.m_rows && col < args.k_valid)
                         buf[i] = __ldg(reinterpret_cast<const float4*>(args.Af + (long)row * args.lda + col));
@@ -396,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     split3(buf[i].y, pc1, L.na);
                     split3(buf[i].z, pc2, L.na);
                     split3(buf[i].w, pc3, L.na);
-                    const uint32_t off = swz64(row, c4 >> 1) + (c4 & 1) * 8;
+                    const uint32_t off = swz<CH>(row, c4 >> 1) + (c4 & 1) * 8;
 #pragma unroll
                     for (int pc = 0; pc < 3; ++pc) {
                         if (pc >= L.na) break;
@@ -431,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int it = 0, tcount = 0, pcount = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < L.n_items && ok; item += gridDim.x, ++tcount) {
+            for (int item = i_beg; item < i_end && ok; item += i_step, ++tcount) {
                 const int acc = tcount % L.n_acc;
                 const uint32_t aph = (uint32_t)(tcount / L.n_acc) & 1u;
                 if (!mbar_wait(&sm->tmem_empty[acc], aph ^ 1u, sm, args.error_flag)) {
@@ -472,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const int ksteps = min(kChunk, args.kdim - kc * kChunk) / 16;
+                    const int ksteps = min(CH, args.kdim - kc * CH) / 16;
                     for (int pi = p0; pi < 6; ++pi) {
                         const bool big = kProd[pi][0] == 0 && kProd[pi][1] == 0;
                         const bool to_hi = big || !(args.hilo || AMODE == A_ROWS);
@@ -481,10 +501,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t cbase = c_smem(s, kProd[pi][1]);
                         for (int ks = 0; ks < ksteps; ++ks) {
                             bool& first = to_hi ? first_hi : first_lo;
-                            const uint64_t ad = umma_desc_sw64(abase + ks * 32);
-                            umma_bf16(d, ad, umma_desc_sw64(cbase + ks * 32), idA, first ? 0u : 1u);
+                            const uint64_t ad = umma_desc<CH>(abase + ks * 32);
+                            umma_bf16(d, ad, umma_desc<CH>(cbase + ks * 32), idA, first ? 0u : 1u);
                             if (nB > 0)
-                                umma_bf16(d + (uint32_t)nA, ad, umma_desc_sw64(cbase + (uint32_t)nA * kRowBytes + ks * 32),
+                                umma_bf16(d + (uint32_t)nA, ad, umma_desc<CH>(cbase + (uint32_t)nA * RB + ks * 32),
                                           idB, first ? 0u : 1u);
                             first = false;
                         }
@@ -511,12 +531,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool has_lo = args.hilo && args.n_products > 1;
         int tcount = 0, pcount = 0;
         int e_nxt_row = -1, e_nxt_k = 0;
-        if (AMODE == A_GATHER && blockIdx.x < L.n_items) {
-            const int t0 = item_tile(blockIdx.x);
+        if (AMODE == A_GATHER && i_beg < i_end) {
+            const int t0 = item_tile(i_beg);
             e_nxt_row = __ldg(args.row_dst + (long)t0 * kTileM + warp * 32 + lane);
             e_nxt_k = __ldg(args.tile_k + t0);
         }
-        for (int item = blockIdx.x; item < L.n_items; item += gridDim.x, ++tcount) {
+        for (int item = i_beg; item < i_end; item += i_step, ++tcount) {
             const int acc = tcount % L.n_acc;
             const uint32_t aph = (uint32_t)(tcount / L.n_acc) & 1u;
             const int n0 = item_n0(item), nthis = item_nthis(item);
@@ -526,8 +546,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (AMODE == A_GATHER) {
                 orow = e_nxt_row;
                 oscale = args.level_scale[(e_nxt_k >> 16) & 31];
-                if (item + (int)gridDim.x < L.n_items) {  // prefetch the next item's rows
-                    const int tn = item_tile(item + gridDim.x);
+                if (item + i_step < i_end) {  // prefetch the next item's rows
+                    const int tn = item_tile(item + i_step);
                     e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + warp * 32 + lane);
                     e_nxt_k = __ldg(args.tile_k + tn);
                 }
@@ -712,11 +732,12 @@ int g_smem_granted[3][64] = {};
 int g_max_smem[64] = {};
 struct MapKey {
     const void* ptr;
-    int rows, kdim;
+    int rows, kdim, ch;
     bool operator<(const MapKey& o) const {
         if (ptr != o.ptr) return ptr < o.ptr;
         if (rows != o.rows) return rows < o.rows;
-        return kdim < o.kdim;
+        if (kdim != o.kdim) return kdim < o.kdim;
+        return ch < o.ch;
     }
 };
 std::map<MapKey, CUtensorMap> g_maps;
@@ -757,10 +778,11 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     L.na = a.n_products == 1 ? 1 : (a.n_products == 3 ? 2 : 3);
     L.nc = L.na;
     L.n_chunks = (a.ndim + a.n_chunk - 1) / a.n_chunk;
-    L.kc_count = (a.kdim + kChunk - 1) / kChunk;
+    const int ch = chunk_of(amode);
+    L.kc_count = (a.kdim + ch - 1) / ch;
     L.c_rows_alloc = (a.n_chunk + kCBoxRows - 1) / kCBoxRows * kCBoxRows;
-    L.a_bytes = kTileM * kRowBytes;
-    L.c_bytes = (uint32_t)L.c_rows_alloc * kRowBytes;
+    L.a_bytes = kTileM * ch * 2;
+    L.c_bytes = (uint32_t)L.c_rows_alloc * ch * 2;
     L.stage_bytes = (uint32_t)L.na * L.a_bytes + (uint32_t)L.nc * L.c_bytes;
     if (gather) {
         L.acc_cols = a.n_chunk * ((a.hilo && a.n_products > 1) ? 2 : 1);
@@ -794,9 +816,9 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     L.stages = avail / (int)L.stage_bytes;
     if (L.stages > 8) L.stages = 8;
     if (L.stages < 2) return cudaErrorInvalidConfiguration;
-    // gather mode: each slot is owned by one producer warp
-    L.prod_warps = L.stages >= kProdWarps ? kProdWarps : L.stages;
-    if (gather) L.stages = L.stages / L.prod_warps * L.prod_warps;
+    // gather mode: one ring slot per producer warp
+    if (gather && L.stages > kProdWarps) L.stages = kProdWarps;
+    L.prod_warps = L.stages;
     L.trans_off = 1024 + (uint32_t)L.stages * L.stage_bytes;
     const size_t smem = 1024 + (size_t)L.trans_off + trans_bytes;
 
@@ -805,17 +827,18 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     const cuuint64_t rows_total = (cuuint64_t)L.nc * a.b_groups * a.ndim;
     {
         std::lock_guard<std::mutex> lock(g_cache_mutex);
-        const MapKey key{a.B, (int)rows_total, a.kdim};
+        const MapKey key{a.B, (int)rows_total, a.kdim, ch};
         auto it = g_maps.find(key);
         if (it != g_maps.end()) {
             bmap = it->second;
         } else {
             const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
             const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
-            const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)kCBoxRows};
+            const cuuint32_t box[2] = {(cuuint32_t)ch, (cuuint32_t)kCBoxRows};
             const cuuint32_t estride[2] = {1, 1};
             CUresult cr = encode(&bmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim,
-                                 gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                 gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
             if (g_maps.size() > 256) g_maps.clear();

@@ -264,3 +264,55 @@ def test_levels_batch_parity(g, oracle_factors, sphere_small, precision):
     ref_all = plan.apply_levels(x_all, 2, 4)
     plan.sync()
     assert rel(out2.cpu().numpy(), ref_all.cpu().numpy().astype(np.float64)) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def torus_mid():
+    """Torus R=1, r=0.3, 300000 points, depth 5, p = 10, eps = 1e-8 (r = 271 > 256:
+    the core runs two MMAs per K step)."""
+    pts = synth.points_torus(300_000, 3)
+    tree = synth.build_tree(pts, 5)
+    qs = {l: synth.random_box_densities(tree.levels[l].shape[0], 1, 488, 500 + l)[:, 0] for l in range(2, 6)}
+    return tree, qs
+
+
+@pytest.mark.parametrize("precision", ["split6", "fp32"])
+def test_p10_parity_levels_batch(g, oracle_factors, torus_mid, precision):
+    tree, qs = torus_mid
+    f = oracle_factors(10, 0.1, 1e-8)
+    plan = make_plan(g, 10, 1e-8, precision, tree, range(2, 6))
+    assert (plan.r, plan.r_pad, plan.n) == (f.r, 272, 488)
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in range(2, 6)])).cuda()
+    out = plan.apply_levels(x_all, 2, 5).cpu().numpy()
+    plan.sync()
+    row = 0
+    for l in range(2, 6):
+        nb = tree.levels[l].shape[0]
+        ref = om.m2l_svd(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64))
+        err = rel(out[row:row + nb], ref)
+        print(f"torus p=10 {precision} level {l}: rel L2 {err:.3e}")
+        assert err <= TOL[precision], err
+        row += nb
+
+
+def test_full_size_torus_p10_sampled(g, oracle_factors):
+    """The 4,194,304-point torus at depth 6, p = 10, eps = 1e-8, split6, all
+    levels in one batch, on sampled targets the oracle computes one by one."""
+    wl = synth.workload("torus4m_p10")
+    tree = wl.tree
+    f = oracle_factors(10, 0.1, 1e-8)
+    plan = make_plan(g, 10, 1e-8, "split6", tree, range(2, 7))
+    qs = {l: synth.random_box_densities(tree.levels[l].shape[0], 1, 488, 700 + l)[:, 0] for l in range(2, 7)}
+    out = plan.apply_levels(torch.from_numpy(np.concatenate([qs[l] for l in range(2, 7)])).cuda(), 2, 6)
+    plan.sync()
+    out = out.cpu().numpy()
+    rng = np.random.default_rng(8)
+    row = 0
+    for l in range(2, 7):
+        nb = tree.levels[l].shape[0]
+        tg = np.sort(rng.choice(nb, size=min(12, nb), replace=False))
+        ref = om.m2l_svd_targets(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64), tg)[:, 0, :]
+        err = rel(out[row:row + nb][tg], ref)
+        print(f"torus4m level {l}: sampled rel L2 {err:.3e}")
+        assert err <= 1e-6, err
+        row += nb
