@@ -161,6 +161,35 @@ int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int 
 int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                                    const float* pbar_down, float* qbar_up, float beta, void* stream);
 
+/* One FMM instance's share of a batch: levels level_lo..level_hi of
+ * `instance` of `plan`, nrhs right-hand sides, DEVICE buffers laid out as
+ * for kifmm_m2l_apply_levels, p_down = beta * p_down + M2L(q_up). */
+typedef struct kifmm_m2l_batch_item {
+    kifmm_m2l_plan plan;
+    int instance;
+    int level_lo, level_hi;
+    int nrhs;
+    const float* q_up;
+    float* p_down;
+    float beta;
+} kifmm_m2l_batch_item;
+
+/* Compressed M2L of many FMM instances of uneven sizes (and of several
+ * operators, e.g. different p) in one batch (Step 3.1 for every instance).
+ * Items are grouped by plan; for each plan one persistent compression, one
+ * core and one expansion launch cover all its items (the core walks one
+ * offset-ordered tile list merged over every item and level).  Tables and
+ * scratch of a batch are built on its first call and cached by the batch's
+ * signature (plans, instances, levels, nrhs, pointers, beta); the cached
+ * batches of a plan are dropped by kifmm_m2l_set_level and by
+ * kifmm_m2l_destroy on that plan.  With use_graph != 0 the launches of
+ * the batch are captured once into a CUDA graph (after one eager pass,
+ * which produces that call's result) and later calls with the same
+ * signature replay the graph on `stream`.  Plans must use a tensor-core
+ * precision (KIFMM_PREC_FP32 plans: KIFMM_ERR_UNSUPPORTED).  Items of one
+ * plan must not write overlapping p_down buffers. */
+int kifmm_m2l_apply_batch(int n_items, const kifmm_m2l_batch_item* items, int use_graph, void* stream);
+
 /* Uncompressed M2L (Eq. eq-m2l), the baseline the compression is compared
  * with:  p_down = beta * p_down + s_l sum_{s in I^t} K_{t-s} q^s  with the
  * FP32 unit-level K_o (formed on first use; 316 n^2 floats of device
@@ -222,6 +251,38 @@ int kifmm_m2l_profile_enable(kifmm_m2l_plan plan, int enable);
  * this library's kernel launches inside those intervals.  Either output
  * may be NULL. */
 int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
+
+/* ---- autotuning ---------------------------------------------------------- */
+
+/* The choice kifmm_m2l_autotune kept: n_chunk = N columns of K~_o per core
+ * work item, contiguous = 1 if each CTA takes one contiguous run of work
+ * items (0: items dealt round-robin), core_ms = the core launch's mean time
+ * (ms) under that choice, from_cache = 1 if read back from the cache file. */
+typedef struct kifmm_m2l_tune_result {
+    int n_chunk;
+    int contiguous;
+    double core_ms;
+    int from_cache;
+} kifmm_m2l_tune_result;
+
+/* Tile autotuner of the core GEMM (Step 3.1's per-offset products, on the
+ * tensor cores).  The paper fixes no launch shape; the candidates here
+ * change only how the core's (tile, N-chunk) work items are spread over the
+ * persistent CTAs, never the arithmetic of an output element (atomic
+ * accumulation order aside, which is never fixed).  Runs
+ * kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up,
+ * p_down, beta = 0, stream) once plus `reps` times (1 <= reps <= 1000) per
+ * candidate, times the core launch with CUDA events, keeps the fastest in
+ * the plan (used from then on by apply, apply_levels and apply_batch on this
+ * plan) and writes it to *result (may be NULL).  p_down is overwritten with
+ * the M2L of q_up.  Synchronises `stream`; drops pending tracing records.
+ * If the environment variable KIFMM_M2L_AUTOTUNE_CACHE names a file, a
+ * previous result for the same operator, device and workload (levels, nrhs,
+ * box and pair counts) is read from it and applied without timing, and a
+ * new result is added to it (a JSON object, one entry per line).
+ * KIFMM_PREC_FP32 plans: KIFMM_ERR_UNSUPPORTED. */
+int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                       const float* q_up, float* p_down, int reps, kifmm_m2l_tune_result* result, void* stream);
 
 /* ---- host-side introspection (no GPU needed) ----------------------------- */
 

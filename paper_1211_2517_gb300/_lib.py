@@ -30,14 +30,26 @@ EXPORTED = (
     "kifmm_m2l_precompute", "kifmm_m2l_destroy", "kifmm_m2l_plan_rank", "kifmm_m2l_set_level",
     "kifmm_m2l_level_pairs", "kifmm_m2l_apply", "kifmm_m2l_apply_adjoint", "kifmm_m2l_apply_dense",
     "kifmm_m2l_apply_noalloc", "kifmm_m2l_apply_levels", "kifmm_m2l_apply_levels_adjoint",
-    "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error",
-    "kifmm_m2l_version",
+    "kifmm_m2l_apply_batch",
+    "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
+    "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error", "kifmm_m2l_version",
 )
 
 
 class Params(ctypes.Structure):
     _fields_ = [("kernel_id", ctypes.c_int), ("p", ctypes.c_int), ("eps", ctypes.c_double),
                 ("d", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("n_chunk", ctypes.c_int), ("contiguous", ctypes.c_int), ("core_ms", ctypes.c_double),
+                ("from_cache", ctypes.c_int)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("instance", ctypes.c_int), ("level_lo", ctypes.c_int),
+                ("level_hi", ctypes.c_int), ("nrhs", ctypes.c_int), ("q_up", ctypes.c_void_p),
+                ("p_down", ctypes.c_void_p), ("beta", ctypes.c_float)]
 
 
 class KifmmError(RuntimeError):
@@ -73,9 +85,11 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_apply_noalloc": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_levels": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_levels_adjoint": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
+        "kifmm_m2l_apply_batch": [i32, ctypes.POINTER(BatchItem), i32, vp],
         "kifmm_m2l_sync": [vp, vp],
         "kifmm_m2l_profile_enable": [vp, i32],
         "kifmm_m2l_profile_read": [vp, ctypes.POINTER(ctypes.c_double), pi64],
+        "kifmm_m2l_autotune": [vp, i32, i32, i32, i32, vp, vp, i32, ctypes.POINTER(TuneResult), vp],
         "kifmm_m2l_factors_host": [ctypes.POINTER(Params), pint, pint, vp, vp, vp],
         "kifmm_m2l_pairs_host": [i32, i32, vp, pi64, vp, vp, vp],
     }

@@ -25,3 +25,23 @@ class M2LFunction(torch.autograd.Function):
 def m2l(q_up: torch.Tensor, plan, level: int, instance: int = 0) -> torch.Tensor:
     """Differentiable compressed M2L of one registered level."""
     return M2LFunction.apply(q_up, plan, level, instance)
+
+
+class M2LLevelsFunction(torch.autograd.Function):
+    """Levels level_lo..level_hi in one batch (kifmm_m2l_apply_levels and its
+    adjoint); inputs and outputs hold the levels' arrays back to back."""
+
+    @staticmethod
+    def forward(ctx, q_all, plan, level_lo, level_hi, instance):
+        ctx.plan, ctx.lo, ctx.hi, ctx.instance = plan, level_lo, level_hi, instance
+        return plan.apply_levels(q_all.contiguous(), level_lo, level_hi, instance)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = ctx.plan.apply_levels(grad_out.contiguous(), ctx.lo, ctx.hi, ctx.instance, adjoint=True)
+        return g, None, None, None, None
+
+
+def m2l_levels(q_all: torch.Tensor, plan, level_lo: int, level_hi: int, instance: int = 0) -> torch.Tensor:
+    """Differentiable compressed M2L of the registered levels level_lo..level_hi."""
+    return M2LLevelsFunction.apply(q_all, plan, level_lo, level_hi, instance)

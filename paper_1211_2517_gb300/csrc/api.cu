@@ -213,6 +213,7 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
         a.b_groups = kOffsets;
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
+        a.contiguous = plan->tune_contig;
         a.row_src = ts->row_src.ptr;
         a.row_dst = ts->row_dst.ptr;
         a.tile_k = ts->tile_k.ptr;
@@ -256,42 +257,8 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
 }
 
 
-// Merged pairs of levels lo..hi (forward or adjoint), built on first use.
 int get_multi(kifmm_m2l_plan plan, int instance, int lo, int hi, bool adjoint, MultiState** out) {
-    const auto key = std::make_tuple(instance, lo, hi, adjoint ? 1 : 0);
-    auto it = plan->multi.find(key);
-    if (it != plan->multi.end()) {
-        *out = it->second.get();
-        return KIFMM_OK;
-    }
-    auto ms = std::make_unique<MultiState>();
-    std::vector<int64_t> box_off(hi - lo + 1);
-    std::vector<PairSet*> sets(hi - lo + 1);
-    for (int l = lo; l <= hi; ++l) {
-        LevelState* ls = find_level(plan, instance, l);
-        box_off[l - lo] = ms->total_boxes;
-        ms->total_boxes += ls->n_boxes;
-        sets[l - lo] = adjoint ? &ls->adj : &ls->fwd;
-    }
-    std::vector<int32_t> src, dst;
-    for (int k = 0; k < kOffsets; ++k)
-        for (int li = 0; li <= hi - lo; ++li) {
-            PairSet& ps = *sets[li];
-            const int64_t b = ps.off_begin[k], e = ps.off_begin[k + 1];
-            if (e == b) continue;
-            ms->groups.push_back({k, li, (int64_t)src.size(), e - b});
-            for (int64_t i = b; i < e; ++i) {
-                src.push_back((int32_t)(ps.h_src[i] + box_off[li]));
-                dst.push_back((int32_t)(ps.h_dst[i] + box_off[li]));
-            }
-        }
-    KIFMM_CUDA_TRY(ms->src.upload(src.data(), src.size()));
-    KIFMM_CUDA_TRY(ms->dst.upload(dst.data(), dst.size()));
-    ms->h_src.swap(src);
-    ms->h_dst.swap(dst);
-    *out = ms.get();
-    plan->multi[key] = std::move(ms);
-    return KIFMM_OK;
+    return get_multi_state(plan, instance, lo, hi, adjoint, out);
 }
 
 int get_multi_tiles(MultiState& ms, int nrhs, TileSet** out) {
@@ -409,6 +376,7 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         a.b_groups = kOffsets;
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
+        a.contiguous = plan->tune_contig;
         a.row_src = ts->row_src.ptr;
         a.row_dst = ts->row_dst.ptr;
         a.tile_k = ts->tile_k.ptr;
@@ -461,7 +429,9 @@ int chunk_for(int ndim) {
     return ((ndim + parts - 1) / parts + 15) / 16 * 16;
 }
 
-int core_chunk(kifmm_m2l_plan plan) {
+int core_chunk(kifmm_m2l_plan plan) { return plan->tune_chunk ? plan->tune_chunk : core_chunk_default(plan); }
+
+int core_chunk_default(kifmm_m2l_plan plan) {
     const int rp = plan->rp;
     // hi and lo side by side must fit the 512 TMEM columns (one slot); a
     // split of N would gather every A row once per part, which costs more
@@ -500,6 +470,45 @@ int make_tileset(const std::vector<Tile>& tiles, const std::vector<int32_t>& src
     KIFMM_CUDA_TRY(out.row_dst.upload(rd.data(), rd.size()));
     KIFMM_CUDA_TRY(out.tile_k.upload(tk.data(), tk.size()));
     out.n_tiles = (int)nt;
+    return KIFMM_OK;
+}
+
+// Merged pairs of levels lo..hi of one instance (forward or adjoint), built
+// on first use and cached in the plan.
+int get_multi_state(kifmm_m2l_plan plan, int instance, int lo, int hi, bool adjoint, MultiState** out) {
+    const auto key = std::make_tuple(instance, lo, hi, adjoint ? 1 : 0);
+    auto it = plan->multi.find(key);
+    if (it != plan->multi.end()) {
+        *out = it->second.get();
+        return KIFMM_OK;
+    }
+    auto ms = std::make_unique<MultiState>();
+    std::vector<int64_t> box_off(hi - lo + 1);
+    std::vector<PairSet*> sets(hi - lo + 1);
+    for (int l = lo; l <= hi; ++l) {
+        LevelState* ls = find_level(plan, instance, l);
+        box_off[l - lo] = ms->total_boxes;
+        ms->total_boxes += ls->n_boxes;
+        sets[l - lo] = adjoint ? &ls->adj : &ls->fwd;
+    }
+    std::vector<int32_t> src, dst;
+    for (int k = 0; k < kOffsets; ++k)
+        for (int li = 0; li <= hi - lo; ++li) {
+            PairSet& ps = *sets[li];
+            const int64_t b = ps.off_begin[k], e = ps.off_begin[k + 1];
+            if (e == b) continue;
+            ms->groups.push_back({k, li, (int64_t)src.size(), e - b});
+            for (int64_t i = b; i < e; ++i) {
+                src.push_back((int32_t)(ps.h_src[i] + box_off[li]));
+                dst.push_back((int32_t)(ps.h_dst[i] + box_off[li]));
+            }
+        }
+    KIFMM_CUDA_TRY(ms->src.upload(src.data(), src.size()));
+    KIFMM_CUDA_TRY(ms->dst.upload(dst.data(), dst.size()));
+    ms->h_src.swap(src);
+    ms->h_dst.swap(dst);
+    *out = ms.get();
+    plan->multi[key] = std::move(ms);
     return KIFMM_OK;
 }
 
@@ -654,6 +663,7 @@ int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out) {
 }
 
 int kifmm_m2l_destroy(kifmm_m2l_plan plan) {
+    if (plan) forget_batches_of(plan);
     delete plan;
     return KIFMM_OK;
 }
@@ -713,6 +723,7 @@ int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double roo
         }
         st = build_pairset(atg, asr, aof, ls->adj);
         if (st != KIFMM_OK) return st;
+        forget_batches_of(plan);
         plan->levels[{instance, level}] = std::move(ls);
         for (auto it = plan->multi.begin(); it != plan->multi.end();) {
             const auto& key = it->first;

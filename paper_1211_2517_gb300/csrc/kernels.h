@@ -52,6 +52,19 @@ cudaError_t launch_scale(float* x, long count, float beta, cudaStream_t stream);
 //   expand    D = alpha A_f32 W^T + beta D                    (A_ROWS,   E_STORE)
 // B operands are BF16 pieces [pieces][b_groups][ndim][kdim] read by TMA.
 enum UmmaAMode { A_GATHER = 0, A_ROWS = 1 };
+
+// Rows modes over many buffers (batches of many instances): the virtual row
+// tiles [tile_begin, tile_begin + ceil(m_rows / 128)) of a launch read rows
+// 0..m_rows-1 of Af and write rows of D (E_STORE, with alpha and beta) or
+// rows out_row + r of Dp / Df / Z (E_SPLIT).
+struct RowSeg {
+    const float* Af;
+    float* D;
+    int m_rows;
+    int tile_begin;
+    int out_row;
+    float alpha, beta;
+};
 enum UmmaEMode { E_RED = 0, E_STORE = 1, E_SPLIT = 2 };
 
 struct UmmaArgs {
@@ -78,6 +91,11 @@ struct UmmaArgs {
     int nrhs;
     int zero_row;             // row of the A pieces that is all zero
     float level_scale[32];    // E_RED: factor applied to a tile's output, by tile.k >> 16
+    const float* scale_table; // E_RED: when set, replaces level_scale (index tile.k >> 16)
+    const RowSeg* segs;       // rows modes: when n_segs > 0, the row segments (device)
+    int n_segs;
+    int seg_tiles;            // rows modes with segments: total virtual row tiles
+    int contiguous;           // core: 1 = each CTA takes a contiguous run of tiles
     // epilogue
     float* D;                 // E_RED / E_STORE: FP32 [*][ldd]
     int ldd;

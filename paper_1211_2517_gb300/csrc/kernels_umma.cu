@@ -267,9 +267,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int RB = CH * 2;           // bytes per shared-memory row
     const int KC = L.kc_count;
     const int n_chunks = L.n_chunks;
-    // Work items of this CTA: every gridDim.x-th item (consecutive CTAs
-    // take consecutive offset-ordered tiles, which share K~_o in L2)
-    const int i_beg = (int)blockIdx.x, i_end = L.n_items, i_step = (int)gridDim.x;
+    // Work items of this CTA: every gridDim.x-th item (consecutive CTAs take
+    // consecutive offset-ordered tiles, which share K~_o in L2), or, for the
+    // core when `contiguous` is set, a contiguous run of the tile list
+    const bool contig = AMODE == A_GATHER && args.contiguous;
+    const int i_beg = contig ? (int)((long)L.n_items * blockIdx.x / gridDim.x) : (int)blockIdx.x;
+    const int i_end = contig ? (int)((long)L.n_items * (blockIdx.x + 1) / gridDim.x) : L.n_items;
+    const int i_step = contig ? 1 : (int)gridDim.x;
+    // rows modes: segment of a virtual row tile (binary search)
+    auto find_seg = [&](int tt) -> int {
+        int lo = 0, hi = args.n_segs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (args.segs[mid].tile_begin <= tt) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -387,14 +401,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             // stores them swizzled.
             float4 buf[8];
             auto load = [&](int item, int kc) {
-                const int m0 = item_tile(item) * kTileM;
+                const int tt = item_tile(item);
+                const float* Af = args.Af;
+                long m0 = (long)tt * kTileM, mrows = args.m_rows;
+                if (args.n_segs > 0) {
+                    const RowSeg sg = args.segs[find_seg(tt)];
+                    Af = sg.Af;
+                    m0 = (long)(tt - sg.tile_begin) * kTileM;
+                    mrows = sg.m_rows;
+                }
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int f = v + 128 * i;
-                    const int row = m0 + f / 8, col = kc * CH + 4 * (f % 8);
+                    const long row = m0 + f / 8;
+                    const int col = kc * CH + 4 * (f % 8);
                     buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (row < args.m_rows && col < args.k_valid)
-                        buf[i] = __ldg(reinterpret_cast<const float4*>(args.Af + (long)row * args.lda + col));
+                    if (row < mrows && col < args.k_valid)
+                        buf[i] = __ldg(reinterpret_cast<const float4*>(Af + row * args.lda + col));
                 }
             };
             int item = blockIdx.x, kc = 0;
@@ -543,14 +566,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             // this lane's output row (tile row warp*32 + lane); -1 = none
             long orow = -1;
             float oscale = 1.0f;
+            float* e_dbase = args.D;
+            float e_alpha = args.alpha, e_beta = args.beta;
             if (AMODE == A_GATHER) {
                 orow = e_nxt_row;
-                oscale = args.level_scale[(e_nxt_k >> 16) & 31];
+                oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
+                                          : args.level_scale[(e_nxt_k >> 16) & 31];
                 if (item + i_step < i_end) {  // prefetch the next item's rows
                     const int tn = item_tile(item + i_step);
                     e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + warp * 32 + lane);
                     e_nxt_k = __ldg(args.tile_k + tn);
                 }
+            } else if (args.n_segs > 0) {
+                const RowSeg sg = args.segs[find_seg(item_tile(item))];
+                const long r = (long)(item_tile(item) - sg.tile_begin) * kTileM + warp * 32 + lane;
+                if (r < sg.m_rows) orow = (EMODE == E_SPLIT) ? sg.out_row + r : r;
+                e_dbase = sg.D;
+                e_alpha = sg.alpha;
+                e_beta = sg.beta;
             } else {
                 const long r = (long)item_tile(item) * kTileM + warp * 32 + lane;
                 if (r < args.m_rows) orow = r;
@@ -657,23 +690,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    __float_as_uint(oscale * x.w));
                     } else if (EMODE == E_STORE) {
                         if (col < args.n_valid) {
-                            float4* dp = reinterpret_cast<float4*>(args.D + grow * args.ldd + col);
-                            float4 y = make_float4(args.alpha * x.x, args.alpha * x.y, args.alpha * x.z,
-                                                   args.alpha * x.w);
-                            if (args.beta != 0.f) {
+                            float4* dp = reinterpret_cast<float4*>(e_dbase + grow * args.ldd + col);
+                            float4 y = make_float4(e_alpha * x.x, e_alpha * x.y, e_alpha * x.z, e_alpha * x.w);
+                            if (e_beta != 0.f) {
                                 const float4 o = *dp;
-                                y.x = fmaf(args.beta, o.x, y.x);
-                                y.y = fmaf(args.beta, o.y, y.y);
-                                y.z = fmaf(args.beta, o.z, y.z);
-                                y.w = fmaf(args.beta, o.w, y.w);
+                                y.x = fmaf(e_beta, o.x, y.x);
+                                y.y = fmaf(e_beta, o.y, y.y);
+                                y.z = fmaf(e_beta, o.z, y.z);
+                                y.w = fmaf(e_beta, o.w, y.w);
                             }
                             *dp = y;
                         }
                     } else {  // E_SPLIT
-                        x.x *= args.alpha;
-                        x.y *= args.alpha;
-                        x.z *= args.alpha;
-                        x.w *= args.alpha;
+                        x.x *= e_alpha;
+                        x.y *= e_alpha;
+                        x.z *= e_alpha;
+                        x.w *= e_alpha;
                         if (args.Df)
                             *reinterpret_cast<float4*>(args.Df + grow * args.ldd + col) = x;
                         if (args.Z)
@@ -794,7 +826,7 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
         L.acc_cols = a.n_chunk;
         L.n_acc = 2;
     }
-    const long row_tiles = gather ? a.n_tiles : ((long)a.m_rows + kTileM - 1) / kTileM;
+    const long row_tiles = gather ? a.n_tiles : (a.n_segs > 0 ? (long)a.seg_tiles : ((long)a.m_rows + kTileM - 1) / kTileM);
     if (row_tiles * L.n_chunks > INT32_MAX) return cudaErrorInvalidValue;
     L.n_items = (int)(row_tiles * L.n_chunks);
     if (L.n_items <= 0) return cudaSuccess;

@@ -110,6 +110,9 @@ struct kifmm_m2l_plan_s {
     std::vector<double> sigma;
     int n_pad = 0;    // n rounded up to 16 (K of the compression, N of the expansion)
     int core_hilo = 0;
+    // core launch choices picked by kifmm_m2l_autotune (0: defaults)
+    int tune_chunk = 0;
+    int tune_contig = 0;
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
     kifmm::DevBuf<int> err_flag;
@@ -156,7 +159,12 @@ LevelState* find_level(kifmm_m2l_plan plan, int instance, int level);
 int check_device(kifmm_m2l_plan plan);
 // N per work item of the compression / expansion GEMMs.
 int chunk_for(int ndim);
-// N per work item of the core GEMM.
+// N per work item of the core GEMM (the autotuned choice, else the default).
 int core_chunk(kifmm_m2l_plan plan);
+int core_chunk_default(kifmm_m2l_plan plan);
+// Merged pairs of levels lo..hi of one instance (built on first use).
+int get_multi_state(kifmm_m2l_plan plan, int instance, int lo, int hi, bool adjoint, MultiState** out);
+// Drop cached batches that use `plan` (on destroy).
+void forget_batches_of(kifmm_m2l_plan plan);
 
 }  // namespace kifmm

@@ -1,0 +1,191 @@
+// kifmm_m2l_autotune: picks the tensor-core core launch's work assignment on
+// the caller's own workload.
+//
+// Candidates change only how the core's (tile, N-chunk) work items are laid
+// out over the persistent CTAs, never the arithmetic of an output element:
+//   contiguous   0: item i goes to CTA i mod grid (neighbouring tiles, which
+//                   share the offset and so the core matrix, run at the same
+//                   time on different SMs and hit the same L2 lines);
+//                1: each CTA takes one contiguous run of items (its own
+//                   offsets, fewer core-matrix switches per CTA).
+//   n_chunk      the plan's default N per item, or half of it (more, smaller
+//                items: better balance, but every A row is gathered once per
+//                N part).
+// Each candidate is timed with CUDA events around the core launch of
+// kifmm_m2l_apply_levels.  With $KIFMM_M2L_AUTOTUNE_CACHE naming a file,
+// results are kept there as a JSON object keyed by operator, device and
+// workload, and a later call with the same key reads the choice back without
+// timing anything.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "kifmm_internal.h"
+#include "plan.h"
+
+using namespace kifmm;
+
+namespace {
+
+std::mutex g_tune_mutex;
+
+std::string tune_key(kifmm_m2l_plan plan, const MultiState* ms, int nrhs, int lo, int hi) {
+    int64_t pairs = 0;
+    for (const auto& g : ms->groups) pairs += g.count;
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, plan->device);
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "p=%d eps=%.6e d=%.6g prec=%d sm=%d%d sms=%d levels=%d-%d nrhs=%d boxes=%lld pairs=%lld",
+                  plan->prm.p, plan->prm.eps, plan->prm.d, plan->prm.precision, prop.major, prop.minor, plan->num_sms,
+                  lo, hi, nrhs, (long long)ms->total_boxes, (long long)pairs);
+    return buf;
+}
+
+// The cache file holds one entry per line:
+//   "<key>": {"n_chunk": N, "contiguous": C, "core_ms": T},
+// inside one pair of braces, so that it is a JSON object.
+std::map<std::string, std::string> read_cache(const char* path) {
+    std::map<std::string, std::string> out;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        const size_t a = line.find('"');
+        if (a == std::string::npos) continue;
+        const size_t b = line.find('"', a + 1);
+        if (b == std::string::npos) continue;
+        const size_t c = line.find('{', b);
+        const size_t d = line.find('}', c == std::string::npos ? b : c);
+        if (c == std::string::npos || d == std::string::npos) continue;
+        out[line.substr(a + 1, b - a - 1)] = line.substr(c, d - c + 1);
+    }
+    return out;
+}
+
+bool parse_entry(const std::string& v, int* chunk, int* contig, double* ms) {
+    const char* s = v.c_str();
+    const char* pc = std::strstr(s, "\"n_chunk\":");
+    const char* pg = std::strstr(s, "\"contiguous\":");
+    const char* pm = std::strstr(s, "\"core_ms\":");
+    if (!pc || !pg || !pm) return false;
+    *chunk = std::atoi(pc + 10);
+    *contig = std::atoi(pg + 13);
+    *ms = std::atof(pm + 10);
+    return true;
+}
+
+int write_cache(const char* path, const std::map<std::string, std::string>& entries) {
+    const std::string tmp = std::string(path) + ".tmp";
+    {
+        std::ofstream f(tmp, std::ios::trunc);
+        if (!f) return -1;
+        f << "{\n";
+        size_t i = 0;
+        for (const auto& e : entries) {
+            f << "\"" << e.first << "\": " << e.second << (++i < entries.size() ? ",\n" : "\n");
+        }
+        f << "}\n";
+        if (!f) return -1;
+    }
+    return std::rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                                  const float* q_up, float* p_down, int reps, kifmm_m2l_tune_result* result,
+                                  void* stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (reps < 1 || reps > 1000 || nrhs < 1) {
+        set_error("reps must be in [1, 1000] and nrhs >= 1");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (plan->prm.precision == KIFMM_PREC_FP32) {
+        set_error("FP32 plans run the SIMT core, which has no launch choices to tune");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    MultiState* ms = nullptr;
+    st = get_multi_state(plan, instance, level_lo, level_hi, false, &ms);
+    if (st != KIFMM_OK) return st;
+    const std::string key = tune_key(plan, ms, nrhs, level_lo, level_hi);
+    const char* path = std::getenv("KIFMM_M2L_AUTOTUNE_CACHE");
+    if (path && *path) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        const auto entries = read_cache(path);
+        auto it = entries.find(key);
+        int c = 0, g = 0;
+        double t = 0;
+        if (it != entries.end() && parse_entry(it->second, &c, &g, &t) && c >= 16 && c % 16 == 0 && c <= 512 &&
+            (g == 0 || g == 1)) {
+            plan->tune_chunk = c;
+            plan->tune_contig = g;
+            if (result) *result = {c, g, t, 1};
+            return KIFMM_OK;
+        }
+    }
+
+    // candidates
+    const int c0 = core_chunk_default(plan);
+    std::vector<int> chunks{c0};
+    const int c1 = (c0 / 2 + 15) / 16 * 16;
+    if (c1 >= 16 && c1 < c0) chunks.push_back(c1);
+    const bool was_profiling = plan->profile;
+    kifmm_m2l_profile_read(plan, nullptr, nullptr);  // drop pending records
+    plan->profile = true;
+    double best = 1e300;
+    int best_c = c0, best_g = 0;
+    st = KIFMM_OK;
+    for (int c : chunks) {
+        for (int g = 0; g < 2 && st == KIFMM_OK; ++g) {
+            plan->tune_chunk = c;
+            plan->tune_contig = g;
+            // one untimed pass (tile tables, first launch), then reps timed ones
+            st = kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, 0.0f, stream);
+            if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, nullptr, nullptr);
+            for (int r = 0; r < reps && st == KIFMM_OK; ++r)
+                st = kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, 0.0f, stream);
+            double t[3] = {0, 0, 0};
+            if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, t, nullptr);
+            if (st == KIFMM_OK) st = kifmm_m2l_sync(plan, stream);
+            if (st == KIFMM_OK && t[1] / reps < best) {
+                best = t[1] / reps;
+                best_c = c;
+                best_g = g;
+            }
+        }
+    }
+    plan->profile = was_profiling;
+    if (st != KIFMM_OK) {
+        plan->tune_chunk = 0;
+        plan->tune_contig = 0;
+        return st;
+    }
+    plan->tune_chunk = best_c == c0 ? 0 : best_c;
+    plan->tune_contig = best_g;
+    if (result) *result = {best_c, best_g, best, 0};
+    if (path && *path) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto entries = read_cache(path);
+        char v[128];
+        std::snprintf(v, sizeof(v), "{\"n_chunk\": %d, \"contiguous\": %d, \"core_ms\": %.6f}", best_c, best_g, best);
+        entries[key] = v;
+        if (write_cache(path, entries) != 0) {
+            set_error(std::string("could not write the autotune cache ") + path);
+            return KIFMM_ERR_INVALID_ARG;
+        }
+    }
+    return KIFMM_OK;
+}

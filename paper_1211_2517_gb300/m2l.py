@@ -188,6 +188,51 @@ class M2LPlan:
         call("kifmm_m2l_profile_read", self._h, ms, ctypes.byref(n))
         return {"compress": ms[0], "core": ms[1], "expand": ms[2]}, n.value
 
+    def autotune(self, x_all, level_lo: int, level_hi: int, instance: int = 0, reps: int = 5, out=None,
+                 stream=None) -> dict:
+        """Pick the core launch's work assignment on this workload (see
+        kifmm_m2l_autotune); ``out`` receives the M2L of ``x_all``."""
+        import torch
+
+        for l in range(level_lo, level_hi + 1):
+            if (instance, l) not in self._levels:
+                cnt = ctypes.c_int64(0)
+                call("kifmm_m2l_level_pairs", self._h, int(instance), int(l), ctypes.byref(cnt))
+        nb = sum(self._levels[(instance, l)] for l in range(level_lo, level_hi + 1))
+        nrhs = 1 if x_all.dim() == 2 else x_all.shape[1]
+        shape = (nb, self.n) if x_all.dim() == 2 else (nb, nrhs, self.n)
+        _check_tensor(x_all, "input", shape)
+        if out is None:
+            out = torch.empty(shape, device=x_all.device, dtype=torch.float32)
+        _check_tensor(out, "out", shape)
+        res = _lib.TuneResult()
+        call("kifmm_m2l_autotune", self._h, int(instance), int(level_lo), int(level_hi), int(nrhs),
+             ctypes.c_void_p(x_all.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(reps), ctypes.byref(res),
+             _stream_handle(stream))
+        return {"n_chunk": res.n_chunk, "contiguous": res.contiguous, "core_ms": res.core_ms,
+                "from_cache": bool(res.from_cache)}
+
     def sync(self, stream=None) -> None:
         """Synchronise the stream and raise on device-side failures."""
         call("kifmm_m2l_sync", self._h, _stream_handle(stream))
+
+
+def apply_batch(items, use_graph: bool = False, stream=None):
+    """Compressed M2L of many instances in one batch.
+
+    ``items``: sequence of dicts with keys plan (M2LPlan), level_lo, level_hi,
+    x (CUDA float32 [boxes, nrhs, n] or [boxes, n], levels back to back),
+    out (same shape), and optional instance (0) and beta (0.0).
+    """
+    arr = (_lib.BatchItem * len(items))()
+    for i, it in enumerate(items):
+        plan, x, out = it["plan"], it["x"], it["out"]
+        inst, lo, hi = it.get("instance", 0), it["level_lo"], it["level_hi"]
+        nb = sum(plan._levels[(inst, l)] for l in range(lo, hi + 1))
+        nrhs = 1 if x.dim() == 2 else x.shape[1]
+        shape = (nb, plan.n) if x.dim() == 2 else (nb, nrhs, plan.n)
+        _check_tensor(x, "x", shape)
+        _check_tensor(out, "out", shape)
+        arr[i] = _lib.BatchItem(plan._h.value, inst, lo, hi, nrhs, x.data_ptr(), out.data_ptr(),
+                                float(it.get("beta", 0.0)))
+    call("kifmm_m2l_apply_batch", len(items), arr, 1 if use_graph else 0, _stream_handle(stream))

@@ -215,6 +215,59 @@ def test_autograd_central_differences(g, oracle_factors):
         assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "split6"])
+def test_full_size_adjoint_autograd_sphere1m(g, oracle_factors, precision):
+    """Loss 0.5 ||phi - phi_t||^2, phi = M2L(q) over levels 2..5 of the
+    1,048,576-point sphere at depth 5 (p = 8, eps = 1e-7, phi_t ~ N(0,1)),
+    differentiated through the levels-batch autograd Function: the gradient
+    against the oracle's transpose product (C_k^T on the reversed offsets),
+    then central differences with h = 1e-3."""
+    from paper_1211_2517_gb300.autograd import m2l_levels
+
+    wl = synth.workload("sphere1m_p8")
+    tree = wl.tree
+    levels = range(2, 6)
+    plan = make_plan(g, 8, 1e-7, precision, tree, levels)
+    nbs = [tree.levels[l].shape[0] for l in levels]
+    rng = np.random.default_rng(55)
+    q0 = np.concatenate([synth.random_box_densities(nb, 1, 296, 700 + l)[:, 0] for nb, l in zip(nbs, levels)])
+    phi_t = rng.standard_normal(q0.shape).astype(np.float32)
+    q = torch.from_numpy(q0).cuda().requires_grad_(True)
+    phit = torch.from_numpy(phi_t).cuda()
+
+    def loss(x):
+        return 0.5 * ((m2l_levels(x, plan, 2, 5).double() - phit.double()) ** 2).sum()
+
+    L = loss(q)
+    L.backward()
+    grad = q.grad.double()
+    f = oracle_factors(8, 0.1, 1e-7)
+    gn = grad.cpu().numpy()
+    row = 0
+    for nb, l in zip(nbs, levels):
+        box = tree.levels[l]
+        sl = slice(row, row + nb)
+        resid = om.m2l_svd(box, l, tree.r0, f, q0[sl].astype(np.float64)) - phi_t[sl]
+        gref = om.m2l_svd_adjoint(box, l, tree.r0, f, resid)
+        err = rel(gn[sl], gref)
+        print(f"sphere1m {precision} level {l}: gradient rel L2 {err:.3e}")
+        assert err <= 1e-5, err
+        row += nb
+    h = 1e-3
+    gdir = grad.float() / grad.float().pow(2).mean().sqrt()
+    for j in range(4):
+        z = torch.from_numpy(rng.standard_normal(q0.shape).astype(np.float32)).cuda()
+        v = gdir + 0.5 * z
+        with torch.no_grad():
+            lp = float(loss(q + h * v))
+            lm = float(loss(q - h * v))
+        fd = (lp - lm) / (2 * h)
+        an = float((grad * v.double()).sum())
+        print(f"sphere1m {precision} direction {j}: fd {fd:.9e} analytic {an:.9e}")
+        assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)
+    plan.close()
+
+
 def test_full_size_sphere_sampled(g, oracle_factors):
     """The 2M-point sphere at depth 6, p = 8, eps = 1e-7 (the benchmark
     workload, split6), every level, on sampled targets the oracle computes
@@ -295,6 +348,45 @@ def test_p10_parity_levels_batch(g, oracle_factors, torus_mid, precision):
         row += nb
 
 
+def test_autotune_keeps_parity_and_caches(g, oracle_factors, torus_mid, monkeypatch, tmp_path):
+    """kifmm_m2l_autotune on the p = 10 torus (four candidates: N chunk 144 or
+    80, round-robin or contiguous items): whatever it keeps, apply_levels still
+    matches the oracle; the choice is written to and read back from the JSON
+    cache file."""
+    import json
+
+    tree, qs = torus_mid
+    f = oracle_factors(10, 0.1, 1e-8)
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("KIFMM_M2L_AUTOTUNE_CACHE", str(cache))
+    plan = make_plan(g, 10, 1e-8, "split6", tree, range(2, 6))
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in range(2, 6)])).cuda()
+    res = plan.autotune(x_all, 2, 5, reps=2)
+    print("autotune", res)
+    assert not res["from_cache"] and res["core_ms"] > 0
+    assert res["n_chunk"] in (144, 80) and res["contiguous"] in (0, 1)
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 1 and list(entries.values())[0]["n_chunk"] == res["n_chunk"]
+    # every candidate is forced in turn through the cache file
+    key = list(entries)[0]
+    refs = {l: om.m2l_svd(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64)) for l in range(2, 6)}
+    for chunk in (144, 80):
+        for contig in (0, 1):
+            cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "core_ms": 1.0}\n}\n' % (key, chunk, contig))
+            got = plan.autotune(x_all, 2, 5, reps=1)
+            assert got["from_cache"] and (got["n_chunk"], got["contiguous"]) == (chunk, contig), got
+            out = plan.apply_levels(x_all, 2, 5).cpu().numpy()
+            plan.sync()
+            row = 0
+            for l in range(2, 6):
+                nb = tree.levels[l].shape[0]
+                err = rel(out[row:row + nb], refs[l])
+                print(f"autotune chunk {chunk} contiguous {contig} level {l}: rel L2 {err:.3e}")
+                assert err <= TOL["split6"], (chunk, contig, l, err)
+                row += nb
+    plan.close()
+
+
 def test_full_size_torus_p10_sampled(g, oracle_factors):
     """The 4,194,304-point torus at depth 6, p = 10, eps = 1e-8, split6, all
     levels in one batch, on sampled targets the oracle computes one by one."""
@@ -316,3 +408,71 @@ def test_full_size_torus_p10_sampled(g, oracle_factors):
         print(f"torus4m level {l}: sampled rel L2 {err:.3e}")
         assert err <= 1e-6, err
         row += nb
+
+
+def _ellipsoid_batch(n_inst, seed0=0):
+    """Small instances of the mixed batch: ellipsoids of uneven sizes, depth 3-5,
+    p in {6, 8, 10}, nrhs in {1, 2, 3}."""
+    rng = np.random.default_rng(seed0)
+    out = []
+    for i in range(n_inst):
+        n = int(np.exp(rng.uniform(np.log(5_000), np.log(60_000))))
+        axes = rng.uniform(0.5, 2.0, size=3)
+        depth = int(rng.integers(3, 6))
+        p = (6, 8, 10)[i % 3]
+        nrhs = int(rng.integers(1, 4))
+        pts = synth.points_ellipsoid(n, 2000 + i, axes)
+        out.append((p, depth, nrhs, synth.build_tree(pts, depth)))
+    return out
+
+
+def test_batch_matches_levels_and_graph_replay(g, oracle_factors):
+    """kifmm_m2l_apply_batch over instances of uneven sizes and three
+    operators (p = 6, 8, 10) against each instance's own batched-levels
+    apply, in eager and CUDA-graph mode, and one instance against the oracle."""
+    from paper_1211_2517_gb300 import apply_batch
+
+    inst = _ellipsoid_batch(9, 11)
+    plans = {p: g.M2LPlan(p, 1e-7, 0.1, "split6") for p in (6, 8, 10)}
+    items, refs = [], []
+    for i, (p, depth, nrhs, tree) in enumerate(inst):
+        plan = plans[p]
+        for l in range(2, depth + 1):
+            plan.set_level(l, tree.levels[l], tree.r0, instance=i)
+        nb = sum(tree.levels[l].shape[0] for l in range(2, depth + 1))
+        x = torch.from_numpy(synth.random_box_densities(nb, nrhs, plan.n, 3000 + i)).cuda()
+        items.append({"plan": plan, "instance": i, "level_lo": 2, "level_hi": depth, "x": x,
+                      "out": torch.zeros_like(x)})
+    for it in items:
+        refs.append(it["plan"].apply_levels(it["x"], 2, it["level_hi"], instance=it["instance"]))
+    torch.cuda.synchronize()
+    for use_graph in (False, True, True):  # eager; graph capture (eager result); graph replay
+        for it in items:
+            it["out"].fill_(float("nan"))
+        apply_batch(items, use_graph=use_graph)
+        torch.cuda.synchronize()
+        for it, ref in zip(items, refs):
+            err = float((it["out"] - ref).double().norm() / ref.double().norm())
+            assert err < 1e-6, (use_graph, err)
+    # accumulate: beta = 1 doubles the result
+    for it in items:
+        it["beta"] = 1.0
+    apply_batch(items)
+    torch.cuda.synchronize()
+    for it, ref in zip(items, refs):
+        err = float((it["out"] - 2 * ref).double().norm() / (2 * ref).double().norm())
+        assert err < 1e-6, err
+    # one p = 8 instance against the oracle, level by level
+    i8 = next(i for i, c in enumerate(inst) if c[0] == 8)
+    p, depth, nrhs, tree = inst[i8]
+    f = oracle_factors(8, 0.1, 1e-7)
+    o = refs[i8].cpu().numpy()
+    x = items[i8]["x"].cpu().numpy().astype(np.float64)
+    row = 0
+    for l in range(2, depth + 1):
+        nb = tree.levels[l].shape[0]
+        ref = om.m2l_svd(tree.levels[l], l, tree.r0, f, x[row:row + nb])
+        assert rel(o[row:row + nb], ref) <= 1e-6
+        row += nb
+    for pl in plans.values():
+        pl.close()
