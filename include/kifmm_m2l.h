@@ -256,11 +256,15 @@ int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
 
 /* The choice kifmm_m2l_autotune kept: n_chunk = N columns of K~_o per core
  * work item, contiguous = 1 if each CTA takes one contiguous run of work
- * items (0: items dealt round-robin), core_ms = the core launch's mean time
- * (ms) under that choice, from_cache = 1 if read back from the cache file. */
+ * items (0: items dealt round-robin), resident = 1 if the core keeps each
+ * tile's rows of q~ in shared memory and streams K~_o in column blocks
+ * (split6 plans; n_chunk then does not apply), core_ms = the core launch's
+ * mean time (ms) under that choice, from_cache = 1 if read back from the
+ * cache file. */
 typedef struct kifmm_m2l_tune_result {
     int n_chunk;
     int contiguous;
+    int resident;
     double core_ms;
     int from_cache;
 } kifmm_m2l_tune_result;

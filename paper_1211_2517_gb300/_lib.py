@@ -42,8 +42,8 @@ class Params(ctypes.Structure):
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("n_chunk", ctypes.c_int), ("contiguous", ctypes.c_int), ("core_ms", ctypes.c_double),
-                ("from_cache", ctypes.c_int)]
+    _fields_ = [("n_chunk", ctypes.c_int), ("contiguous", ctypes.c_int), ("resident", ctypes.c_int),
+                ("core_ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):

@@ -193,6 +193,7 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
         a.contiguous = plan->tune_contig;
+        a.core_resident = plan->tune_resident;
         a.row_src = g.tiles.row_src.ptr;
         a.row_dst = g.tiles.row_dst.ptr;
         a.tile_k = g.tiles.tile_k.ptr;

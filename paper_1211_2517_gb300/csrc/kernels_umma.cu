@@ -39,6 +39,7 @@
 
 #include <cstdint>
 #include <map>
+#include <type_traits>
 #include <mutex>
 
 #include "kernels.h"
@@ -107,8 +108,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false on timeout / abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Smem* sm, int* err) {
+// Bounded wait: true when the phase completed, false on timeout / abort
+// (SM: the kernel's barrier block, which holds the CTA's abort flag).
+template <class SM>
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, SM* sm, int* err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
@@ -229,8 +232,6 @@ struct Layout {
     uint32_t a_bytes, c_bytes, stage_bytes, trans_off;
 };
 
-// Product table (a piece, b piece), smallest terms first; (0,0) last.
-__constant__ int8_t kProd[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
 
 constexpr int kTransStride = 36;  // floats per row of the epilogue transpose buffer (16-byte rows, no bank conflicts)
 constexpr int kMaxRowsChunk = 64; // N per work item of the rows modes (partial sums live in registers)
@@ -262,7 +263,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* stage_base = smem_raw + 1024;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int S = L.stages;
-    const int p0 = 6 - args.n_products;  // first entry of kProd used
     constexpr int CH = chunk_of(AMODE);  // K elements per stage
     constexpr int RB = CH * 2;           // bytes per shared-memory row
     const int KC = L.kc_count;
@@ -471,76 +471,99 @@ __global__ void __launch_bounds__(kThreads, 1)
         // one of two ping-pong partial slots that the epilogue drains into
         // FP32 registers (no accumulator chain is longer than 4 MMA steps);
         // the small products accumulate over the item in a lo slot.
+        // One thread issues at the tensor pipe's own rate only if its
+        // instruction stream between MMAs is a few integer adds: the product
+        // table is a compile-time constant (NP = n_products), descriptors are
+        // advanced by adding 16-byte offsets to one base descriptor, and the
+        // ring position is kept incrementally.
         if (lane == 0) {
-            int it = 0, tcount = 0, pcount = 0;
-            bool ok = true;
-            for (int item = i_beg; item < i_end && ok; item += i_step, ++tcount) {
-                const int acc = tcount % L.n_acc;
-                const uint32_t aph = (uint32_t)(tcount / L.n_acc) & 1u;
-                if (!mbar_wait(&sm->tmem_empty[acc], aph ^ 1u, sm, args.error_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const int nthis = item_nthis(item);
-                const int nA = nthis <= 256 ? nthis : ((nthis / 2 + 15) / 16) * 16;
-                const int nB = nthis - nA;
-                const uint32_t idA = umma_idesc_bf16(nA), idB = nB > 0 ? umma_idesc_bf16(nB) : 0u;
-                uint32_t d_hi, d_lo;
-                if (AMODE == A_ROWS) {
-                    // columns: part[0], part[1], lo[0], lo[1], each n_chunk wide
-                    d_lo = tmem + (uint32_t)((2 + acc) * args.n_chunk);
-                    d_hi = d_lo;  // set per K-chunk
-                } else {
-                    d_hi = tmem + (uint32_t)(acc * L.acc_cols);
-                    d_lo = args.hilo ? d_hi + (uint32_t)args.n_chunk : d_hi;
-                }
-                bool first_hi = true, first_lo = true;
-                int ps = 0;
-                for (int kc = 0; kc < KC; ++kc, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (uint32_t)(it / S) & 1u;
-                    if (AMODE == A_ROWS && kc % kPartChunks == 0) {
-                        ps = pcount % 2;
-                        const uint32_t pph = (uint32_t)(pcount / 2) & 1u;
-                        if (!mbar_wait(&sm->part_empty[ps], pph ^ 1u, sm, args.error_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        d_hi = tmem + (uint32_t)(ps * args.n_chunk);
-                        first_hi = true;
-                    }
-                    if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag)) {
+            auto run = [&](auto np_tag) {
+                constexpr int NP = decltype(np_tag)::value;
+                constexpr int P0 = 6 - NP;
+                const uint64_t desc0 = umma_desc<CH>(smem_u32(stage_base));
+                const uint32_t stage_u = L.stage_bytes >> 4, a_u = L.a_bytes >> 4, c_u = L.c_bytes >> 4;
+                const uint32_t c0_u = (uint32_t)L.na * a_u;
+                const bool split_lo = AMODE == A_ROWS || args.hilo;
+                int s = 0, tcount = 0, pcount = 0;
+                uint32_t ph = 0;
+                bool ok = true;
+                for (int item = i_beg; item < i_end && ok; item += i_step, ++tcount) {
+                    const int acc = L.n_acc == 2 ? (tcount & 1) : 0;
+                    const uint32_t aph = (uint32_t)(L.n_acc == 2 ? (tcount >> 1) : tcount) & 1u;
+                    if (!mbar_wait(&sm->tmem_empty[acc], aph ^ 1u, sm, args.error_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const int ksteps = min(CH, args.kdim - kc * CH) / 16;
-                    for (int pi = p0; pi < 6; ++pi) {
-                        const bool big = kProd[pi][0] == 0 && kProd[pi][1] == 0;
-                        const bool to_hi = big || !(args.hilo || AMODE == A_ROWS);
-                        const uint32_t d = to_hi ? d_hi : d_lo;
-                        const uint32_t abase = a_smem(s, kProd[pi][0]);
-                        const uint32_t cbase = c_smem(s, kProd[pi][1]);
-                        for (int ks = 0; ks < ksteps; ++ks) {
-                            bool& first = to_hi ? first_hi : first_lo;
-                            const uint64_t ad = umma_desc<CH>(abase + ks * 32);
-                            umma_bf16(d, ad, umma_desc<CH>(cbase + ks * 32), idA, first ? 0u : 1u);
-                            if (nB > 0)
-                                umma_bf16(d + (uint32_t)nA, ad, umma_desc<CH>(cbase + (uint32_t)nA * RB + ks * 32),
-                                          idB, first ? 0u : 1u);
-                            first = false;
+                    const int nthis = item_nthis(item);
+                    const int nA = nthis <= 256 ? nthis : ((nthis / 2 + 15) / 16) * 16;
+                    const int nB = nthis - nA;
+                    const uint32_t idA = umma_idesc_bf16(nA), idB = nB > 0 ? umma_idesc_bf16(nB) : 0u;
+                    const uint32_t nB_off = (uint32_t)(nA * RB) >> 4;
+                    uint32_t d_hi, d_lo;
+                    if (AMODE == A_ROWS) {
+                        // columns: part[0], part[1], lo[0], lo[1], each n_chunk wide
+                        d_lo = tmem + (uint32_t)((2 + acc) * args.n_chunk);
+                        d_hi = d_lo;  // set per K-chunk
+                    } else {
+                        d_hi = tmem + (uint32_t)(acc * L.acc_cols);
+                        d_lo = args.hilo ? d_hi + (uint32_t)args.n_chunk : d_hi;
+                    }
+                    bool hi_on = false, lo_on = false;  // accumulate into the slot (false: overwrite)
+                    int ps = 0;
+                    for (int kc = 0; kc < KC; ++kc) {
+                        if (AMODE == A_ROWS && kc % kPartChunks == 0) {
+                            ps = pcount & 1;
+                            const uint32_t pph = (uint32_t)(pcount >> 1) & 1u;
+                            if (!mbar_wait(&sm->part_empty[ps], pph ^ 1u, sm, args.error_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            d_hi = tmem + (uint32_t)(ps * args.n_chunk);
+                            hi_on = false;
+                        }
+                        if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const bool two = args.kdim - kc * CH >= 32;  // K steps of 16 in this chunk: 2 or 1
+                        const uint64_t sd = desc0 + (uint64_t)((uint32_t)s * stage_u);
+#pragma unroll
+                        for (int pi = P0; pi < 6; ++pi) {
+                            constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
+                            const bool big = kA[pi] == 0 && kB[pi] == 0;
+                            const bool to_hi = big || !split_lo;
+                            const uint32_t d = to_hi ? d_hi : d_lo;
+                            const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
+                            const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
+                            const uint32_t en0 = (to_hi ? hi_on : lo_on) ? 1u : 0u;
+                            umma_bf16(d, ad, bd, idA, en0);
+                            if (nB > 0) umma_bf16(d + (uint32_t)nA, ad, bd + nB_off, idB, en0);
+                            if (two) {
+                                umma_bf16(d, ad + 2, bd + 2, idA, 1u);
+                                if (nB > 0) umma_bf16(d + (uint32_t)nA, ad + 2, bd + nB_off + 2, idB, 1u);
+                            }
+                            if (to_hi) hi_on = true;
+                            else lo_on = true;
+                        }
+                        umma_commit(&sm->empty[s]);
+                        if (AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) {
+                            umma_commit(&sm->part_full[ps]);
+                            ++pcount;
+                        }
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
                         }
                     }
-                    umma_commit(&sm->empty[s]);
-                    if (AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) {
-                        umma_commit(&sm->part_full[ps]);
-                        ++pcount;
-                    }
+                    if (!ok) break;
+                    umma_commit(&sm->tmem_full[acc]);
                 }
-                if (!ok) break;
-                umma_commit(&sm->tmem_full[acc]);
-            }
+            };
+            if (args.n_products == 1) run(std::integral_constant<int, 1>{});
+            else if (args.n_products == 3) run(std::integral_constant<int, 3>{});
+            else run(std::integral_constant<int, 6>{});
             umma_commit(&sm->drain);
             const unsigned long long t0 = global_ns();
             while (!mbar_try_wait(&sm->drain, 0u) && global_ns() - t0 < kWaitNs) {
@@ -738,6 +761,316 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Core GEMM with the A tile resident in shared memory (split6 with hilo).
+//
+// With hilo, one 128-row tile needs 2 N TMEM columns (hi and lo); for
+// N = r_pad = 192 that is 384 of the 512 columns, so the classic kernel has
+// one accumulator slot and each tile's epilogue (bounded by the L2's
+// reduction rate) runs between two tiles' MMAs.  Here the A tile (all K,
+// 3 pieces: 144 KB for K = 192) stays in shared memory for the whole tile and
+// K~_o is streamed in NB column blocks of width BN <= 128: a block's hi and
+// lo take 2 BN columns, two blocks ping-pong in TMEM, and the epilogue of one
+// block overlaps the MMAs of the next.  Per output element the sums run in
+// the same order as in the classic kernel.
+//
+// Warp roles (384 threads):
+//   warps 0-3   epilogue (as in the classic kernel, per N block)
+//   warps 4-9   A producers: warp 4 + w gathers the K-chunks j = w (mod 6)
+//               of every tile into A slot j (cp.async, 64-byte swizzle)
+//   warp 10     B producer: one thread TMA-loads the (block, K-chunk) tiles
+//               of K~_o through a ring of SB slots
+//   warp 11     TMEM allocation and the MMA-issuing thread
+// A slot j is released (for the next tile) by the MMA commit that follows
+// the last block's use of it.
+constexpr int kResAWarps = 6, kResBWarp = 10, kResMmaWarp = 11;
+constexpr int kResMaxKC = 8, kResMaxSB = 4;
+
+struct RSmem {
+    uint64_t a_full[kResMaxKC], a_empty[kResMaxKC];
+    uint64_t b_full[kResMaxSB], b_empty[kResMaxSB];
+    uint64_t t_full[2], t_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort_flag;
+};
+
+struct RLayout {
+    int kc_count;            // K chunks of 32 = A slots
+    int nb, bn;              // N blocks, block width (last block may be narrower)
+    int sb;                  // B ring slots
+    int n_items;             // tiles
+    uint32_t b_off;          // B ring offset from the A region (= A bytes)
+    uint32_t b_piece_bytes;  // bn * 64
+    uint32_t trans_off;      // transpose buffers, from the A region
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    core_resident_kernel(const __grid_constant__ CUtensorMap bmap, const UmmaArgs args, const RLayout L) {
+    extern __shared__ __align__(1024) uint8_t smem_dyn[];
+    uint8_t* smem_raw = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+    RSmem* sm = reinterpret_cast<RSmem*>(smem_raw);
+    uint8_t* a_region = smem_raw + 1024;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int CH = 32, RB = 64;
+    constexpr uint32_t kAPiece = kTileM * CH * 2;  // 8 KB
+    const int KC = L.kc_count, NB = L.nb, BN = L.bn, SB = L.sb;
+    const bool contig = args.contiguous != 0;
+    const int i_beg = contig ? (int)((long)L.n_items * blockIdx.x / gridDim.x) : (int)blockIdx.x;
+    const int i_end = contig ? (int)((long)L.n_items * (blockIdx.x + 1) / gridDim.x) : L.n_items;
+    const int i_step = contig ? 1 : (int)gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < KC; ++j) {
+            mbar_init(&sm->a_full[j], 32);
+            mbar_init(&sm->a_empty[j], 1);
+        }
+        for (int b = 0; b < SB; ++b) {
+            mbar_init(&sm->b_full[b], 1);
+            mbar_init(&sm->b_empty[b], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&sm->t_full[a], 1);
+            mbar_init(&sm->t_empty[a], kEpiWarps * 32);
+        }
+        mbar_init(&sm->drain, 1);
+        sm->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kResMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(&sm->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+    auto a_slot = [&](int j, int piece) -> uint32_t {
+        return smem_u32(a_region + (size_t)(j * 3 + piece) * kAPiece);
+    };
+    auto b_slot = [&](int b, int piece) -> uint32_t {
+        return smem_u32(a_region + L.b_off + (size_t)(b * 3 + piece) * L.b_piece_bytes);
+    };
+
+    if (warp >= kEpiWarps && warp < kEpiWarps + kResAWarps) {
+        // ================= A producers =================
+        const int aw = warp - kEpiWarps;
+        constexpr int CPR = CH / 8, RPI = 32 / CPR, NR = kTileM / RPI;
+        const int cch = lane % CPR, rl = lane / CPR;
+        bool ok = true;
+        int ic = 0;
+        int nrow[NR];
+        if (aw < KC && i_beg < i_end) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) nrow[i] = __ldg(args.row_src + (long)i_beg * kTileM + rl + RPI * i);
+        }
+        for (int item = i_beg; item < i_end && ok && aw < KC; item += i_step, ++ic) {
+            const __nv_bfloat16* rowp[NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) rowp[i] = args.A + (long)(nrow[i] < 0 ? args.zero_row : nrow[i]) * args.kdim;
+            if (item + i_step < i_end) {
+#pragma unroll
+                for (int i = 0; i < NR; ++i)
+                    nrow[i] = __ldg(args.row_src + (long)(item + i_step) * kTileM + rl + RPI * i);
+            }
+            for (int j = aw; j < KC; j += kResAWarps) {
+                if (!mbar_wait(&sm->a_empty[j], (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag)) {
+                    ok = false;
+                    break;
+                }
+                const int col = j * CH + cch * 8;
+                const uint32_t bytes = col < args.kdim ? 16u : 0u;
+                const int colc = col < args.kdim ? col : 0;
+#pragma unroll
+                for (int pc = 0; pc < 3; ++pc) {
+                    const uint32_t sbase = a_slot(j, pc);
+                    const long poff = pc * args.a_piece_stride + colc;
+#pragma unroll
+                    for (int i = 0; i < NR; ++i) cp_async16(sbase + swz<CH>(rl + RPI * i, cch), rowp[i] + poff, bytes);
+                }
+                cp_async_commit();
+                cp_async_wait_0();
+                fence_proxy_async();
+                mbar_arrive(&sm->a_full[j]);
+            }
+        }
+        cp_async_wait_0();
+    } else if (warp == kResBWarp) {
+        // ================= B producer =================
+        if (lane == 0) {
+            int b = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int item = i_beg; item < i_end && ok; item += i_step) {
+                const int group = __ldg(args.tile_k + item) & 0xFFFF;
+                for (int nb = 0; nb < NB && ok; ++nb) {
+                    for (int kc = 0; kc < KC; ++kc) {
+                        if (!mbar_wait(&sm->b_empty[b], ph ^ 1u, sm, args.error_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&sm->b_full[b], 3u * L.b_piece_bytes);
+#pragma unroll
+                        for (int pc = 0; pc < 3; ++pc)
+                            tma_load_2d(b_slot(b, pc), &bmap, kc * CH, (pc * args.b_groups + group) * args.ndim + nb * BN,
+                                        &sm->b_full[b]);
+                        if (++b == SB) {
+                            b = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                const unsigned long long t0 = global_ns();
+                while (global_ns() - t0 < 1000000ull) {
+                }
+            }
+        }
+    } else if (warp == kResMmaWarp) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            const uint64_t adesc0 = umma_desc<CH>(a_slot(0, 0));
+            const uint64_t bdesc0 = umma_desc<CH>(b_slot(0, 0));
+            const uint32_t a_u = kAPiece >> 4, bp_u = L.b_piece_bytes >> 4;
+            int b = 0, bc = 0, ic = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int item = i_beg; item < i_end && ok; item += i_step, ++ic) {
+                for (int nb = 0; nb < NB && ok; ++nb, ++bc) {
+                    const int slot = bc & 1;
+                    if (!mbar_wait(&sm->t_empty[slot], (uint32_t)((bc >> 1) & 1) ^ 1u, sm, args.error_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int nthis = min(BN, args.ndim - nb * BN);
+                    const uint32_t idesc = umma_idesc_bf16(nthis);
+                    const uint32_t d_hi = tmem + (uint32_t)(slot * 2 * BN), d_lo = d_hi + (uint32_t)BN;
+                    bool hi_on = false, lo_on = false;
+                    for (int kc = 0; kc < KC; ++kc) {
+                        if (nb == 0 && !mbar_wait(&sm->a_full[kc], (uint32_t)(ic & 1), sm, args.error_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        if (!mbar_wait(&sm->b_full[b], ph, sm, args.error_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const bool two = args.kdim - kc * CH >= 32;
+                        const uint64_t ad = adesc0 + (uint64_t)((uint32_t)(kc * 3) * a_u);
+                        const uint64_t bd = bdesc0 + (uint64_t)((uint32_t)(b * 3) * bp_u);
+#pragma unroll
+                        for (int pi = 0; pi < 6; ++pi) {
+                            constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
+                            const bool to_hi = kA[pi] == 0 && kB[pi] == 0;
+                            const uint32_t d = to_hi ? d_hi : d_lo;
+                            const uint64_t pa = ad + (uint64_t)(kA[pi] * a_u), pb = bd + (uint64_t)(kB[pi] * bp_u);
+                            umma_bf16(d, pa, pb, idesc, (to_hi ? hi_on : lo_on) ? 1u : 0u);
+                            if (two) umma_bf16(d, pa + 2, pb + 2, idesc, 1u);
+                            if (to_hi) hi_on = true;
+                            else lo_on = true;
+                        }
+                        umma_commit(&sm->b_empty[b]);
+                        if (nb == NB - 1) umma_commit(&sm->a_empty[kc]);
+                        if (++b == SB) {
+                            b = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    umma_commit(&sm->t_full[slot]);
+                }
+            }
+            umma_commit(&sm->drain);
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&sm->drain, 0u) && global_ns() - t0 < kWaitNs) {
+            }
+        }
+        __syncwarp();
+    } else if (warp < kEpiWarps) {
+        // ================= epilogue =================
+        float* trans = reinterpret_cast<float*>(a_region + L.trans_off) + warp * 32 * kTransStride;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        int bc = 0;
+        int e_nxt_row = -1, e_nxt_k = 0;
+        if (i_beg < i_end) {
+            e_nxt_row = __ldg(args.row_dst + (long)i_beg * kTileM + warp * 32 + lane);
+            e_nxt_k = __ldg(args.tile_k + i_beg);
+        }
+        bool ok = true;
+        for (int item = i_beg; item < i_end && ok; item += i_step) {
+            const long orow = e_nxt_row;
+            const float oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
+                                                  : args.level_scale[(e_nxt_k >> 16) & 31];
+            if (item + i_step < i_end) {
+                e_nxt_row = __ldg(args.row_dst + (long)(item + i_step) * kTileM + warp * 32 + lane);
+                e_nxt_k = __ldg(args.tile_k + item + i_step);
+            }
+            long prow[8];
+#pragma unroll
+            for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
+            const int c4 = lane % 8;
+            for (int nb = 0; nb < NB; ++nb, ++bc) {
+                const int slot = bc & 1;
+                const bool got = mbar_wait(&sm->t_full[slot], (uint32_t)((bc >> 1) & 1), sm, args.error_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int nthis = min(BN, args.ndim - nb * BN);
+                const uint32_t col_hi = (uint32_t)(slot * 2 * BN), col_lo = col_hi + (uint32_t)BN;
+                for (int c = 0; c < nthis; c += 32) {
+                    uint32_t r[32], r2[32];
+                    const bool full32 = c + 32 <= nthis;
+                    if (full32) {
+                        tmem_ld32(tmem + lane_base + col_hi + (uint32_t)c, r);
+                        tmem_ld32(tmem + lane_base + col_lo + (uint32_t)c, r2);
+                    } else {
+                        tmem_ld16(tmem + lane_base + col_hi + (uint32_t)c, r);
+                        tmem_ld16(tmem + lane_base + col_lo + (uint32_t)c, r2);
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * q) = make_float4(
+                            __uint_as_float(r[4 * q]) + __uint_as_float(r2[4 * q]),
+                            __uint_as_float(r[4 * q + 1]) + __uint_as_float(r2[4 * q + 1]),
+                            __uint_as_float(r[4 * q + 2]) + __uint_as_float(r2[4 * q + 2]),
+                            __uint_as_float(r[4 * q + 3]) + __uint_as_float(r2[4 * q + 3]));
+                    __syncwarp();
+                    const int ncols = full32 ? 32 : 16;
+#pragma unroll
+                    for (int pass = 0; pass < 8; ++pass) {
+                        const int rr = pass * 4 + lane / 8;
+                        const long grow = prow[pass];
+                        if (grow < 0 || 4 * c4 >= ncols) continue;
+                        const float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
+                        red_add_v4(args.D + grow * args.ldd + nb * BN + c + 4 * c4, __float_as_uint(oscale * x.x),
+                                   __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
+                                   __float_as_uint(oscale * x.w));
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                mbar_arrive(&sm->t_empty[slot]);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kResMmaWarp) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -760,19 +1093,46 @@ EncodeTiledFn get_encode_fn() {
 // already granted to each kernel instantiation on each device, each device's
 // opt-in limit, and encoded tensor maps of the B operands.
 std::mutex g_cache_mutex;
-int g_smem_granted[3][64] = {};
+int g_smem_granted[4][64] = {};
 int g_max_smem[64] = {};
 struct MapKey {
     const void* ptr;
-    int rows, kdim, ch;
+    int rows, kdim, ch, box_rows;
     bool operator<(const MapKey& o) const {
         if (ptr != o.ptr) return ptr < o.ptr;
         if (rows != o.rows) return rows < o.rows;
         if (kdim != o.kdim) return kdim < o.kdim;
-        return ch < o.ch;
+        if (ch != o.ch) return ch < o.ch;
+        return box_rows < o.box_rows;
     }
 };
+
 std::map<MapKey, CUtensorMap> g_maps;
+
+// B pieces viewed as a 2D tensor [rows_total][kdim] of BF16, boxes of
+// ch x box_rows, 64-byte (ch = 32) or 32-byte (ch = 16) swizzle.
+cudaError_t get_bmap(const UmmaArgs& a, cuuint64_t rows_total, int ch, int box_rows, EncodeTiledFn encode,
+                     CUtensorMap* out) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    const MapKey key{a.B, (int)rows_total, a.kdim, ch, box_rows};
+    auto it = g_maps.find(key);
+    if (it != g_maps.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
+    const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)ch, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    CUresult cr = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim, gstride, box,
+                         estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (g_maps.size() > 256) g_maps.clear();
+    g_maps.emplace(key, *out);
+    return cudaSuccess;
+}
 
 template <int AM, int EM>
 cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L, size_t smem, int grid,
@@ -791,6 +1151,63 @@ cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L
     return cudaGetLastError();
 }
 
+// The A-resident core (split6 with hilo); cudaErrorNotSupported when the
+// A tile or the B ring does not fit in shared memory.
+cudaError_t launch_core_resident(const UmmaArgs& a, int num_sms, cudaStream_t stream, EncodeTiledFn encode) {
+    if (a.n_products != 6 || !a.hilo) return cudaErrorNotSupported;
+    const int KC = (a.kdim + 31) / 32;
+    if (KC > kResMaxKC) return cudaErrorNotSupported;
+    // N blocks: two slots of hi + lo (4 BN columns) fit in 512
+    int nb = 1, bn = (a.ndim + 15) / 16 * 16;
+    while (4 * bn > 512) {
+        ++nb;
+        bn = ((a.ndim + nb - 1) / nb + 15) / 16 * 16;
+    }
+    int dev = 0, max_smem = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return ce;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        if (!g_max_smem[dev]) {
+            ce = cudaDeviceGetAttribute(&g_max_smem[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (ce != cudaSuccess) return ce;
+        }
+        max_smem = g_max_smem[dev];
+    }
+    RLayout L{};
+    L.kc_count = KC;
+    L.nb = nb;
+    L.bn = bn;
+    L.n_items = a.n_tiles;
+    const uint32_t a_bytes = (uint32_t)KC * 3u * (uint32_t)(kTileM * 32 * 2);
+    const uint32_t trans_bytes = kEpiWarps * 32 * kTransStride * 4;
+    L.b_off = a_bytes;
+    L.b_piece_bytes = (uint32_t)bn * 64u;
+    const long avail = (long)max_smem - 2048 - (long)a_bytes - (long)trans_bytes;
+    int sb = (int)(avail / (long)(3u * L.b_piece_bytes));
+    if (sb > kResMaxSB) sb = kResMaxSB;
+    if (sb < 2) return cudaErrorNotSupported;
+    L.sb = sb;
+    L.trans_off = a_bytes + (uint32_t)sb * 3u * L.b_piece_bytes;
+    if (L.n_items <= 0) return cudaSuccess;
+    const size_t smem = 2048 + (size_t)L.trans_off + trans_bytes;
+    CUtensorMap bmap;
+    ce = get_bmap(a, (cuuint64_t)3 * a.b_groups * a.ndim, 32, bn, encode, &bmap);
+    if (ce != cudaSuccess) return ce;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        if (g_smem_granted[3][dev] < (int)smem) {
+            ce = cudaFuncSetAttribute(core_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (ce != cudaSuccess) return ce;
+            g_smem_granted[3][dev] = (int)smem;
+        }
+    }
+    const int grid = num_sms < L.n_items ? num_sms : L.n_items;
+    core_resident_kernel<<<grid, kThreads, smem, stream>>>(bmap, a, L);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cudaStream_t stream) {
@@ -805,6 +1222,10 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (a.ldd % 4 != 0) return cudaErrorInvalidValue;
     EncodeTiledFn encode = get_encode_fn();
     if (!encode) return cudaErrorNotSupported;
+    if (gather && a.core_resident) {
+        const cudaError_t e = launch_core_resident(a, num_sms, stream, encode);
+        if (e != cudaErrorNotSupported) return e;
+    }
 
     Layout L{};
     L.na = a.n_products == 1 ? 1 : (a.n_products == 3 ? 2 : 3);
@@ -856,27 +1277,8 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
 
     // B pieces viewed as a 2D tensor [pieces * b_groups * ndim rows][kdim]
     CUtensorMap bmap;
-    const cuuint64_t rows_total = (cuuint64_t)L.nc * a.b_groups * a.ndim;
-    {
-        std::lock_guard<std::mutex> lock(g_cache_mutex);
-        const MapKey key{a.B, (int)rows_total, a.kdim, ch};
-        auto it = g_maps.find(key);
-        if (it != g_maps.end()) {
-            bmap = it->second;
-        } else {
-            const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
-            const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
-            const cuuint32_t box[2] = {(cuuint32_t)ch, (cuuint32_t)kCBoxRows};
-            const cuuint32_t estride[2] = {1, 1};
-            CUresult cr = encode(&bmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim,
-                                 gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                 ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-            if (g_maps.size() > 256) g_maps.clear();
-            g_maps.emplace(key, bmap);
-        }
-    }
+    ce = get_bmap(a, (cuuint64_t)L.nc * a.b_groups * a.ndim, ch, kCBoxRows, encode, &bmap);
+    if (ce != cudaSuccess) return ce;
 
     const int grid = num_sms < L.n_items ? num_sms : L.n_items;
     if (gather) return launch_t<A_GATHER, E_RED>(bmap, a, L, smem, grid, stream, dev);

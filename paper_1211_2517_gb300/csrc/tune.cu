@@ -11,6 +11,10 @@
 //   n_chunk      the plan's default N per item, or half of it (more, smaller
 //                items: better balance, but every A row is gathered once per
 //                N part).
+//   resident     split6 only: the core variant that keeps each tile's A rows
+//                in shared memory and streams K~_o in column blocks, so that
+//                the epilogue of one block overlaps the MMAs of the next (its
+//                N per item is the whole row; n_chunk does not apply).
 // Each candidate is timed with CUDA events around the core launch of
 // kifmm_m2l_apply_levels.  With $KIFMM_M2L_AUTOTUNE_CACHE naming a file,
 // results are kept there as a JSON object keyed by operator, device and
@@ -51,7 +55,7 @@ std::string tune_key(kifmm_m2l_plan plan, const MultiState* ms, int nrhs, int lo
 }
 
 // The cache file holds one entry per line:
-//   "<key>": {"n_chunk": N, "contiguous": C, "core_ms": T},
+//   "<key>": {"n_chunk": N, "contiguous": C, "resident": R, "core_ms": T},
 // inside one pair of braces, so that it is a JSON object.
 std::map<std::string, std::string> read_cache(const char* path) {
     std::map<std::string, std::string> out;
@@ -70,14 +74,16 @@ std::map<std::string, std::string> read_cache(const char* path) {
     return out;
 }
 
-bool parse_entry(const std::string& v, int* chunk, int* contig, double* ms) {
+bool parse_entry(const std::string& v, int* chunk, int* contig, int* resident, double* ms) {
     const char* s = v.c_str();
     const char* pc = std::strstr(s, "\"n_chunk\":");
     const char* pg = std::strstr(s, "\"contiguous\":");
+    const char* pr = std::strstr(s, "\"resident\":");
     const char* pm = std::strstr(s, "\"core_ms\":");
-    if (!pc || !pg || !pm) return false;
+    if (!pc || !pg || !pr || !pm) return false;
     *chunk = std::atoi(pc + 10);
     *contig = std::atoi(pg + 13);
+    *resident = std::atoi(pr + 11);
     *ms = std::atof(pm + 10);
     return true;
 }
@@ -126,61 +132,71 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         const auto entries = read_cache(path);
         auto it = entries.find(key);
-        int c = 0, g = 0;
+        int c = 0, g = 0, rs = 0;
         double t = 0;
-        if (it != entries.end() && parse_entry(it->second, &c, &g, &t) && c >= 16 && c % 16 == 0 && c <= 512 &&
-            (g == 0 || g == 1)) {
-            plan->tune_chunk = c;
+        if (it != entries.end() && parse_entry(it->second, &c, &g, &rs, &t) && c >= 16 && c % 16 == 0 &&
+            c <= 512 && (g == 0 || g == 1) && (rs == 0 || rs == 1)) {
+            plan->tune_chunk = c == core_chunk_default(plan) ? 0 : c;
             plan->tune_contig = g;
-            if (result) *result = {c, g, t, 1};
+            plan->tune_resident = rs;
+            if (result) *result = {c, g, rs, t, 1};
             return KIFMM_OK;
         }
     }
 
-    // candidates
+    // candidates (n_chunk, contiguous, resident)
+    struct Cand {
+        int chunk, contig, resident;
+    };
     const int c0 = core_chunk_default(plan);
-    std::vector<int> chunks{c0};
     const int c1 = (c0 / 2 + 15) / 16 * 16;
-    if (c1 >= 16 && c1 < c0) chunks.push_back(c1);
+    std::vector<Cand> cands;
+    for (int g = 0; g < 2; ++g) {
+        if (plan->core_hilo) cands.push_back({c0, g, 1});
+        cands.push_back({c0, g, 0});
+        if (c1 >= 16 && c1 < c0) cands.push_back({c1, g, 0});
+    }
     const bool was_profiling = plan->profile;
     kifmm_m2l_profile_read(plan, nullptr, nullptr);  // drop pending records
     plan->profile = true;
     double best = 1e300;
-    int best_c = c0, best_g = 0;
+    Cand bestc = cands[0];
     st = KIFMM_OK;
-    for (int c : chunks) {
-        for (int g = 0; g < 2 && st == KIFMM_OK; ++g) {
-            plan->tune_chunk = c;
-            plan->tune_contig = g;
-            // one untimed pass (tile tables, first launch), then reps timed ones
+    for (const Cand& cd : cands) {
+        if (st != KIFMM_OK) break;
+        plan->tune_chunk = cd.chunk == c0 ? 0 : cd.chunk;
+        plan->tune_contig = cd.contig;
+        plan->tune_resident = cd.resident;
+        // one untimed pass (tile tables, first launch), then reps timed ones
+        st = kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, 0.0f, stream);
+        if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, nullptr, nullptr);
+        for (int r = 0; r < reps && st == KIFMM_OK; ++r)
             st = kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, 0.0f, stream);
-            if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, nullptr, nullptr);
-            for (int r = 0; r < reps && st == KIFMM_OK; ++r)
-                st = kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, 0.0f, stream);
-            double t[3] = {0, 0, 0};
-            if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, t, nullptr);
-            if (st == KIFMM_OK) st = kifmm_m2l_sync(plan, stream);
-            if (st == KIFMM_OK && t[1] / reps < best) {
-                best = t[1] / reps;
-                best_c = c;
-                best_g = g;
-            }
+        double t[3] = {0, 0, 0};
+        if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, t, nullptr);
+        if (st == KIFMM_OK) st = kifmm_m2l_sync(plan, stream);
+        if (st == KIFMM_OK && t[1] / reps < best) {
+            best = t[1] / reps;
+            bestc = cd;
         }
     }
     plan->profile = was_profiling;
     if (st != KIFMM_OK) {
         plan->tune_chunk = 0;
         plan->tune_contig = 0;
+        plan->tune_resident = 1;
         return st;
     }
-    plan->tune_chunk = best_c == c0 ? 0 : best_c;
-    plan->tune_contig = best_g;
-    if (result) *result = {best_c, best_g, best, 0};
+    plan->tune_chunk = bestc.chunk == c0 ? 0 : bestc.chunk;
+    plan->tune_contig = bestc.contig;
+    plan->tune_resident = bestc.resident;
+    if (result) *result = {bestc.chunk, bestc.contig, bestc.resident, best, 0};
     if (path && *path) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto entries = read_cache(path);
-        char v[128];
-        std::snprintf(v, sizeof(v), "{\"n_chunk\": %d, \"contiguous\": %d, \"core_ms\": %.6f}", best_c, best_g, best);
+        char v[160];
+        std::snprintf(v, sizeof(v), "{\"n_chunk\": %d, \"contiguous\": %d, \"resident\": %d, \"core_ms\": %.6f}",
+                      bestc.chunk, bestc.contig, bestc.resident, best);
         entries[key] = v;
         if (write_cache(path, entries) != 0) {
             set_error(std::string("could not write the autotune cache ") + path);

@@ -209,8 +209,8 @@ class M2LPlan:
         call("kifmm_m2l_autotune", self._h, int(instance), int(level_lo), int(level_hi), int(nrhs),
              ctypes.c_void_p(x_all.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(reps), ctypes.byref(res),
              _stream_handle(stream))
-        return {"n_chunk": res.n_chunk, "contiguous": res.contiguous, "core_ms": res.core_ms,
-                "from_cache": bool(res.from_cache)}
+        return {"n_chunk": res.n_chunk, "contiguous": res.contiguous, "resident": res.resident,
+                "core_ms": res.core_ms, "from_cache": bool(res.from_cache)}
 
     def sync(self, stream=None) -> None:
         """Synchronise the stream and raise on device-side failures."""
