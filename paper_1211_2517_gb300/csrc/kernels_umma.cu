@@ -529,23 +529,37 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tc_fence_after();
                         const bool two = args.kdim - kc * CH >= 32;  // K steps of 16 in this chunk: 2 or 1
                         const uint64_t sd = desc0 + (uint64_t)((uint32_t)s * stage_u);
+                        constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
+                        if (two && nB == 0) {
+                            // common case, kept free of branches between the MMAs
 #pragma unroll
-                        for (int pi = P0; pi < 6; ++pi) {
-                            constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
-                            const bool big = kA[pi] == 0 && kB[pi] == 0;
-                            const bool to_hi = big || !split_lo;
-                            const uint32_t d = to_hi ? d_hi : d_lo;
-                            const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
-                            const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
-                            const uint32_t en0 = (to_hi ? hi_on : lo_on) ? 1u : 0u;
-                            umma_bf16(d, ad, bd, idA, en0);
-                            if (nB > 0) umma_bf16(d + (uint32_t)nA, ad, bd + nB_off, idB, en0);
-                            if (two) {
+                            for (int pi = P0; pi < 6; ++pi) {
+                                const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !split_lo;
+                                const uint32_t d = to_hi ? d_hi : d_lo;
+                                const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
+                                const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
+                                umma_bf16(d, ad, bd, idA, (to_hi ? hi_on : lo_on) ? 1u : 0u);
                                 umma_bf16(d, ad + 2, bd + 2, idA, 1u);
-                                if (nB > 0) umma_bf16(d + (uint32_t)nA, ad + 2, bd + nB_off + 2, idB, 1u);
+                                hi_on = hi_on || to_hi;
+                                lo_on = lo_on || !to_hi;
                             }
-                            if (to_hi) hi_on = true;
-                            else lo_on = true;
+                        } else {
+#pragma unroll
+                            for (int pi = P0; pi < 6; ++pi) {
+                                const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !split_lo;
+                                const uint32_t d = to_hi ? d_hi : d_lo;
+                                const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
+                                const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
+                                const uint32_t en0 = (to_hi ? hi_on : lo_on) ? 1u : 0u;
+                                umma_bf16(d, ad, bd, idA, en0);
+                                if (nB > 0) umma_bf16(d + (uint32_t)nA, ad, bd + nB_off, idB, en0);
+                                if (two) {
+                                    umma_bf16(d, ad + 2, bd + 2, idA, 1u);
+                                    if (nB > 0) umma_bf16(d + (uint32_t)nA, ad + 2, bd + nB_off + 2, idB, 1u);
+                                }
+                                hi_on = hi_on || to_hi;
+                                lo_on = lo_on || !to_hi;
+                            }
                         }
                         umma_commit(&sm->empty[s]);
                         if (AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) {
@@ -964,16 +978,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const bool two = args.kdim - kc * CH >= 32;
                         const uint64_t ad = adesc0 + (uint64_t)((uint32_t)(kc * 3) * a_u);
                         const uint64_t bd = bdesc0 + (uint64_t)((uint32_t)(b * 3) * bp_u);
+                        constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
+                        if (two) {
+                            // common case, kept free of branches between the MMAs
 #pragma unroll
-                        for (int pi = 0; pi < 6; ++pi) {
-                            constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
-                            const bool to_hi = kA[pi] == 0 && kB[pi] == 0;
-                            const uint32_t d = to_hi ? d_hi : d_lo;
-                            const uint64_t pa = ad + (uint64_t)(kA[pi] * a_u), pb = bd + (uint64_t)(kB[pi] * bp_u);
-                            umma_bf16(d, pa, pb, idesc, (to_hi ? hi_on : lo_on) ? 1u : 0u);
-                            if (two) umma_bf16(d, pa + 2, pb + 2, idesc, 1u);
-                            if (to_hi) hi_on = true;
-                            else lo_on = true;
+                            for (int pi = 0; pi < 6; ++pi) {
+                                const bool to_hi = kA[pi] == 0 && kB[pi] == 0;
+                                const uint32_t d = to_hi ? d_hi : d_lo;
+                                const uint64_t pa = ad + (uint64_t)(kA[pi] * a_u), pb = bd + (uint64_t)(kB[pi] * bp_u);
+                                umma_bf16(d, pa, pb, idesc, (to_hi ? hi_on : lo_on) ? 1u : 0u);
+                                umma_bf16(d, pa + 2, pb + 2, idesc, 1u);
+                                if (to_hi) hi_on = true;
+                                else lo_on = true;
+                            }
+                        } else {
+#pragma unroll
+                            for (int pi = 0; pi < 6; ++pi) {
+                                const bool to_hi = kA[pi] == 0 && kB[pi] == 0;
+                                const uint32_t d = to_hi ? d_hi : d_lo;
+                                const uint64_t pa = ad + (uint64_t)(kA[pi] * a_u), pb = bd + (uint64_t)(kB[pi] * bp_u);
+                                umma_bf16(d, pa, pb, idesc, (to_hi ? hi_on : lo_on) ? 1u : 0u);
+                                if (to_hi) hi_on = true;
+                                else lo_on = true;
+                            }
                         }
                         umma_commit(&sm->b_empty[b]);
                         if (nb == NB - 1) umma_commit(&sm->a_empty[kc]);
