@@ -330,8 +330,9 @@ def run_ours(args, rank, world, local_rank):
     roofline = {
         "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
         "frac": achieved / bf16_peak, "traffic": traffic,
-        "kernel": ("core_resident_kernel (A-resident split6 core, K~_o in column blocks)"
-                   if tune and tune.get("resident") else "umma_kernel<A_GATHER,E_RED> (offset-grouped core)"),
+        "kernel": {1: "core_resident_kernel (A-resident split6 core, K~_o in column blocks)",
+                   2: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, per-K-chunk partials drained)"}.get(
+                       (tune or {}).get("variant"), "umma_kernel<A_GATHER,E_RED> (offset-grouped core)"),
         "algorithmic_flops_per_step": flops_step,
         "flops_per_unit": f"2 r^2 = {2 * r * r} per box pair (r = {r})",
         "launches_per_step": 1,
@@ -378,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": dict(workload_desc(total_pairs, r, rp, args.precision),
-                       core_variant=({k: tune[k] for k in ("n_chunk", "contiguous", "resident")} if tune else "default")),
+                       core_variant=({k: tune[k] for k in ("n_chunk", "contiguous", "variant")} if tune else "default")),
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,

@@ -256,24 +256,29 @@ int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
 
 /* The choice kifmm_m2l_autotune kept: n_chunk = N columns of K~_o per core
  * work item, contiguous = 1 if each CTA takes one contiguous run of work
- * items (0: items dealt round-robin), resident = 1 if the core keeps each
- * tile's rows of q~ in shared memory and streams K~_o in column blocks
- * (split6 plans; n_chunk then does not apply), core_ms = the core launch's
- * mean time (ms) under that choice, from_cache = 1 if read back from the
- * cache file. */
+ * items (0: items dealt round-robin), variant = the split6 core variant
+ * (0: hi and lo accumulators per tile, epilogue after the tile's MMAs;
+ * 1: each tile's rows of q~ resident in shared memory, K~_o streamed in
+ * column blocks, n_chunk then does not apply; 2 / 3: partial sums of
+ * two / one K-chunks drained into registers while the next partial's MMAs
+ * run; other precisions: 0), core_ms = the core launch's mean time (ms) under that
+ * choice, from_cache = 1 if read back from the cache file. */
 typedef struct kifmm_m2l_tune_result {
     int n_chunk;
     int contiguous;
-    int resident;
+    int variant;
     double core_ms;
     int from_cache;
 } kifmm_m2l_tune_result;
 
 /* Tile autotuner of the core GEMM (Step 3.1's per-offset products, on the
  * tensor cores).  The paper fixes no launch shape; the candidates here
- * change only how the core's (tile, N-chunk) work items are spread over the
- * persistent CTAs, never the arithmetic of an output element (atomic
- * accumulation order aside, which is never fixed).  Runs
+ * change how the core's work is tiled and spread over the persistent CTAs
+ * (N per work item, round-robin or contiguous work) and, for split6, where
+ * partial sums are kept (the three variants above).  The piece products
+ * are the same for every candidate; the split6 variants differ in how the
+ * FP32 partial sums are grouped (each stays within the split6 tolerance),
+ * the others only in atomic accumulation order, which is never fixed.  Runs
  * kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up,
  * p_down, beta = 0, stream) once plus `reps` times (1 <= reps <= 1000) per
  * candidate, times the core launch with CUDA events, keeps the fastest in

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("n_chunk", ctypes.c_int), ("contiguous", ctypes.c_int), ("resident", ctypes.c_int),
+    _fields_ = [("n_chunk", ctypes.c_int), ("contiguous", ctypes.c_int), ("variant", ctypes.c_int),
                 ("core_ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
 
 

@@ -214,7 +214,8 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
         a.contiguous = plan->tune_contig;
-        a.core_resident = plan->tune_resident;
+        a.core_resident = plan->tune_variant == 1;
+        a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
         a.row_src = ts->row_src.ptr;
         a.row_dst = ts->row_dst.ptr;
         a.tile_k = ts->tile_k.ptr;
@@ -378,7 +379,8 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
         a.contiguous = plan->tune_contig;
-        a.core_resident = plan->tune_resident;
+        a.core_resident = plan->tune_variant == 1;
+        a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
         a.row_src = ts->row_src.ptr;
         a.row_dst = ts->row_dst.ptr;
         a.tile_k = ts->tile_k.ptr;

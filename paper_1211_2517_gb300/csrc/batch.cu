@@ -193,7 +193,8 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
         a.contiguous = plan->tune_contig;
-        a.core_resident = plan->tune_resident;
+        a.core_resident = plan->tune_variant == 1;
+        a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
         a.row_src = g.tiles.row_src.ptr;
         a.row_dst = g.tiles.row_dst.ptr;
         a.tile_k = g.tiles.tile_k.ptr;

@@ -97,6 +97,7 @@ struct UmmaArgs {
     int seg_tiles;            // rows modes with segments: total virtual row tiles
     int contiguous;           // core: 1 = each CTA takes a contiguous run of tiles
     int core_resident;        // core, split6 with hilo: 1 = A tile resident in shared memory, K~_o in N blocks
+    int core_drain;           // core, split6: K-chunks per partial drained into registers by 8 epilogue warps (0: off)
     // epilogue
     float* D;                 // E_RED / E_STORE: FP32 [*][ldd]
     int ldd;

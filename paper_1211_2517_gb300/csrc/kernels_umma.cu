@@ -229,6 +229,7 @@ __device__ __forceinline__ uint32_t swz(int m, int c) {
 struct Layout {
     int stages, na, nc, c_rows_alloc, n_acc, acc_cols, n_items, n_chunks, kc_count;
     int prod_warps;  // A_GATHER: producer warps in use; divides `stages`
+    int drain;       // A_GATHER: K-chunks per partial drained by 8 epilogue warps (0: no drain; see the epilogue)
     uint32_t a_bytes, c_bytes, stage_bytes, trans_off;
 };
 
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&sm->tmem_full[a], 1);
             mbar_init(&sm->tmem_empty[a], kEpiWarps * 32);
             mbar_init(&sm->part_full[a], 1);
-            mbar_init(&sm->part_empty[a], kEpiWarps * 32);
+            mbar_init(&sm->part_empty[a], (AMODE == A_GATHER && L.drain ? 2 : 1) * kEpiWarps * 32);
         }
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
@@ -323,7 +324,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto item_n0 = [&](int item) { return (item % n_chunks) * args.n_chunk; };
     auto item_nthis = [&](int item) { return min(args.n_chunk, args.ndim - item_n0(item)); };
 
-    if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
+    // drain mode: warps 7-10 (idle producers when at most 3 stages) are a
+    // second epilogue group
+    const bool epi2 = AMODE == A_GATHER && L.drain && warp >= kEpiWarps + 3 && warp < kEpiWarps + kProdWarps;
+    if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps && !epi2) {
         // ================= producers =================
         const int v = threadIdx.x - kEpiWarps * 32;  // 0..127
         const bool tma_thread = AMODE == A_GATHER ? (lane == 0) : (v == 0);
@@ -483,14 +487,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint64_t desc0 = umma_desc<CH>(smem_u32(stage_base));
                 const uint32_t stage_u = L.stage_bytes >> 4, a_u = L.a_bytes >> 4, c_u = L.c_bytes >> 4;
                 const uint32_t c0_u = (uint32_t)L.na * a_u;
-                const bool split_lo = AMODE == A_ROWS || args.hilo;
+                // drain (core): every product into one per-K-chunk partial
+                const bool drain = AMODE == A_GATHER && L.drain;
+                const bool split_lo = AMODE == A_ROWS || (args.hilo && !drain);
                 int s = 0, tcount = 0, pcount = 0;
                 uint32_t ph = 0;
                 bool ok = true;
                 for (int item = i_beg; item < i_end && ok; item += i_step, ++tcount) {
                     const int acc = L.n_acc == 2 ? (tcount & 1) : 0;
                     const uint32_t aph = (uint32_t)(L.n_acc == 2 ? (tcount >> 1) : tcount) & 1u;
-                    if (!mbar_wait(&sm->tmem_empty[acc], aph ^ 1u, sm, args.error_flag)) {
+                    if (!drain && !mbar_wait(&sm->tmem_empty[acc], aph ^ 1u, sm, args.error_flag)) {
                         ok = false;
                         break;
                     }
@@ -512,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     bool hi_on = false, lo_on = false;  // accumulate into the slot (false: overwrite)
                     int ps = 0;
                     for (int kc = 0; kc < KC; ++kc) {
-                        if (AMODE == A_ROWS && kc % kPartChunks == 0) {
+                        if ((AMODE == A_ROWS && kc % kPartChunks == 0) || (drain && kc % L.drain == 0)) {
                             ps = pcount & 1;
                             const uint32_t pph = (uint32_t)(pcount >> 1) & 1u;
                             if (!mbar_wait(&sm->part_empty[ps], pph ^ 1u, sm, args.error_flag)) {
@@ -520,6 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 break;
                             }
                             d_hi = tmem + (uint32_t)(ps * args.n_chunk);
+                            if (drain) d_lo = d_hi;
                             hi_on = false;
                         }
                         if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag)) {
@@ -562,7 +569,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                         umma_commit(&sm->empty[s]);
-                        if (AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) {
+                        if ((AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) ||
+                            (drain && (kc % L.drain == L.drain - 1 || kc == KC - 1))) {
                             umma_commit(&sm->part_full[ps]);
                             ++pcount;
                         }
@@ -572,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     if (!ok) break;
-                    umma_commit(&sm->tmem_full[acc]);
+                    if (!drain) umma_commit(&sm->tmem_full[acc]);
                 }
             };
             if (args.n_products == 1) run(std::integral_constant<int, 1>{});
@@ -584,6 +592,105 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
+    } else if (AMODE == A_GATHER && L.drain) {
+        // ================= epilogue, drain mode (core) =================
+        // Eight warps: warp w reads TMEM lane quarter w mod 4 and the 32-wide
+        // column chunks of its half of the item's N columns (warps 0-3 the
+        // first half, warps 7-10 the second).  Each partial (L.drain K-chunks
+        // of every product) is added to per-row FP32 running sums in
+        // registers (round to nearest), so no accumulator chain in TMEM is
+        // longer than L.drain K-chunks, and the MMAs run up to two partials
+        // ahead of the drains.  After the tile's last partial the sums are
+        // scaled by s_l and reduced into p~ as in the classic epilogue; the
+        // MMAs of the next tile fill the two partial slots meanwhile.
+        const int q = warp & 3;
+        const int half = warp < kEpiWarps ? 0 : 1;
+        const int ew = warp < kEpiWarps ? warp : warp - 3;
+        float* trans = reinterpret_cast<float*>(smem_raw + L.trans_off) + ew * 32 * kTransStride;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int pcount = 0;
+        int e_nxt_row = -1, e_nxt_k = 0;
+        if (i_beg < i_end) {
+            const int t0 = item_tile(i_beg);
+            e_nxt_row = __ldg(args.row_dst + (long)t0 * kTileM + q * 32 + lane);
+            e_nxt_k = __ldg(args.tile_k + t0);
+        }
+        bool ok = true;
+        for (int item = i_beg; item < i_end && ok; item += i_step) {
+            const long orow = e_nxt_row;
+            const float oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
+                                                  : args.level_scale[(e_nxt_k >> 16) & 31];
+            if (item + i_step < i_end) {
+                const int tn = item_tile(item + i_step);
+                e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + q * 32 + lane);
+                e_nxt_k = __ldg(args.tile_k + tn);
+            }
+            const int n0 = item_n0(item), nthis = item_nthis(item);
+            const int nch = (nthis + 31) / 32;
+            const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
+            float sums[96];
+#pragma unroll
+            for (int j = 0; j < 96; ++j) sums[j] = 0.f;
+            for (int kc = 0; kc < KC; kc += L.drain) {
+                const int ps = pcount & 1;
+                const bool got = mbar_wait(&sm->part_full[ps], (uint32_t)(pcount >> 1) & 1u, sm, args.error_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t pcol = (uint32_t)(ps * args.n_chunk);
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    const int c = (c_beg + jj) * 32;
+                    if (c_beg + jj < c_end) {
+                        uint32_t r[32];
+                        if (c + 32 <= nthis) {
+                            tmem_ld32(tmem + lane_base + pcol + (uint32_t)c, r);
+                        } else {
+                            tmem_ld16(tmem + lane_base + pcol + (uint32_t)c, r);
+#pragma unroll
+                            for (int j = 16; j < 32; ++j) r[j] = 0u;
+                        }
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) sums[jj * 32 + j] += __uint_as_float(r[j]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&sm->part_empty[ps]);
+                ++pcount;
+            }
+            if (!ok) break;
+            long prow[8];
+#pragma unroll
+            for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
+            const int c4 = lane % 8;
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+                const int c = (c_beg + jj) * 32;
+                if (c_beg + jj < c_end) {
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq)
+                        *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * qq) =
+                            make_float4(sums[jj * 32 + 4 * qq], sums[jj * 32 + 4 * qq + 1], sums[jj * 32 + 4 * qq + 2],
+                                        sums[jj * 32 + 4 * qq + 3]);
+                    __syncwarp();
+                    const int ncols = c + 32 <= nthis ? 32 : 16;
+#pragma unroll
+                    for (int pass = 0; pass < 8; ++pass) {
+                        const int rr = pass * 4 + lane / 8;
+                        const long grow = prow[pass];
+                        if (grow < 0 || 4 * c4 >= ncols) continue;
+                        const float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
+                        red_add_v4(args.D + grow * args.ldd + n0 + c + 4 * c4, __float_as_uint(oscale * x.x),
+                                   __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
+                                   __float_as_uint(oscale * x.w));
+                    }
+                    __syncwarp();
+                }
+            }
+        }
     } else {
         // ================= epilogue =================
         float* trans = reinterpret_cast<float*>(smem_raw + L.trans_off) + warp * 32 * kTransStride;
@@ -1291,9 +1398,18 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
         }
         max_smem = g_max_smem[dev];
     }
-    const uint32_t trans_bytes = kEpiWarps * 32 * kTransStride * 4;
-    const int avail = max_smem - 2048 - (int)trans_bytes;
+    // drain mode (split6 core): 8 epilogue warps, which needs at most 3
+    // producer warps (= stages) and N <= 192 per item (96 sums per thread)
+    L.drain = gather && a.core_drain > 0 && a.n_products == 6 && a.n_chunk <= 192 ? (a.core_drain > 1 ? 2 : 1) : 0;
+    uint32_t trans_bytes = (L.drain ? 2 : 1) * kEpiWarps * 32 * kTransStride * 4;
+    int avail = max_smem - 2048 - (int)trans_bytes;
     L.stages = avail / (int)L.stage_bytes;
+    if (L.drain && (L.stages > 3 || L.stages < 2)) {
+        L.drain = 0;
+        trans_bytes = kEpiWarps * 32 * kTransStride * 4;
+        avail = max_smem - 2048 - (int)trans_bytes;
+        L.stages = avail / (int)L.stage_bytes;
+    }
     if (L.stages > 8) L.stages = 8;
     if (L.stages < 2) return cudaErrorInvalidConfiguration;
     // gather mode: one ring slot per producer warp

@@ -113,7 +113,9 @@ struct kifmm_m2l_plan_s {
     // core launch choices picked by kifmm_m2l_autotune (0: defaults)
     int tune_chunk = 0;
     int tune_contig = 0;
-    int tune_resident = 1;  // split6: A-resident core where it fits
+    // core variant (split6): 0 classic, 1 A-resident (where it fits),
+    // 2 / 3 partials of two / one K-chunks drained into registers
+    int tune_variant = 2;
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
     kifmm::DevBuf<int> err_flag;

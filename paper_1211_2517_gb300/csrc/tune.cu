@@ -11,10 +11,13 @@
 //   n_chunk      the plan's default N per item, or half of it (more, smaller
 //                items: better balance, but every A row is gathered once per
 //                N part).
-//   resident     split6 only: the core variant that keeps each tile's A rows
-//                in shared memory and streams K~_o in column blocks, so that
-//                the epilogue of one block overlaps the MMAs of the next (its
-//                N per item is the whole row; n_chunk does not apply).
+//   variant      split6 only: 0 the classic core (hi and lo accumulators per
+//                tile, epilogue after the tile's MMAs); 1 the core that keeps
+//                each tile's A rows in shared memory and streams K~_o in
+//                column blocks whose epilogues overlap the next block's MMAs
+//                (n_chunk does not apply); 2 and 3 partial sums of two K-chunks
+//                (2) or one (3) drained into registers by eight epilogue
+//                warps while the next partial's MMAs run.
 // Each candidate is timed with CUDA events around the core launch of
 // kifmm_m2l_apply_levels.  With $KIFMM_M2L_AUTOTUNE_CACHE naming a file,
 // results are kept there as a JSON object keyed by operator, device and
@@ -55,7 +58,7 @@ std::string tune_key(kifmm_m2l_plan plan, const MultiState* ms, int nrhs, int lo
 }
 
 // The cache file holds one entry per line:
-//   "<key>": {"n_chunk": N, "contiguous": C, "resident": R, "core_ms": T},
+//   "<key>": {"n_chunk": N, "contiguous": C, "variant": V, "core_ms": T},
 // inside one pair of braces, so that it is a JSON object.
 std::map<std::string, std::string> read_cache(const char* path) {
     std::map<std::string, std::string> out;
@@ -74,16 +77,16 @@ std::map<std::string, std::string> read_cache(const char* path) {
     return out;
 }
 
-bool parse_entry(const std::string& v, int* chunk, int* contig, int* resident, double* ms) {
+bool parse_entry(const std::string& v, int* chunk, int* contig, int* variant, double* ms) {
     const char* s = v.c_str();
     const char* pc = std::strstr(s, "\"n_chunk\":");
     const char* pg = std::strstr(s, "\"contiguous\":");
-    const char* pr = std::strstr(s, "\"resident\":");
+    const char* pr = std::strstr(s, "\"variant\":");
     const char* pm = std::strstr(s, "\"core_ms\":");
     if (!pc || !pg || !pr || !pm) return false;
     *chunk = std::atoi(pc + 10);
     *contig = std::atoi(pg + 13);
-    *resident = std::atoi(pr + 11);
+    *variant = std::atoi(pr + 10);
     *ms = std::atof(pm + 10);
     return true;
 }
@@ -135,24 +138,28 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
         int c = 0, g = 0, rs = 0;
         double t = 0;
         if (it != entries.end() && parse_entry(it->second, &c, &g, &rs, &t) && c >= 16 && c % 16 == 0 &&
-            c <= 512 && (g == 0 || g == 1) && (rs == 0 || rs == 1)) {
+            c <= 512 && (g == 0 || g == 1) && rs >= 0 && rs <= 3) {
             plan->tune_chunk = c == core_chunk_default(plan) ? 0 : c;
             plan->tune_contig = g;
-            plan->tune_resident = rs;
+            plan->tune_variant = rs;
             if (result) *result = {c, g, rs, t, 1};
             return KIFMM_OK;
         }
     }
 
-    // candidates (n_chunk, contiguous, resident)
+    // candidates (n_chunk, contiguous, variant)
     struct Cand {
-        int chunk, contig, resident;
+        int chunk, contig, variant;
     };
     const int c0 = core_chunk_default(plan);
     const int c1 = (c0 / 2 + 15) / 16 * 16;
     std::vector<Cand> cands;
     for (int g = 0; g < 2; ++g) {
-        if (plan->core_hilo) cands.push_back({c0, g, 1});
+        if (plan->core_hilo) {
+            cands.push_back({c0, g, 2});
+            cands.push_back({c0, g, 3});
+            cands.push_back({c0, g, 1});
+        }
         cands.push_back({c0, g, 0});
         if (c1 >= 16 && c1 < c0) cands.push_back({c1, g, 0});
     }
@@ -166,7 +173,7 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
         if (st != KIFMM_OK) break;
         plan->tune_chunk = cd.chunk == c0 ? 0 : cd.chunk;
         plan->tune_contig = cd.contig;
-        plan->tune_resident = cd.resident;
+        plan->tune_variant = cd.variant;
         // one untimed pass (tile tables, first launch), then reps timed ones
         st = kifmm_m2l_apply_levels(plan, instance, level_lo, level_hi, nrhs, q_up, p_down, 0.0f, stream);
         if (st == KIFMM_OK) st = kifmm_m2l_profile_read(plan, nullptr, nullptr);
@@ -184,19 +191,19 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
     if (st != KIFMM_OK) {
         plan->tune_chunk = 0;
         plan->tune_contig = 0;
-        plan->tune_resident = 1;
+        plan->tune_variant = 2;
         return st;
     }
     plan->tune_chunk = bestc.chunk == c0 ? 0 : bestc.chunk;
     plan->tune_contig = bestc.contig;
-    plan->tune_resident = bestc.resident;
-    if (result) *result = {bestc.chunk, bestc.contig, bestc.resident, best, 0};
+    plan->tune_variant = bestc.variant;
+    if (result) *result = {bestc.chunk, bestc.contig, bestc.variant, best, 0};
     if (path && *path) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto entries = read_cache(path);
         char v[160];
-        std::snprintf(v, sizeof(v), "{\"n_chunk\": %d, \"contiguous\": %d, \"resident\": %d, \"core_ms\": %.6f}",
-                      bestc.chunk, bestc.contig, bestc.resident, best);
+        std::snprintf(v, sizeof(v), "{\"n_chunk\": %d, \"contiguous\": %d, \"variant\": %d, \"core_ms\": %.6f}",
+                      bestc.chunk, bestc.contig, bestc.variant, best);
         entries[key] = v;
         if (write_cache(path, entries) != 0) {
             set_error(std::string("could not write the autotune cache ") + path);

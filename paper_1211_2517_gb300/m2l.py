@@ -209,7 +209,7 @@ class M2LPlan:
         call("kifmm_m2l_autotune", self._h, int(instance), int(level_lo), int(level_hi), int(nrhs),
              ctypes.c_void_p(x_all.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(reps), ctypes.byref(res),
              _stream_handle(stream))
-        return {"n_chunk": res.n_chunk, "contiguous": res.contiguous, "resident": res.resident,
+        return {"n_chunk": res.n_chunk, "contiguous": res.contiguous, "variant": res.variant,
                 "core_ms": res.core_ms, "from_cache": bool(res.from_cache)}
 
     def sync(self, stream=None) -> None:

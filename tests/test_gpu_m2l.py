@@ -372,7 +372,7 @@ def test_autotune_keeps_parity_and_caches(g, oracle_factors, torus_mid, monkeypa
     refs = {l: om.m2l_svd(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64)) for l in range(2, 6)}
     for chunk in (144, 80):
         for contig in (0, 1):
-            cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "resident": 0, "core_ms": 1.0}\n}\n'
+            cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "variant": 0, "core_ms": 1.0}\n}\n'
                              % (key, chunk, contig))
             got = plan.autotune(x_all, 2, 5, reps=1)
             assert got["from_cache"] and (got["n_chunk"], got["contiguous"]) == (chunk, contig), got
@@ -389,10 +389,11 @@ def test_autotune_keeps_parity_and_caches(g, oracle_factors, torus_mid, monkeypa
 
 
 def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch, tmp_path):
-    """Every core variant the autotuner can pick for a p = 8 split6 plan (the
-    A-resident kernel, which streams K~_o in two column blocks of 96; the
-    classic kernel with N = 192 or 96 per item; round-robin or contiguous
-    tiles) against the oracle, forward and adjoint, levels 2..4 with 3 rhs."""
+    """Every core variant the autotuner can pick for a p = 8 split6 plan
+    (partials of two or one K-chunks drained into registers; the A-resident kernel, which
+    streams K~_o in two column blocks of 96; the classic kernel with N = 192
+    or 96 per item; round-robin or contiguous tiles) against the oracle,
+    forward and adjoint, levels 2..4 with 3 rhs."""
     tree, qs = sphere_small
     f = oracle_factors(8, 0.1, 1e-7)
     cache = tmp_path / "tune.json"
@@ -407,11 +408,12 @@ def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch
     refs = {(l, adj): (om.m2l_svd_adjoint if adj else om.m2l_svd)(tree.levels[l], l, tree.r0, f,
                                                                    qs[l].astype(np.float64))
             for l in (2, 3, 4) for adj in (False, True)}
-    for chunk, contig, resident in [(192, 0, 1), (192, 1, 1), (192, 0, 0), (192, 1, 0), (96, 0, 0)]:
-        cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "resident": %d, "core_ms": 1.0}\n}\n'
-                         % (key, chunk, contig, resident))
+    for chunk, contig, variant in [(192, 0, 2), (192, 1, 2), (192, 0, 3), (192, 0, 1), (192, 1, 1), (192, 0, 0),
+                                   (192, 1, 0), (96, 0, 0)]:
+        cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "variant": %d, "core_ms": 1.0}\n}\n'
+                         % (key, chunk, contig, variant))
         got = plan.autotune(x_all, 2, 4, reps=1)
-        assert got["from_cache"] and (got["n_chunk"], got["contiguous"], got["resident"]) == (chunk, contig, resident)
+        assert got["from_cache"] and (got["n_chunk"], got["contiguous"], got["variant"]) == (chunk, contig, variant)
         for adj in (False, True):
             out = plan.apply_levels(x_all, 2, 4, adjoint=adj).cpu().numpy()
             plan.sync()
@@ -419,9 +421,9 @@ def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch
             for l in (2, 3, 4):
                 nb = tree.levels[l].shape[0]
                 err = rel(out[row:row + nb], refs[(l, adj)])
-                print(f"variant chunk {chunk} contiguous {contig} resident {resident} adjoint {adj} level {l}: "
+                print(f"variant chunk {chunk} contiguous {contig} variant {variant} adjoint {adj} level {l}: "
                       f"rel L2 {err:.3e}")
-                assert err <= TOL["split6"], (chunk, contig, resident, adj, l, err)
+                assert err <= TOL["split6"], (chunk, contig, variant, adj, l, err)
                 row += nb
     plan.close()
 
