@@ -238,19 +238,26 @@ constexpr int kTransStride = 36;  // floats per row of the epilogue transpose bu
 constexpr int kMaxRowsChunk = 64; // N per work item of the rows modes (partial sums live in registers)
 constexpr int kPartChunks = 2;    // rows modes: K-chunks per drained partial of the (0,0) product
 
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// x (low half) and y (high half) rounded to nearest-even BF16 and packed
+__device__ __forceinline__ uint32_t cvt_bf16x2(float x, float y) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(y), "f"(x));
+    return d;
 }
 
-// split x into `np` BF16 pieces (round to nearest at each step)
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 (&p)[3], int np) {
+// Split x and y into `np` BF16 pieces each (round to nearest at each step,
+// x_i + x_(i+1) + ... reproduces x to 8 np bits); piece i of both is h[i]
+// (x low half, y high half); pieces past np are zero.  The BF16 values
+// convert back to FP32 exactly by placing their bits in the high half.
+__device__ __forceinline__ void split3x2(float x, float y, uint32_t (&h)[3], int np) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         if (i < np) {
-            p[i] = __float2bfloat16_rn(x);
-            x -= __bfloat162float(p[i]);
+            h[i] = cvt_bf16x2(x, y);
+            x -= __uint_as_float(h[i] << 16);
+            y -= __uint_as_float(h[i] & 0xFFFF0000u);
         } else {
-            p[i] = __float2bfloat16_rn(0.f);
+            h[i] = 0u;
         }
     }
 }
@@ -438,17 +445,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < 8; ++i) {
                     const int f = v + 128 * i;
                     const int row = f / 8, c4 = f % 8;
-                    __nv_bfloat16 pc0[3], pc1[3], pc2[3], pc3[3];
-                    split3(buf[i].x, pc0, L.na);
-                    split3(buf[i].y, pc1, L.na);
-                    split3(buf[i].z, pc2, L.na);
-                    split3(buf[i].w, pc3, L.na);
+                    uint32_t lo[3], hi[3];
+                    split3x2(buf[i].x, buf[i].y, lo, L.na);
+                    split3x2(buf[i].z, buf[i].w, hi, L.na);
                     const uint32_t off = swz<CH>(row, c4 >> 1) + (c4 & 1) * 8;
 #pragma unroll
                     for (int pc = 0; pc < 3; ++pc) {
                         if (pc >= L.na) break;
-                        const uint32_t lo = pack_bf16x2(pc0[pc], pc1[pc]), hi = pack_bf16x2(pc2[pc], pc3[pc]);
-                        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_smem(s, pc) + off), "r"(lo), "r"(hi)
+                        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a_smem(s, pc) + off), "r"(lo[pc]),
+                                     "r"(hi[pc])
                                      : "memory");
                     }
                 }
@@ -854,15 +859,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                             *reinterpret_cast<float4*>(args.Df + grow * args.ldd + col) = x;
                         if (args.Z)
                             *reinterpret_cast<float4*>(args.Z + grow * args.ldd + col) = make_float4(0.f, 0.f, 0.f, 0.f);
-                        __nv_bfloat16 q0[3], q1[3], q2[3], q3[3];
-                        split3(x.x, q0, args.dp_pieces);
-                        split3(x.y, q1, args.dp_pieces);
-                        split3(x.z, q2, args.dp_pieces);
-                        split3(x.w, q3, args.dp_pieces);
+                        uint32_t lo[3], hi[3];
+                        split3x2(x.x, x.y, lo, args.dp_pieces);
+                        split3x2(x.z, x.w, hi, args.dp_pieces);
 #pragma unroll
                         for (int pc = 0; pc < 3; ++pc) {
                             if (pc >= args.dp_pieces) break;
-                            uint2 pk = make_uint2(pack_bf16x2(q0[pc], q1[pc]), pack_bf16x2(q2[pc], q3[pc]));
+                            uint2 pk = make_uint2(lo[pc], hi[pc]);
                             *reinterpret_cast<uint2*>(args.Dp + pc * args.dp_piece_stride + grow * args.ldd + col) = pk;
                         }
                     }
