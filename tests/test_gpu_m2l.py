@@ -215,22 +215,32 @@ def test_autograd_central_differences(g, oracle_factors):
         assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)
 
 
+@pytest.fixture(scope="module")
+def sphere1m_upward():
+    """The 1,048,576-point sphere at depth 5 with its upward-equivalent
+    densities from the oracle's S2M/M2M of the U[-1,1] point densities."""
+    wl = synth.workload("sphere1m_p8")
+    qup = upward.upward_pass(wl.tree, wl.points, wl.p, wl.d, wl.densities)
+    return wl, {l: qup[l].astype(np.float32) for l in range(2, 6)}
+
+
 @pytest.mark.parametrize("precision", ["fp32", "split6"])
-def test_full_size_adjoint_autograd_sphere1m(g, oracle_factors, precision):
-    """Loss 0.5 ||phi - phi_t||^2, phi = M2L(q) over levels 2..5 of the
-    1,048,576-point sphere at depth 5 (p = 8, eps = 1e-7, phi_t ~ N(0,1)),
-    differentiated through the levels-batch autograd Function: the gradient
-    against the oracle's transpose product (C_k^T on the reversed offsets),
-    then central differences with h = 1e-3."""
+def test_full_size_adjoint_autograd_sphere1m(g, oracle_factors, sphere1m_upward, precision):
+    """Loss 0.5 ||phi - phi_t||^2, phi = M2L(q^u) over levels 2..5 of the
+    1,048,576-point sphere at depth 5 (p = 8, eps = 1e-7, phi_t ~ N(0,1),
+    q^u from S2M/M2M of the point densities), differentiated through the
+    levels-batch autograd Function: the gradient against the oracle's
+    transpose product (C_k^T on the reversed offsets), then central
+    differences with h = 1e-3 along 8 seeded directions."""
     from paper_1211_2517_gb300.autograd import m2l_levels
 
-    wl = synth.workload("sphere1m_p8")
+    wl, qup = sphere1m_upward
     tree = wl.tree
     levels = range(2, 6)
     plan = make_plan(g, 8, 1e-7, precision, tree, levels)
     nbs = [tree.levels[l].shape[0] for l in levels]
     rng = np.random.default_rng(55)
-    q0 = np.concatenate([synth.random_box_densities(nb, 1, 296, 700 + l)[:, 0] for nb, l in zip(nbs, levels)])
+    q0 = np.concatenate([qup[l] for l in levels])
     phi_t = rng.standard_normal(q0.shape).astype(np.float32)
     q = torch.from_numpy(q0).cuda().requires_grad_(True)
     phit = torch.from_numpy(phi_t).cuda()
@@ -253,9 +263,12 @@ def test_full_size_adjoint_autograd_sphere1m(g, oracle_factors, precision):
         print(f"sphere1m {precision} level {l}: gradient rel L2 {err:.3e}")
         assert err <= 1e-5, err
         row += nb
+    # Directions with O(1) entries (the gradient's direction, scaled to unit
+    # RMS, plus seeded N(0,1)/2): a unit-norm direction would move each of
+    # the 1.9M FP32 entries by ~1e-9, below their resolution.
     h = 1e-3
     gdir = grad.float() / grad.float().pow(2).mean().sqrt()
-    for j in range(4):
+    for j in range(8):
         z = torch.from_numpy(rng.standard_normal(q0.shape).astype(np.float32)).cuda()
         v = gdir + 0.5 * z
         with torch.no_grad():
