@@ -237,6 +237,36 @@ int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
 int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                             const float* q_up, float* p_down, float beta, void* stream);
 
+/* ---- stage 2: per-offset low-rank cores (Sec. 3.2) ----------------------- */
+
+/* Switch the plan's core to the second compression stage of Sec. 3.2
+ * (Eq. eq-lra): each unit-level core is factored in FP64 on the host,
+ * K~_o = U_o S_o Q_o^T, and truncated to the k_o singular values with
+ * sigma >= eps2 * sigma_0(K_fat), eps2 = c2 * eps / r (Eq. eq-vareps2, with
+ * eps = the plan's eps_1 and r its rank); then
+ *   p~^t += s_l Uhat_o (Vhat_o q~^s),  Uhat_o = U_o[:, :k_o] (r x k_o),
+ *                                      Vhat_o = S_o Q_o^T restricted (k_o x r),
+ * two skinny GEMMs per tile on the tensor cores instead of one r x r product.
+ * Applies to every later apply / apply_adjoint / apply_levels / apply_batch /
+ * apply_noalloc on this plan (the adjoint uses the reversed offset's factors).
+ * c2 <= 0 switches back to the single-stage cores.  Tensor-core precisions
+ * only (KIFMM_PREC_FP32: KIFMM_ERR_UNSUPPORTED); every k_o must be <= 96 and
+ * r_pad <= 320 (else KIFMM_ERR_UNSUPPORTED: take a larger c2).  Host work:
+ * the FP64 factors (from the plan's cache if $KIFMM_M2L_CACHE is set, else
+ * recomputed) and 316 r x r SVDs; device memory: 2 x 3 x 316 x 96 x r_pad
+ * BF16 values. */
+int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2);
+
+/* The per-offset ranks k_o of stage 2 (k[316], HOST memory, offsets in the
+ * lexicographic order above).  KIFMM_ERR_STATE when stage 2 is off. */
+int kifmm_m2l_stage2_ranks(kifmm_m2l_plan plan, int* k);
+
+/* Host-only stage 2 (no GPU needed): the FP64 precompute of
+ * kifmm_m2l_precompute followed by the factoring of kifmm_m2l_set_stage2;
+ * writes the 316 ranks to k and, if core is not NULL, the truncated cores
+ * Uhat_o Vhat_o to core[316][r][r] (row-major, r from kifmm_m2l_factors_host). */
+int kifmm_m2l_stage2_host(const kifmm_m2l_params* params, double c2, int* k, double* core);
+
 /* ---- tracing ------------------------------------------------------------ */
 
 /* Per-stage timing (enable != 0 turns it on, 0 off; off by default).  While

@@ -251,6 +251,42 @@ def stage2_factors(f: SvdFactors, eps2: float):
     return out
 
 
+def m2l_svd_stage2(box_ijk, level: int, r0: float, f: SvdFactors, s2, q_up, lists=None) -> np.ndarray:
+    """Compressed M2L with the second stage of Sec. 3.2 (Eq. eq-lra): every
+    core K~_o is replaced by its truncation Uhat_o Vhat_o (``s2`` from
+    ``stage2_factors``), applied as two products:
+
+        t    = Vhat_o q~^s
+        p~^t = s_l sum_{s in I^t} Uhat_o t
+    """
+    q, squeeze = _as3(q_up)
+    tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
+    qt = q @ f.R
+    pt = np.zeros(q.shape[:2] + (f.r,))
+    for k in np.unique(ok):
+        sel = ok == k
+        uh, vh = s2[k]
+        pt[tg[sel]] += (qt[sr[sel]] @ vh.T) @ uh.T
+    pt *= level_scale(level, r0)
+    out = pt @ f.U.T
+    return out[:, 0, :] if squeeze else out
+
+
+def m2l_svd_stage2_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, s2, pbar, lists=None) -> np.ndarray:
+    """Transpose of ``m2l_svd_stage2``: q-bar~^s = s_l sum_t Vhat_o^T (Uhat_o^T p-bar~^t)."""
+    pb, squeeze = _as3(pbar)
+    tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
+    pt = pb @ f.U
+    qt = np.zeros(pb.shape[:2] + (f.r,))
+    for k in np.unique(ok):
+        sel = ok == k
+        uh, vh = s2[k]
+        qt[sr[sel]] += (pt[tg[sel]] @ uh) @ vh
+    qt *= level_scale(level, r0)
+    out = qt @ f.R.T
+    return out[:, 0, :] if squeeze else out
+
+
 def eps2_from_c2(c2: float, eps1: float, r: int) -> float:
     """eps2 = C2 eps1 / p~ with p~ the compressed dimension (Eq. eq-vareps2)."""
     return c2 * eps1 / r

@@ -5,6 +5,6 @@ in hand-written sm_103a kernels behind the C ABI of include/kifmm_m2l.h
 (libkifmm_m2l.so, built in-tree by ``paper_1211_2517_gb300.build``).
 """
 from ._lib import EXPORTED, KifmmError, lib  # noqa: F401
-from .m2l import M2LPlan, apply_batch, factors_host, pairs_host, surface_count  # noqa: F401
+from .m2l import M2LPlan, apply_batch, factors_host, pairs_host, stage2_host, surface_count  # noqa: F401
 
-__all__ = ["M2LPlan", "apply_batch", "factors_host", "pairs_host", "surface_count", "KifmmError", "lib", "EXPORTED"]
+__all__ = ["M2LPlan", "apply_batch", "factors_host", "pairs_host", "stage2_host", "surface_count", "KifmmError", "lib", "EXPORTED"]

@@ -31,6 +31,7 @@ EXPORTED = (
     "kifmm_m2l_level_pairs", "kifmm_m2l_apply", "kifmm_m2l_apply_adjoint", "kifmm_m2l_apply_dense",
     "kifmm_m2l_apply_noalloc", "kifmm_m2l_apply_levels", "kifmm_m2l_apply_levels_adjoint",
     "kifmm_m2l_apply_batch",
+    "kifmm_m2l_set_stage2", "kifmm_m2l_stage2_ranks", "kifmm_m2l_stage2_host",
     "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
     "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error", "kifmm_m2l_version",
 )
@@ -90,6 +91,9 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_profile_enable": [vp, i32],
         "kifmm_m2l_profile_read": [vp, ctypes.POINTER(ctypes.c_double), pi64],
         "kifmm_m2l_autotune": [vp, i32, i32, i32, i32, vp, vp, i32, ctypes.POINTER(TuneResult), vp],
+        "kifmm_m2l_set_stage2": [vp, ctypes.c_double],
+        "kifmm_m2l_stage2_ranks": [vp, pint],
+        "kifmm_m2l_stage2_host": [ctypes.POINTER(Params), ctypes.c_double, pint, vp],
         "kifmm_m2l_factors_host": [ctypes.POINTER(Params), pint, pint, vp, vp, vp],
         "kifmm_m2l_pairs_host": [i32, i32, vp, pi64, vp, vp, vp],
     }

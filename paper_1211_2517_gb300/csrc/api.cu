@@ -216,6 +216,10 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
         a.contiguous = plan->tune_contig;
         a.core_resident = plan->tune_variant == 1;
         a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
+        a.s2_on = plan->s2_on;
+        a.s2_V = plan->s2V.ptr;
+        a.s2_U = plan->s2U.ptr;
+        a.s2_k16 = plan->s2_k16.ptr;
         a.row_src = ts->row_src.ptr;
         a.row_dst = ts->row_dst.ptr;
         a.tile_k = ts->tile_k.ptr;
@@ -381,6 +385,10 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         a.contiguous = plan->tune_contig;
         a.core_resident = plan->tune_variant == 1;
         a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
+        a.s2_on = plan->s2_on;
+        a.s2_V = plan->s2V.ptr;
+        a.s2_U = plan->s2U.ptr;
+        a.s2_k16 = plan->s2_k16.ptr;
         a.row_src = ts->row_src.ptr;
         a.row_dst = ts->row_dst.ptr;
         a.tile_k = ts->tile_k.ptr;
@@ -680,6 +688,128 @@ int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n) {
     if (r) *r = plan->r;
     if (r_pad) *r_pad = plan->rp;
     if (n) *n = plan->n;
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (!(c2 > 0)) {
+        plan->s2_on = 0;
+        plan->s2_c2 = 0;
+        plan->s2_k.clear();
+        return KIFMM_OK;
+    }
+    if (plan->prm.precision == KIFMM_PREC_FP32) {
+        set_error("stage 2 runs on the tensor-core precisions only (FP32 plans use the SIMT core)");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
+    if (plan->rp > 512 - 2 * 96) {
+        set_error("stage 2 needs r_pad <= 320");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    try {
+        Factors f;
+        st = compute_factors(plan->prm, f);
+        if (st != KIFMM_OK) return st;
+        Stage2 s2;
+        st = compute_stage2(f, c2, s2);
+        if (st != KIFMM_OK) return st;
+        int kmax = 0;
+        for (int k : s2.k) kmax = std::max(kmax, k);
+        if (kmax > 96) {
+            set_error("stage 2: a per-offset rank exceeds 96 (largest " + std::to_string(kmax) +
+                      "); use a larger c2");
+            return KIFMM_ERR_UNSUPPORTED;
+        }
+        const int r = plan->r, rp = plan->rp;
+        std::vector<int> k16(kOffsets);
+        for (int o = 0; o < kOffsets; ++o) k16[o] = std::max(16, (s2.k[o] + 15) / 16 * 16);
+        // Vhat_o rows, [3][316][96][rp]; Uhat_o rows, [3][316][rp][96]; zero padding
+        auto split_upload = [&](kifmm::DevBuf<__nv_bfloat16>& dst, size_t per, auto value_at) -> int {
+            std::vector<uint16_t> h(per * 3, 0);
+            for (size_t e = 0; e < per; ++e) {
+                double v = value_at(e);
+                if (v == 0.0) continue;
+                for (int pc = 0; pc < 3; ++pc) {
+                    const uint16_t b = bf16_bits_rn((float)v);
+                    h[pc * per + e] = b;
+                    v -= (double)bf16_to_float(b);
+                }
+            }
+            KIFMM_CUDA_TRY(dst.ensure(h.size()));
+            KIFMM_CUDA_TRY(cudaMemcpy(dst.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
+            return KIFMM_OK;
+        };
+        st = split_upload(plan->s2V, (size_t)kOffsets * 96 * rp, [&](size_t e) -> double {
+            const size_t o = e / ((size_t)96 * rp), j = (e / rp) % 96, b = e % rp;
+            return (j < (size_t)s2.k[o] && b < (size_t)r) ? s2.Vh[o][j * r + b] : 0.0;
+        });
+        if (st != KIFMM_OK) return st;
+        st = split_upload(plan->s2U, (size_t)kOffsets * rp * 96, [&](size_t e) -> double {
+            const size_t o = e / ((size_t)rp * 96), a = (e / 96) % rp, j = e % 96;
+            return (a < (size_t)r && j < (size_t)s2.k[o]) ? s2.Uh[o][a * s2.k[o] + j] : 0.0;
+        });
+        if (st != KIFMM_OK) return st;
+        KIFMM_CUDA_TRY(plan->s2_k16.upload(k16.data(), k16.size()));
+        plan->s2_k = s2.k;
+        plan->s2_c2 = c2;
+        plan->s2_on = 1;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed in kifmm_m2l_set_stage2");
+        return KIFMM_ERR_OOM;
+    }
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_stage2_host(const kifmm_m2l_params* params, double c2, int* k, double* core) {
+    int st = check_params(params);
+    if (st != KIFMM_OK) return st;
+    if (!k) {
+        set_error("k is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    try {
+        Factors f;
+        st = compute_factors(*params, f);
+        if (st != KIFMM_OK) return st;
+        Stage2 s2;
+        st = compute_stage2(f, c2, s2);
+        if (st != KIFMM_OK) return st;
+        const int r = f.r;
+        for (int o = 0; o < kOffsets; ++o) {
+            k[o] = s2.k[o];
+            if (!core) continue;
+            double* c = core + (size_t)o * r * r;
+            const int ko = s2.k[o];
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b) {
+                    double acc = 0;
+                    for (int j = 0; j < ko; ++j) acc += s2.Uh[o][(size_t)a * ko + j] * s2.Vh[o][(size_t)j * r + b];
+                    c[(size_t)a * r + b] = acc;
+                }
+        }
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed in kifmm_m2l_stage2_host");
+        return KIFMM_ERR_OOM;
+    }
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_stage2_ranks(kifmm_m2l_plan plan, int* k) {
+    if (!plan || !k) {
+        set_error("plan or k is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (!plan->s2_on) {
+        set_error("stage 2 is off: call kifmm_m2l_set_stage2 first");
+        return KIFMM_ERR_STATE;
+    }
+    for (int o = 0; o < kOffsets; ++o) k[o] = plan->s2_k[o];
     return KIFMM_OK;
 }
 

@@ -195,6 +195,10 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.contiguous = plan->tune_contig;
         a.core_resident = plan->tune_variant == 1;
         a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
+        a.s2_on = plan->s2_on;
+        a.s2_V = plan->s2V.ptr;
+        a.s2_U = plan->s2U.ptr;
+        a.s2_k16 = plan->s2_k16.ptr;
         a.row_src = g.tiles.row_src.ptr;
         a.row_dst = g.tiles.row_dst.ptr;
         a.tile_k = g.tiles.tile_k.ptr;

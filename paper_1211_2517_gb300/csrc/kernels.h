@@ -98,6 +98,11 @@ struct UmmaArgs {
     int contiguous;           // core: 1 = each CTA takes a contiguous run of tiles
     int core_resident;        // core, split6 with hilo: 1 = A tile resident in shared memory, K~_o in N blocks
     int core_drain;           // core, split6: K-chunks per partial drained into registers by 8 epilogue warps (0: off)
+    // core, stage 2 (Sec. 3.2): K~_o = Uhat_o Vhat_o with per-offset rank k_o
+    int s2_on;
+    const __nv_bfloat16* s2_V;  // pieces [pieces][316][96][kdim]: rows of Vhat_o, zero past k_o
+    const __nv_bfloat16* s2_U;  // pieces [pieces][316][ndim][96]: rows of Uhat_o, zero past k_o
+    const int* s2_k16;          // [316] k_o rounded up to 16 (16..96)
     // epilogue
     float* D;                 // E_RED / E_STORE: FP32 [*][ldd]
     int ldd;

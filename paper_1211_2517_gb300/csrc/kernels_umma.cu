@@ -1208,6 +1208,372 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Stage-2 core (Sec. 3.2, Eq. eq-lra).  With K~_o = Uhat_o Vhat_o (rank k_o,
+// rounded up to k16 <= 96), a tile's product is two skinny GEMMs:
+//   T = Q~_rows Vhat_o^T   (128 x k16, K = r_pad)     split products, hi/lo
+//   P = T Uhat_o^T         (128 x r_pad, K = k16)     split products
+// T never leaves the SM: the epilogue warps read it from TMEM, add hi and lo,
+// split it into BF16 pieces and store them, 64B-swizzled, as the A operand of
+// the second GEMM.  P is reduced into p~ as in the other cores.
+//
+// Warp roles (384 threads):
+//   warps 0-3   epilogue: T split, then the reduction of P
+//   warps 4-6   producers, one ring slot each: the first GEMM's stages (q~
+//               rows by cp.async, Vhat_o by TMA) and the second GEMM's stages
+//               (Uhat_o by TMA, one 96-row part of N per stage)
+//   warp 11     TMEM allocation and the MMA-issuing thread
+// TMEM columns: T hi [0, 96), T lo [96, 192), P [192, 192 + r_pad).
+// The next tile's first GEMM runs while the epilogue reduces P.
+constexpr int kS2Stages = 3, kS2Kmax = 96, kS2Part = 96;
+constexpr int kOffsetsHost = KIFMM_N_OFFSETS;
+
+struct S2Smem {
+    uint64_t full[kS2Stages], empty[kS2Stages];
+    uint64_t t_full, t_empty, tsplit, tbuf_free, p_full, p_empty, drain;
+    uint32_t tmem_base;
+    volatile int abort_flag;
+};
+
+struct S2Layout {
+    int kc1;                 // K chunks of the first GEMM (r_pad / 32, rounded up)
+    int nh;                  // 96-row parts of N in the second GEMM
+    int n_items;             // tiles
+    uint32_t stage_bytes;    // A pieces (3 x 8 KB) + B pieces (3 x 96 rows x 64 B)
+    uint32_t tbuf_off;       // T pieces [3 chunks][pieces][128 x 64 B], from the stage ring base
+    uint32_t trans_off;      // epilogue transpose buffers, from the stage ring base
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+    core_stage2_kernel(const __grid_constant__ CUtensorMap vmap, const __grid_constant__ CUtensorMap umap,
+                       const UmmaArgs args, const S2Layout L) {
+    extern __shared__ __align__(1024) uint8_t smem_dyn[];
+    uint8_t* smem_raw = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+    S2Smem* sm = reinterpret_cast<S2Smem*>(smem_raw);
+    uint8_t* ring = smem_raw + 1024;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int CH = 32, RB = 64;
+    constexpr int PC = NP == 6 ? 3 : (NP == 3 ? 2 : 1);  // BF16 pieces
+    constexpr int P0 = 6 - NP;
+    constexpr bool HILO = NP > 1;
+    constexpr uint32_t kAPiece = kTileM * CH * 2;            // 8 KB
+    constexpr uint32_t kBPiece = kS2Kmax * RB;               // 6 KB
+    constexpr uint32_t kBOff = 3 * kAPiece;                  // B pieces follow 3 A pieces
+    const int S = kS2Stages, KC1 = L.kc1, NH = L.nh;
+    const bool contig = args.contiguous != 0;
+    const int i_beg = contig ? (int)((long)L.n_items * blockIdx.x / gridDim.x) : (int)blockIdx.x;
+    const int i_end = contig ? (int)((long)L.n_items * (blockIdx.x + 1) / gridDim.x) : L.n_items;
+    const int i_step = contig ? 1 : (int)gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < S; ++b) {
+            mbar_init(&sm->full[b], 33);
+            mbar_init(&sm->empty[b], 1);
+        }
+        mbar_init(&sm->t_full, 1);
+        mbar_init(&sm->t_empty, kEpiWarps * 32);
+        mbar_init(&sm->tsplit, kEpiWarps * 32);
+        mbar_init(&sm->tbuf_free, 1);
+        mbar_init(&sm->p_full, 1);
+        mbar_init(&sm->p_empty, kEpiWarps * 32);
+        mbar_init(&sm->drain, 1);
+        sm->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kEpiWarps + kProdWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(&sm->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+    auto stage_base = [&](int b) -> uint8_t* { return ring + (size_t)b * L.stage_bytes; };
+    auto tbuf = [&](int c2, int pc) -> uint8_t* { return ring + L.tbuf_off + (size_t)(c2 * 3 + pc) * kAPiece; };
+    auto k16_of = [&](int item) -> int { return __ldg(args.s2_k16 + (__ldg(args.tile_k + item) & 0xFFFF)); };
+
+    if (warp >= kEpiWarps && warp < kEpiWarps + kS2Stages) {
+        // ================= producers =================
+        const int pw = warp - kEpiWarps;
+        constexpr int CPR = CH / 8, RPI = 32 / CPR, NR = kTileM / RPI;
+        const int cch = lane % CPR, rl = lane / CPR;
+        int it = 0;
+        bool ok = true;
+        for (int item = i_beg; item < i_end && ok; item += i_step) {
+            const int group = __ldg(args.tile_k + item) & 0xFFFF;
+            const int k16 = __ldg(args.s2_k16 + group);
+            const int nst = KC1 + ((k16 + 31) / 32) * NH;
+            int srow[NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int r = __ldg(args.row_src + (long)item * kTileM + rl + RPI * i);
+                srow[i] = r < 0 ? args.zero_row : r;
+            }
+            for (int j = 0; j < nst; ++j, ++it) {
+                if (it % S != pw) continue;
+                const int b = it % S;
+                const uint32_t ph = (uint32_t)(it / S) & 1u;
+                if (!mbar_wait(&sm->empty[b], ph ^ 1u, sm, args.error_flag)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* sb = stage_base(b);
+                if (j < KC1) {
+                    const int col = j * CH + cch * 8;
+                    const uint32_t bytes = col < args.kdim ? 16u : 0u;
+                    const int colc = col < args.kdim ? col : 0;
+#pragma unroll
+                    for (int pc = 0; pc < PC; ++pc) {
+                        const __nv_bfloat16* base = args.A + pc * args.a_piece_stride + colc;
+                        const uint32_t sa = smem_u32(sb + pc * kAPiece);
+#pragma unroll
+                        for (int i = 0; i < NR; ++i)
+                            cp_async16(sa + swz<CH>(rl + RPI * i, cch), base + (long)srow[i] * args.kdim, bytes);
+                    }
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&sm->full[b], (uint32_t)(PC * k16 * RB));
+                        for (int pc = 0; pc < PC; ++pc)
+                            for (int rb = 0; rb < k16; rb += 16)
+                                tma_load_2d(smem_u32(sb + kBOff + pc * kBPiece + rb * RB), &vmap, j * CH,
+                                            (pc * KIFMM_N_OFFSETS + group) * kS2Kmax + rb, &sm->full[b]);
+                    }
+                } else {
+                    const int jj = j - KC1, c2 = jj / NH, h = jj % NH;
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&sm->full[b], (uint32_t)(PC * kBPiece));
+                        for (int pc = 0; pc < PC; ++pc)
+                            tma_load_2d(smem_u32(sb + kBOff + pc * kBPiece), &umap, c2 * CH,
+                                        (pc * KIFMM_N_OFFSETS + group) * args.ndim + h * kS2Part, &sm->full[b]);
+                    }
+                }
+                cp_async_commit();
+                cp_async_wait_0();
+                fence_proxy_async();
+                mbar_arrive(&sm->full[b]);
+            }
+        }
+        cp_async_wait_0();
+        if (!ok && lane == 0) {
+            const unsigned long long t0 = global_ns();
+            while (global_ns() - t0 < 1000000ull) {
+            }
+        }
+    } else if (warp == kEpiWarps + kProdWarps) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            const uint64_t ring_desc = umma_desc<CH>(smem_u32(ring));
+            const uint32_t stage_u = L.stage_bytes >> 4, a_u = kAPiece >> 4, bo_u = kBOff >> 4, bp_u = kBPiece >> 4;
+            const uint64_t tdesc = umma_desc<CH>(smem_u32(ring + L.tbuf_off));
+            int b = 0, ic = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
+            for (int item = i_beg; item < i_end && ok; item += i_step, ++ic) {
+                const int k16 = k16_of(item);
+                const int nc2 = (k16 + 31) / 32;
+                // first GEMM: T = Q~ Vhat^T
+                if (!mbar_wait(&sm->t_empty, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t idT = umma_idesc_bf16(k16);
+                const uint32_t d_hi = tmem, d_lo = HILO ? tmem + (uint32_t)kS2Kmax : tmem;
+                bool hi_on = false, lo_on = false;
+                for (int kc = 0; kc < KC1; ++kc) {
+                    if (!mbar_wait(&sm->full[b], ph, sm, args.error_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t sd = ring_desc + (uint64_t)((uint32_t)b * stage_u);
+                    if (args.kdim - kc * CH >= 32) {
+#pragma unroll
+                        for (int pi = P0; pi < 6; ++pi) {
+                            const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !HILO;
+                            const uint32_t d = to_hi ? d_hi : d_lo;
+                            const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u), bd = sd + (uint64_t)(bo_u + kB[pi] * bp_u);
+                            umma_bf16(d, ad, bd, idT, (to_hi ? hi_on : lo_on) ? 1u : 0u);
+                            umma_bf16(d, ad + 2, bd + 2, idT, 1u);
+                            hi_on = hi_on || to_hi;
+                            lo_on = lo_on || !to_hi;
+                        }
+                    } else {
+#pragma unroll
+                        for (int pi = P0; pi < 6; ++pi) {
+                            const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !HILO;
+                            const uint32_t d = to_hi ? d_hi : d_lo;
+                            const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u), bd = sd + (uint64_t)(bo_u + kB[pi] * bp_u);
+                            umma_bf16(d, ad, bd, idT, (to_hi ? hi_on : lo_on) ? 1u : 0u);
+                            hi_on = hi_on || to_hi;
+                            lo_on = lo_on || !to_hi;
+                        }
+                    }
+                    umma_commit(&sm->empty[b]);
+                    if (++b == S) {
+                        b = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&sm->t_full);
+                // second GEMM: P = T Uhat^T, T pieces from shared memory
+                if (!mbar_wait(&sm->tsplit, (uint32_t)(ic & 1), sm, args.error_flag) ||
+                    !mbar_wait(&sm->p_empty, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t p_on = 0;  // bit h: part h of P has been written
+                for (int c2 = 0; c2 < nc2 && ok; ++c2) {
+                    const bool two = k16 - c2 * CH >= 32;
+                    for (int h = 0; h < NH; ++h) {
+                        if (!mbar_wait(&sm->full[b], ph, sm, args.error_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int nh_cols = min(kS2Part, args.ndim - h * kS2Part);
+                        const uint32_t idP = umma_idesc_bf16(nh_cols);
+                        const uint32_t dP = tmem + (uint32_t)(2 * kS2Kmax + h * kS2Part);
+                        const uint64_t sd = ring_desc + (uint64_t)((uint32_t)b * stage_u);
+                        const uint64_t td = tdesc + (uint64_t)((uint32_t)(c2 * 3) * a_u);
+#pragma unroll
+                        for (int pi = P0; pi < 6; ++pi) {
+                            const uint64_t ad = td + (uint64_t)(kA[pi] * a_u), bd = sd + (uint64_t)(bo_u + kB[pi] * bp_u);
+                            umma_bf16(dP, ad, bd, idP, ((p_on >> h) & 1u) ? 1u : 0u);
+                            p_on |= 1u << h;
+                            if (two) umma_bf16(dP, ad + 2, bd + 2, idP, 1u);
+                        }
+                        umma_commit(&sm->empty[b]);
+                        if (++b == S) {
+                            b = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&sm->p_full);
+                umma_commit(&sm->tbuf_free);
+            }
+            umma_commit(&sm->drain);
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&sm->drain, 0u) && global_ns() - t0 < kWaitNs) {
+            }
+        }
+        __syncwarp();
+    } else if (warp < kEpiWarps) {
+        // ================= epilogue =================
+        float* trans = reinterpret_cast<float*>(ring + L.trans_off) + warp * 32 * kTransStride;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int m = warp * 32 + lane;  // tile row = TMEM lane
+        int ic = 0;
+        bool ok = true;
+        for (int item = i_beg; item < i_end && ok; item += i_step, ++ic) {
+            const long orow = __ldg(args.row_dst + (long)item * kTileM + m);
+            const int code = __ldg(args.tile_k + item);
+            const float oscale = args.scale_table ? __ldg(args.scale_table + (code >> 16)) : args.level_scale[(code >> 16) & 31];
+            const int k16 = __ldg(args.s2_k16 + (code & 0xFFFF));
+            // T: TMEM -> hi + lo -> BF16 pieces in shared memory
+            bool got = mbar_wait(&sm->tbuf_free, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag);
+            got = got && mbar_wait(&sm->t_full, (uint32_t)(ic & 1), sm, args.error_flag);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            for (int c = 0; c < k16; c += 32) {
+                uint32_t r[32], r2[32];
+                const bool full32 = c + 32 <= k16;
+                if (full32) tmem_ld32(tmem + lane_base + (uint32_t)c, r);
+                else tmem_ld16(tmem + lane_base + (uint32_t)c, r);
+                if (HILO) {
+                    if (full32) tmem_ld32(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+                    else tmem_ld16(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!full32 && q >= 2) break;
+                    uint32_t pk[3][4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float x = __uint_as_float(r[8 * q + 2 * e]), y = __uint_as_float(r[8 * q + 2 * e + 1]);
+                        if (HILO) {
+                            x += __uint_as_float(r2[8 * q + 2 * e]);
+                            y += __uint_as_float(r2[8 * q + 2 * e + 1]);
+                        }
+                        uint32_t hh[3];
+                        split3x2(x, y, hh, PC);
+#pragma unroll
+                        for (int pc = 0; pc < 3; ++pc) pk[pc][e] = hh[pc];
+                    }
+#pragma unroll
+                    for (int pc = 0; pc < PC; ++pc)
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(tbuf(c / 32, pc)) +
+                                                                                        swz<CH>(m, q)),
+                                     "r"(pk[pc][0]), "r"(pk[pc][1]), "r"(pk[pc][2]), "r"(pk[pc][3])
+                                     : "memory");
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sm->t_empty);
+            fence_proxy_async();
+            mbar_arrive(&sm->tsplit);
+            // P: TMEM -> transpose -> reductions into p~
+            got = mbar_wait(&sm->p_full, (uint32_t)(ic & 1), sm, args.error_flag);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            long prow[8];
+#pragma unroll
+            for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
+            const int c4 = lane % 8;
+            for (int c = 0; c < args.ndim; c += 32) {
+                uint32_t r[32];
+                const bool full32 = c + 32 <= args.ndim;
+                const uint32_t a0 = tmem + lane_base + (uint32_t)(2 * kS2Kmax + c);
+                if (full32) tmem_ld32(a0, r);
+                else tmem_ld16(a0, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * q) =
+                        make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                    __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                __syncwarp();
+                const int ncols = full32 ? 32 : 16;
+#pragma unroll
+                for (int pass = 0; pass < 8; ++pass) {
+                    const int rr = pass * 4 + lane / 8;
+                    const long grow = prow[pass];
+                    if (grow < 0 || 4 * c4 >= ncols) continue;
+                    const float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
+                    red_add_v4(args.D + grow * args.ldd + c + 4 * c4, __float_as_uint(oscale * x.x),
+                               __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
+                               __float_as_uint(oscale * x.w));
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            mbar_arrive(&sm->p_empty);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kEpiWarps + kProdWarps) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -1230,7 +1596,7 @@ EncodeTiledFn get_encode_fn() {
 // already granted to each kernel instantiation on each device, each device's
 // opt-in limit, and encoded tensor maps of the B operands.
 std::mutex g_cache_mutex;
-int g_smem_granted[4][64] = {};
+int g_smem_granted[8][64] = {};
 int g_max_smem[64] = {};
 struct MapKey {
     const void* ptr;
@@ -1246,22 +1612,22 @@ struct MapKey {
 
 std::map<MapKey, CUtensorMap> g_maps;
 
-// B pieces viewed as a 2D tensor [rows_total][kdim] of BF16, boxes of
-// ch x box_rows, 64-byte (ch = 32) or 32-byte (ch = 16) swizzle.
-cudaError_t get_bmap(const UmmaArgs& a, cuuint64_t rows_total, int ch, int box_rows, EncodeTiledFn encode,
-                     CUtensorMap* out) {
+// A BF16 matrix viewed as a 2D tensor [rows][cols], boxes of ch x box_rows,
+// 64-byte (ch = 32) or 32-byte (ch = 16) swizzle.
+cudaError_t get_map2d(const __nv_bfloat16* ptr, cuuint64_t rows, int cols, int ch, int box_rows,
+                      EncodeTiledFn encode, CUtensorMap* out) {
     std::lock_guard<std::mutex> lock(g_cache_mutex);
-    const MapKey key{a.B, (int)rows_total, a.kdim, ch, box_rows};
+    const MapKey key{ptr, (int)rows, cols, ch, box_rows};
     auto it = g_maps.find(key);
     if (it != g_maps.end()) {
         *out = it->second;
         return cudaSuccess;
     }
-    const cuuint64_t gdim[2] = {(cuuint64_t)a.kdim, rows_total};
-    const cuuint64_t gstride[1] = {(cuuint64_t)a.kdim * 2};
+    const cuuint64_t gdim[2] = {(cuuint64_t)cols, rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
     const cuuint32_t box[2] = {(cuuint32_t)ch, (cuuint32_t)box_rows};
     const cuuint32_t estride[2] = {1, 1};
-    CUresult cr = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.B), gdim, gstride, box,
+    CUresult cr = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), gdim, gstride, box,
                          estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1269,6 +1635,12 @@ cudaError_t get_bmap(const UmmaArgs& a, cuuint64_t rows_total, int ch, int box_r
     if (g_maps.size() > 256) g_maps.clear();
     g_maps.emplace(key, *out);
     return cudaSuccess;
+}
+
+// B pieces viewed as a 2D tensor [rows_total][kdim].
+cudaError_t get_bmap(const UmmaArgs& a, cuuint64_t rows_total, int ch, int box_rows, EncodeTiledFn encode,
+                     CUtensorMap* out) {
+    return get_map2d(a.B, rows_total, a.kdim, ch, box_rows, encode, out);
 }
 
 template <int AM, int EM>
@@ -1345,6 +1717,57 @@ cudaError_t launch_core_resident(const UmmaArgs& a, int num_sms, cudaStream_t st
     return cudaGetLastError();
 }
 
+// The stage-2 core (Sec. 3.2).
+cudaError_t launch_core_stage2(const UmmaArgs& a, int num_sms, cudaStream_t stream, EncodeTiledFn encode) {
+    if (!a.s2_V || !a.s2_U || !a.s2_k16) return cudaErrorInvalidValue;
+    if (a.ndim % 16 != 0 || a.ndim < 16 || a.ndim > 512 - 2 * kS2Kmax || a.kdim % 16 != 0 || a.kdim <= 0)
+        return cudaErrorInvalidValue;
+    int dev = 0, max_smem = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return ce;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        if (!g_max_smem[dev]) {
+            ce = cudaDeviceGetAttribute(&g_max_smem[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (ce != cudaSuccess) return ce;
+        }
+        max_smem = g_max_smem[dev];
+    }
+    S2Layout L{};
+    L.kc1 = (a.kdim + 31) / 32;
+    L.nh = (a.ndim + kS2Part - 1) / kS2Part;
+    L.n_items = a.n_tiles;
+    L.stage_bytes = 3u * kTileM * 32u * 2u + 3u * kS2Kmax * 64u;
+    L.tbuf_off = kS2Stages * L.stage_bytes;
+    L.trans_off = L.tbuf_off + 9u * kTileM * 32u * 2u;
+    const uint32_t trans_bytes = kEpiWarps * 32 * kTransStride * 4;
+    const size_t smem = 2048 + (size_t)L.trans_off + trans_bytes;
+    if ((long)smem > (long)max_smem) return cudaErrorInvalidConfiguration;
+    if (L.n_items <= 0) return cudaSuccess;
+    CUtensorMap vmap, umap;
+    ce = get_map2d(a.s2_V, (cuuint64_t)3 * kOffsetsHost * kS2Kmax, a.kdim, 32, 16, encode, &vmap);
+    if (ce != cudaSuccess) return ce;
+    ce = get_map2d(a.s2_U, (cuuint64_t)3 * kOffsetsHost * a.ndim, kS2Kmax, 32, kS2Part, encode, &umap);
+    if (ce != cudaSuccess) return ce;
+    const int grid = num_sms < L.n_items ? num_sms : L.n_items;
+    auto go = [&](auto kern, int slot) -> cudaError_t {
+        {
+            std::lock_guard<std::mutex> lock(g_cache_mutex);
+            if (g_smem_granted[slot][dev] < (int)smem) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                g_smem_granted[slot][dev] = (int)smem;
+            }
+        }
+        kern<<<grid, kThreads, smem, stream>>>(vmap, umap, a, L);
+        return cudaGetLastError();
+    };
+    if (a.n_products == 6) return go(core_stage2_kernel<6>, 4);
+    if (a.n_products == 3) return go(core_stage2_kernel<3>, 5);
+    return go(core_stage2_kernel<1>, 6);
+}
+
 }  // namespace
 
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cudaStream_t stream) {
@@ -1359,6 +1782,7 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (a.ldd % 4 != 0) return cudaErrorInvalidValue;
     EncodeTiledFn encode = get_encode_fn();
     if (!encode) return cudaErrorNotSupported;
+    if (gather && a.s2_on) return launch_core_stage2(a, num_sms, stream, encode);
     if (gather && a.core_resident) {
         const cudaError_t e = launch_core_resident(a, num_sms, stream, encode);
         if (e != cudaErrorNotSupported) return e;

@@ -44,6 +44,18 @@ struct Factors {
 // Full host precompute, with the optional on-disk cache.  Returns a status.
 int compute_factors(const kifmm_m2l_params& prm, Factors& f);
 
+// Stage-2 per-offset factors (Sec. 3.2, Eq. eq-lra): K~_o = U_o S_o Q_o^T,
+// keep the k_o singular values >= eps2 * sigma_0(K_fat) with
+// eps2 = c2 * eps1 / r (Eq. eq-vareps2); Uhat_o = U_o[:, :k_o] (r x k_o),
+// Vhat_o = S Q^T restricted to those k_o (k_o x r), both row-major.
+struct Stage2 {
+    double c2 = 0, eps2 = 0;
+    std::vector<int> k;                   // [316]
+    std::vector<std::vector<double>> Uh;  // [316] r x k_o
+    std::vector<std::vector<double>> Vh;  // [316] k_o x r
+};
+int compute_stage2(const Factors& f, double c2, Stage2& s2);
+
 // Validate a params struct; returns a status and sets the error message.
 int check_params(const kifmm_m2l_params* prm);
 

@@ -216,6 +216,10 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
         a.b_groups = kOffsets;
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
+        a.s2_on = plan->s2_on;
+        a.s2_V = plan->s2V.ptr;
+        a.s2_U = plan->s2U.ptr;
+        a.s2_k16 = plan->s2_k16.ptr;
         a.row_src = row_src;
         a.row_dst = row_dst;
         a.tile_k = tile_k;

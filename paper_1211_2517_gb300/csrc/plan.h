@@ -118,6 +118,12 @@ struct kifmm_m2l_plan_s {
     int tune_variant = 2;
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
+    // stage 2 (Sec. 3.2): per-offset low-rank cores, off until kifmm_m2l_set_stage2
+    int s2_on = 0;
+    double s2_c2 = 0;
+    std::vector<int> s2_k;                     // [316] ranks k_o
+    kifmm::DevBuf<__nv_bfloat16> s2V, s2U;     // 3 BF16 pieces each
+    kifmm::DevBuf<int> s2_k16;                 // [316] k_o rounded up to 16
     kifmm::DevBuf<int> err_flag;
     std::map<std::pair<int, int>, std::unique_ptr<kifmm::LevelState>> levels;
     // multi-level batches keyed by (instance, level_lo, level_hi, adjoint)

@@ -489,6 +489,59 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
     return KIFMM_OK;
 }
 
+int compute_stage2(const Factors& f, double c2, Stage2& s2) {
+    if (!(c2 > 0) || f.r < 1 || f.sigma.empty()) {
+        set_error("stage 2 needs c2 > 0 and computed factors");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    const int r = f.r;
+    s2.c2 = c2;
+    s2.eps2 = c2 * (f.eps > 0 ? f.eps : 0.0) / r;
+    const double thr = s2.eps2 * f.sigma[0];
+    s2.k.assign(kOffsets, 0);
+    s2.Uh.assign(kOffsets, {});
+    s2.Vh.assign(kOffsets, {});
+    try {
+        ThreadTeam team(team_size());
+        team.run([&](int tid, int nt) {
+            ThreadTeam solo(1);
+            // the round-robin Jacobi pairs columns two by two: pad an odd r with
+            // a zero row and column (one extra zero singular value)
+            const int re = r + (r & 1);
+            std::vector<double> A, V, sig, u(r);
+            for (int o = tid; o < kOffsets; o += nt) {
+                const double* C = f.C.data() + (size_t)o * r * r;
+                // columns of K~_o, column-major, for the one-sided Jacobi SVD
+                A.assign((size_t)re * re, 0.0);
+                for (int c = 0; c < r; ++c)
+                    for (int i = 0; i < r; ++i) A[(size_t)c * re + i] = C[(size_t)i * r + c];
+                jacobi_svd(re, A, V, sig, solo);  // V: right singular vectors q_j (columns), sig descending
+                int k = 0;
+                while (k < r && sig[k] >= thr && sig[k] > 0) ++k;
+                s2.k[o] = k;
+                s2.Uh[o].assign((size_t)r * k, 0.0);
+                s2.Vh[o].assign((size_t)k * r, 0.0);
+                for (int j = 0; j < k; ++j) {
+                    const double* q = V.data() + (size_t)j * re;
+                    // u_j = K~_o q_j / sigma_j
+                    for (int a = 0; a < r; ++a) {
+                        double acc = 0;
+                        const double* ca = C + (size_t)a * r;
+                        for (int b = 0; b < r; ++b) acc += ca[b] * q[b];
+                        u[a] = acc / sig[j];
+                    }
+                    for (int a = 0; a < r; ++a) s2.Uh[o][(size_t)a * k + j] = u[a];
+                    for (int b = 0; b < r; ++b) s2.Vh[o][(size_t)j * r + b] = sig[j] * q[b];
+                }
+            }
+        });
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed in the stage-2 precompute");
+        return KIFMM_ERR_OOM;
+    }
+    return KIFMM_OK;
+}
+
 int build_pairs(int level, int n_boxes, const int32_t* ijk, std::vector<int32_t>& tgt, std::vector<int32_t>& src,
                 std::vector<int32_t>& off) {
     tgt.clear();

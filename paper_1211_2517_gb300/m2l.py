@@ -41,6 +41,19 @@ def factors_host(p: int, eps: float, d: float = 0.1):
     return sigma, U, C
 
 
+def stage2_host(p: int, eps: float, c2: float, d: float = 0.1):
+    """The library's host stage-2 factoring (Sec. 3.2): (ranks [316] int32,
+    truncated cores Uhat_o Vhat_o [316, r, r] float64)."""
+    prm = _params(p, eps, d, "fp32")
+    n, r = ctypes.c_int(0), ctypes.c_int(0)
+    call("kifmm_m2l_factors_host", ctypes.byref(prm), ctypes.byref(n), ctypes.byref(r), None, None, None)
+    k = np.zeros(_lib.N_OFFSETS, np.int32)
+    core = np.empty((_lib.N_OFFSETS, r.value, r.value))
+    call("kifmm_m2l_stage2_host", ctypes.byref(prm), float(c2), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+         core.ctypes.data)
+    return k, core
+
+
 def pairs_host(level: int, box_ijk):
     """Interaction-list pairs built by the library on the host.
 
@@ -211,6 +224,19 @@ class M2LPlan:
              _stream_handle(stream))
         return {"n_chunk": res.n_chunk, "contiguous": res.contiguous, "variant": res.variant,
                 "core_ms": res.core_ms, "from_cache": bool(res.from_cache)}
+
+    def set_stage2(self, c2: float) -> None:
+        """Per-offset low-rank cores (Sec. 3.2) with eps2 = c2 * eps / r;
+        c2 <= 0 switches them off (see kifmm_m2l_set_stage2)."""
+        call("kifmm_m2l_set_stage2", self._h, float(c2))
+
+    def stage2_ranks(self):
+        """The 316 per-offset ranks k_o of stage 2 (numpy int32)."""
+        import numpy as np
+
+        k = np.zeros(316, np.int32)
+        call("kifmm_m2l_stage2_ranks", self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return k
 
     def sync(self, stream=None) -> None:
         """Synchronise the stream and raise on device-side failures."""

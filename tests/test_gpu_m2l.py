@@ -441,6 +441,45 @@ def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["split6", "split3", "bf16"])
+def test_stage2_parity(g, oracle_factors, sphere_small, precision):
+    """Stage 2 (Sec. 3.2) with c2 = 1 on the p = 8 sphere: the library's
+    per-offset ranks equal the oracle's, and apply_levels (forward and
+    adjoint, levels 2..4, 3 rhs) and apply match the oracle's two-product
+    M2L; switching stage 2 off restores the single-stage operator."""
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    fac = om.stage2_factors(f, om.eps2_from_c2(1.0, 1e-7, f.r))
+    plan = make_plan(g, 8, 1e-7, precision, tree, (2, 3, 4))
+    plan.set_stage2(1.0)
+    k = plan.stage2_ranks()
+    assert np.array_equal(k, [uh.shape[1] for uh, _ in fac])
+    print(f"stage-2 ranks: min {k.min()} mean {k.mean():.1f} max {k.max()} (r = {f.r})")
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in (2, 3, 4)])).cuda()
+    for adjoint in (False, True):
+        out = plan.apply_levels(x_all, 2, 4, adjoint=adjoint).cpu().numpy()
+        plan.sync()
+        row = 0
+        for l in (2, 3, 4):
+            nb = tree.levels[l].shape[0]
+            fn = om.m2l_svd_stage2_adjoint if adjoint else om.m2l_svd_stage2
+            ref = fn(tree.levels[l], l, tree.r0, f, fac, qs[l].astype(np.float64))
+            err = rel(out[row:row + nb], ref)
+            print(f"stage2 {precision} adjoint={adjoint} level {l}: rel L2 {err:.3e}")
+            assert err <= TOL[precision], err
+            row += nb
+    ref = om.m2l_svd_stage2(tree.levels[4], 4, tree.r0, f, fac, qs[4].astype(np.float64))
+    out = plan.apply(torch.from_numpy(qs[4]).cuda(), 4)
+    plan.sync()
+    assert rel(out.cpu().numpy(), ref) <= TOL[precision]
+    plan.set_stage2(0.0)
+    out = plan.apply(torch.from_numpy(qs[4]).cuda(), 4)
+    plan.sync()
+    ref1 = om.m2l_svd(tree.levels[4], 4, tree.r0, f, qs[4].astype(np.float64))
+    assert rel(out.cpu().numpy(), ref1) <= TOL[precision]
+    plan.close()
+
+
 def test_full_size_torus_p10_sampled(g, oracle_factors):
     """The 4,194,304-point torus at depth 6, p = 10, eps = 1e-8, split6, all
     levels in one batch, on sampled targets the oracle computes one by one."""

@@ -137,3 +137,24 @@ def test_pairs_edge_cases(native):
     # too far apart (parents not adjacent): none
     tg, _, _ = native.pairs_host(3, np.array([[0, 0, 0], [4, 0, 0]]))
     assert tg.size == 0
+
+
+@pytest.mark.parametrize("p,eps,c2", [(4, 1e-4, 10.0), (6, 1e-7, 1.0)])
+def test_stage2_host_matches_oracle(native, oracle_factors, p, eps, c2):
+    """The library's FP64 stage-2 factoring (Sec. 3.2) against the oracle's:
+    the same per-offset ranks and the same truncated operators, compared
+    through U~ (Uhat_o Vhat_o) R~^T since the two precomputes pick different
+    bases of the same subspace."""
+    k, core = native.stage2_host(p, eps, c2, 0.1)
+    sigma, U, _ = native.factors_host(p, eps, 0.1)
+    f = oracle_factors(p, 0.1, eps)
+    fac = om.stage2_factors(f, om.eps2_from_c2(c2, eps, f.r))
+    ranks = np.array([uh.shape[1] for uh, _ in fac])
+    assert np.array_equal(k, ranks)
+    assert ranks.min() < f.r
+    kmax = np.abs(f.K).max()
+    for o in range(0, 316, 5):
+        uh, vh = fac[o]
+        a = U @ core[o] @ U.T
+        b = f.U @ (uh @ vh) @ f.R.T
+        assert np.abs(a - b).max() < 1e-10 * kmax, o

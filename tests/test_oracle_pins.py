@@ -335,3 +335,55 @@ def test_stage2_error_bounds(oracle_factors):
 
 def test_eps1_formula():
     assert m2l.eps1_from_c1(0.1, 6) == pytest.approx(0.1 * 2.0 ** -6 / 6)
+
+
+def _stage2_case():
+    pts, tree, q, p = _small_case(n=4000, p=4)
+    box = tree.levels[3]
+    rng = np.random.default_rng(11)
+    qq = rng.standard_normal((box.shape[0], 2, 6 * (p - 1) ** 2 + 2))
+    return tree, box, qq, p
+
+
+def test_stage2_m2l_reduces_to_stage1_without_truncation(oracle_factors):
+    # eps2 below every singular value of every core: Uhat_o Vhat_o = K~_o and
+    # the two-product form equals the single-stage compressed M2L
+    tree, box, qq, p = _stage2_case()
+    f = oracle_factors(p, 0.1, 1e-6)
+    fac = m2l.stage2_factors(f, 1e-300)
+    a = m2l.m2l_svd_stage2(box, 3, tree.r0, f, fac, qq)
+    b = m2l.m2l_svd(box, 3, tree.r0, f, qq)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_stage2_m2l_error_bound(oracle_factors):
+    # per target t: |p_s2 - p_1| <= s_l |U~|_2 sum_s sigma_{k_o+1}(K~_o) |q~_s|
+    # with |U~|_2 = 1 and sigma_{k_o+1} < eps2 sigma_0 (Eq. eq-lra truncation)
+    tree, box, qq, p = _stage2_case()
+    f = oracle_factors(p, 0.1, 1e-6)
+    eps2 = 3e-4
+    fac = m2l.stage2_factors(f, eps2)
+    assert min(uh.shape[1] for uh, _ in fac) < f.r
+    a = m2l.m2l_svd_stage2(box, 3, tree.r0, f, fac, qq)
+    b = m2l.m2l_svd(box, 3, tree.r0, f, qq)
+    tg, sr, ok = geo.interaction_lists(box)
+    qt = qq @ f.R
+    sl = m2l.level_scale(3, tree.r0)
+    bound = np.zeros(box.shape[0])
+    for t, s in zip(tg, sr):
+        bound[t] += sl * eps2 * f.sigma[0] * np.linalg.norm(qt[s])
+    err = np.linalg.norm(a - b, axis=2).max(axis=1) if a.ndim == 3 else np.linalg.norm(a - b, axis=1)
+    assert np.all(err <= bound * (1 + 1e-9) + 1e-13 * np.abs(b).max())
+    assert err.max() > 0  # the truncation is visible
+
+
+def test_stage2_adjoint_is_the_transpose(oracle_factors):
+    tree, box, qq, p = _stage2_case()
+    f = oracle_factors(p, 0.1, 1e-6)
+    fac = m2l.stage2_factors(f, m2l.eps2_from_c2(10.0, 1e-6, f.r))
+    rng = np.random.default_rng(12)
+    y = rng.standard_normal(qq.shape)
+    ax = m2l.m2l_svd_stage2(box, 3, tree.r0, f, fac, qq)
+    aty = m2l.m2l_svd_stage2_adjoint(box, 3, tree.r0, f, fac, y)
+    lhs, rhs = float(np.sum(ax * y)), float(np.sum(qq * aty))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(ax) * np.linalg.norm(y)
