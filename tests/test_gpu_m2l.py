@@ -569,3 +569,61 @@ def test_batch_matches_levels_and_graph_replay(g, oracle_factors):
         row += nb
     for pl in plans.values():
         pl.close()
+
+
+def test_batch64_full_config(g, oracle_factors):
+    """The 64-instance mixed batch at full size: ellipsoids with N
+    log-uniform in [5e4, 1e6], depth 3-6, p in {6, 8, 10}, 16 rhs each
+    (6.0M (box, rhs) rows, 8.2 GB of input), all M2L levels, in one grouped
+    batch captured into a CUDA graph and replayed; each instance against its
+    own batched-levels apply, and one instance per p against the oracle on
+    sampled targets of its deepest level."""
+    from paper_1211_2517_gb300 import apply_batch
+
+    inst = [synth.ellipsoid_instance(i) for i in range(64)]
+    plans = {p: g.M2LPlan(p, 1e-7, 0.1, "split6") for p in (6, 8, 10)}
+    items = []
+    for i, wl in enumerate(inst):
+        plan = plans[wl.p]
+        for l in range(2, wl.depth + 1):
+            plan.set_level(l, wl.tree.levels[l], wl.tree.r0, instance=i)
+        nb = sum(wl.tree.levels[l].shape[0] for l in range(2, wl.depth + 1))
+        x = torch.from_numpy(synth.random_box_densities32(nb, 16, plan.n, 5000 + i)).cuda()
+        items.append({"plan": plan, "instance": i, "level_lo": 2, "level_hi": wl.depth, "x": x,
+                      "out": torch.empty_like(x)})
+    rows = sum(it["x"].shape[0] * 16 for it in items)
+    print(f"batch64: {rows} (box, rhs) rows, {sum(it['x'].numel() for it in items) * 4 / 1e9:.2f} GB input")
+    apply_batch(items, use_graph=True)   # eager pass + capture
+    torch.cuda.synchronize()
+    first = [it["out"].clone() for it in items[:8]]
+    for it in items:
+        it["out"].fill_(float("nan"))
+    apply_batch(items, use_graph=True)   # graph replay
+    torch.cuda.synchronize()
+    for a, it in zip(first, items[:8]):
+        assert rel(it["out"].cpu().numpy(), a.cpu().numpy().astype(np.float64)) <= 1e-6
+    # each instance against its own batched-levels apply
+    for it in items[::7]:
+        ref = it["plan"].apply_levels(it["x"], 2, it["level_hi"], instance=it["instance"])
+        torch.cuda.synchronize()
+        err = float((it["out"] - ref).double().norm() / ref.double().norm())
+        assert err <= 1e-6, (it["instance"], err)
+    # one instance per p against the oracle, sampled targets of the deepest level
+    rng = np.random.default_rng(64)
+    for p in (6, 8, 10):
+        i = min((j for j, wl in enumerate(inst) if wl.p == p and wl.depth >= 4),
+                key=lambda j: inst[j].tree.levels[inst[j].depth].shape[0])
+        wl = inst[i]
+        f = oracle_factors(p, 0.1, 1e-7)
+        l = wl.depth
+        row0 = sum(wl.tree.levels[m].shape[0] for m in range(2, l))
+        nb = wl.tree.levels[l].shape[0]
+        q = items[i]["x"][row0:row0 + nb].cpu().numpy().astype(np.float64)
+        tg = np.sort(rng.choice(nb, size=min(16, nb), replace=False))
+        ref = om.m2l_svd_targets(wl.tree.levels[l], l, wl.tree.r0, f, q, tg)
+        out = items[i]["out"][row0:row0 + nb].cpu().numpy()[tg]
+        err = rel(out, ref)
+        print(f"batch64 instance {i} (p={p}, depth {l}, {nb} boxes): sampled rel L2 {err:.3e}")
+        assert err <= 1e-6, err
+    for plan in plans.values():
+        plan.close()
