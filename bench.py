@@ -166,6 +166,21 @@ def oracle_sample(wl, seconds_budget):
     return done_pairs, spent, "oracle.m2l.m2l_svd (NumPy FP64, BLAS) on " + "; ".join(parts)
 
 
+def job_throughput(local_ms: float, local_units: float, steps: int, device, world: int):
+    """Whole-job throughput of weak-scaled replicas: the units every rank
+    processed, summed, over the slowest rank's time (max over ranks).
+    Returns (units per second, max_ms, summed units)."""
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+    max_ms, units = float(t.item()), float(u.item())
+    return units * steps / (max_ms / 1e3), max_ms, units
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -306,14 +321,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = sampler.stop()
     plan.sync()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    units = torch.tensor([float(total_pairs)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(units, op=torch.distributed.ReduceOp.SUM)
-    max_ms = float(t.item())
-    job_pairs = float(units.item())
-    value = job_pairs * args.steps / (max_ms / 1e3)
+    value, max_ms, job_pairs = job_throughput(total_ms, total_pairs, args.steps, dev, world)
     launches_per_step = 3  # compression, core and expansion of all levels
 
     # ---- roofline of the core kernel (traced pass, same conditions) -----
@@ -357,12 +365,8 @@ def run_ours(args, rank, world, local_rank):
     k_e2e = min(args.steps, 50)
     e2e_ms = timed(e2e_step, k_e2e)
     h2d = hq.numel() * 4
-    e2e_value = total_pairs * k_e2e / (e2e_ms / 1e3)
-    te = torch.tensor([e2e_value], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MIN)
-        te *= world
-    e2e = {"value": float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
+    e2e_value, _, _ = job_throughput(e2e_ms, total_pairs, k_e2e, dev, world)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
 
     # ---- adjoint and the plain FP32 dense M2L on the same GPU -----------
     k_small = min(args.steps, 10)
@@ -477,12 +481,7 @@ def run_batch64(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = sampler.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    units = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(units, op=torch.distributed.ReduceOp.SUM)
-    max_ms = float(t.item())
+    value, max_ms, _ = job_throughput(total_ms, pairs, args.steps, dev, world)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -491,7 +490,7 @@ def run_batch64(args, rank, world, local_rank):
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     achieved = flops / (total_ms / args.steps / 1e3) / 1e12
     line = {
-        "metric": METRIC, "value": float(units.item()) * args.steps / (max_ms / 1e3), "unit": UNIT,
+        "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "batch64: 64 ellipsoid instances (axes U[0.5,2], N log-uniform 5e4-1e6, depth "
