@@ -322,7 +322,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     plan.sync()
     value, max_ms, job_pairs = job_throughput(total_ms, total_pairs, args.steps, dev, world)
-    launches_per_step = 3  # compression, core and expansion of all levels
+    launches_per_step = 5  # split + compression, core, split + expansion, over all levels
 
     # ---- roofline of the core kernel (traced pass, same conditions) -----
     k_prof = min(args.steps, 20)
@@ -502,7 +502,7 @@ def run_batch64(args, rank, world, local_rank):
                      "frac": achieved / bf16_peak, "traffic": None,
                      "kernel": "whole batch (compression, core and expansion of three operators)",
                      "flops_per_unit": "2 r^2 per box pair and rhs"},
-        "clocks": clocks, "e2e": None, "gpu_launches": 9 * args.steps, "cpu_baseline": None,
+        "clocks": clocks, "e2e": None, "gpu_launches": 15 * args.steps, "cpu_baseline": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -146,9 +146,10 @@ int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nr
 
 /* Compressed M2L of the consecutive registered levels level_lo..level_hi
  * of one instance as one batch (Step 3.1 over the downward pass's M2L
- * levels): the same result as kifmm_m2l_apply on each level, in three
- * kernel launches for all levels together (compression of every row, one
- * core over the levels' pairs merged by offset, expansion of every row).
+ * levels): the same result as kifmm_m2l_apply on each level, in five
+ * kernel launches for all levels together (split into BF16 pieces and
+ * compression of every row, one core over the levels' pairs merged by
+ * offset, split and expansion of every row).
  * q_up and p_down hold the levels' arrays back to back in level order:
  * [n_boxes(level_lo)][nrhs][n], then level_lo + 1, ...  DEVICE float32.
  * 0 <= level_lo <= level_hi < level_lo + 32; the merged pair list is built
@@ -176,8 +177,9 @@ typedef struct kifmm_m2l_batch_item {
 
 /* Compressed M2L of many FMM instances of uneven sizes (and of several
  * operators, e.g. different p) in one batch (Step 3.1 for every instance).
- * Items are grouped by plan; for each plan one persistent compression, one
- * core and one expansion launch cover all its items (the core walks one
+ * Items are grouped by plan; for each plan one split and one persistent
+ * compression launch, one core launch, and one split and one expansion
+ * launch cover all its items (the core walks one
  * offset-ordered tile list merged over every item and level).  Tables and
  * scratch of a batch are built on its first call and cached by the batch's
  * signature (plans, instances, levels, nrhs, pointers, beta); the cached

@@ -167,29 +167,13 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
 
     // 1. compression  q~ = R~^T q  (adjoint: U~^T pbar; R~ = U~, so one factor
     //    serves both directions), written as the core's operand; p~ = 0
+    const long vtiles = (rows + 127) / 128;
+    KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, 1);
-        UmmaArgs a{};
-        a.Af = x_in;
-        a.lda = n;
-        a.k_valid = n;
-        a.m_rows = (int)rows;
-        a.kdim = plan->n_pad;
-        a.B = plan->Rtb.ptr;
-        a.b_groups = 1;
-        a.ndim = rp;
-        a.n_chunk = chunk_for(rp);
-        a.ldd = rp;
-        a.alpha = 1.0f;
-        a.Dp = fp32_core ? nullptr : plan->qb.ptr;
-        a.dp_piece_stride = piece_stride;
-        a.dp_pieces = fp32_core ? 0 : plan->pieces;
-        a.Df = fp32_core ? plan->qt.ptr : nullptr;
-        a.Z = plan->pt.ptr;
-        a.n_products = 6;
-        a.hilo = 1;
-        a.error_flag = plan->err_flag.ptr;
-        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_SPLIT, a, plan->num_sms, s));
+        StageTimer timer(plan, s, 0, 2);
+        st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
+                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
+        if (st != KIFMM_OK) return st;
     }
 
     // 2. core over offset-grouped pairs
@@ -238,26 +222,9 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
 
     // 3. expansion  y = beta y + s_l U~ p~   (adjoint: R~ q~bar; R~ = U~)
     {
-        StageTimer timer(plan, s, 2, 1);
-        UmmaArgs a{};
-        a.Af = plan->pt.ptr;
-        a.lda = rp;
-        a.k_valid = rp;
-        a.m_rows = (int)rows;
-        a.kdim = rp;
-        a.B = plan->Ub.ptr;
-        a.b_groups = 1;
-        a.ndim = plan->n_pad;
-        a.n_chunk = chunk_for(plan->n_pad);
-        a.D = y_out;
-        a.ldd = n;
-        a.alpha = scale;
-        a.beta = beta;
-        a.n_valid = n;
-        a.n_products = 6;
-        a.hilo = 1;
-        a.error_flag = plan->err_flag.ptr;
-        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_STORE, a, plan->num_sms, s));
+        StageTimer timer(plan, s, 2, 2);
+        st = run_expand(plan, plan->pt.ptr, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, y_out, scale, beta, s);
+        if (st != KIFMM_OK) return st;
     }
     return KIFMM_OK;
 }
@@ -286,9 +253,9 @@ int get_multi_tiles(MultiState& ms, int nrhs, TileSet** out) {
     return KIFMM_OK;
 }
 
-// Levels lo..hi of one instance in three launches: compression of all their
-// rows, one core over the merged offset-ordered tiles (each tile scaled by
-// its level's s_l), expansion of all rows.
+// Levels lo..hi of one instance in five launches: split and compression of
+// all their rows, one core over the merged offset-ordered tiles (each tile
+// scaled by its level's s_l), split and expansion of all rows.
 int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, const float* x_in, float* y_out,
                  float beta, void* stream, bool adjoint) {
     if (!plan) {
@@ -337,29 +304,13 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
     TileSet* ts = nullptr;
     st = get_multi_tiles(*ms, nrhs, &ts);
     if (st != KIFMM_OK) return st;
+    const long vtiles = (rows + 127) / 128;
+    KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, 1);
-        UmmaArgs a{};
-        a.Af = x_in;
-        a.lda = n;
-        a.k_valid = n;
-        a.m_rows = (int)rows;
-        a.kdim = plan->n_pad;
-        a.B = plan->Rtb.ptr;
-        a.b_groups = 1;
-        a.ndim = rp;
-        a.n_chunk = chunk_for(rp);
-        a.ldd = rp;
-        a.alpha = 1.0f;
-        a.Dp = fp32_core ? nullptr : plan->qb.ptr;
-        a.dp_piece_stride = piece_stride;
-        a.dp_pieces = fp32_core ? 0 : plan->pieces;
-        a.Df = fp32_core ? plan->qt.ptr : nullptr;
-        a.Z = plan->pt.ptr;
-        a.n_products = 6;
-        a.hilo = 1;
-        a.error_flag = plan->err_flag.ptr;
-        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_SPLIT, a, plan->num_sms, s));
+        StageTimer timer(plan, s, 0, 2);
+        st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
+                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
+        if (st != KIFMM_OK) return st;
     }
     ScaleTable scales{};
     for (int l = lo; l <= hi; ++l) {
@@ -405,26 +356,9 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     }
     {
-        StageTimer timer(plan, s, 2, 1);
-        UmmaArgs a{};
-        a.Af = plan->pt.ptr;
-        a.lda = rp;
-        a.k_valid = rp;
-        a.m_rows = (int)rows;
-        a.kdim = rp;
-        a.B = plan->Ub.ptr;
-        a.b_groups = 1;
-        a.ndim = plan->n_pad;
-        a.n_chunk = chunk_for(plan->n_pad);
-        a.D = y_out;
-        a.ldd = n;
-        a.alpha = 1.0f;
-        a.beta = beta;
-        a.n_valid = n;
-        a.n_products = 6;
-        a.hilo = 1;
-        a.error_flag = plan->err_flag.ptr;
-        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_STORE, a, plan->num_sms, s));
+        StageTimer timer(plan, s, 2, 2);
+        st = run_expand(plan, plan->pt.ptr, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, y_out, 1.0f, beta, s);
+        if (st != KIFMM_OK) return st;
     }
     return KIFMM_OK;
 }
@@ -450,6 +384,87 @@ int core_chunk_default(kifmm_m2l_plan plan) {
     // than the lost overlap of epilogue and MMA
     if (plan->core_hilo && plan->products > 1 && 2 * rp > 512) return (rp / 2 + 15) / 16 * 16;
     return rp;
+}
+
+// N per work item of the identity-row GEMMs: <= 192 (96 running sums per
+// thread in the drained epilogue), split further while the tiles would not
+// fill two waves of CTAs.
+static int rows_chunk(int ndim, long n_tiles, int num_sms) {
+    int c = (ndim + 191) / 192;
+    while (n_tiles * c < 2L * num_sms && ndim / (c + 1) >= 64) ++c;
+    return ((ndim + c - 1) / c + 15) / 16 * 16;
+}
+
+size_t split_elems(kifmm_m2l_plan plan, long n_tiles) {
+    return (size_t)3 * 128 * (size_t)std::max<long>(n_tiles, 1) * (size_t)std::max(plan->n_pad, plan->rp);
+}
+
+int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* segs, int n_segs, int n_tiles,
+                 __nv_bfloat16* split, __nv_bfloat16* qb, long qb_stride, float* qt, float* pt, cudaStream_t s) {
+    if (n_tiles <= 0) return KIFMM_OK;
+    const int n = plan->n, np = plan->n_pad, rp = plan->rp;
+    const long sp_stride = (long)n_tiles * 128 * np;
+    KIFMM_CUDA_TRY(launch_split_rows(x, m_rows, n, n, np, segs, n_segs, n_tiles, split, sp_stride, 3, s));
+    UmmaArgs a{};
+    a.A = split;
+    a.a_piece_stride = sp_stride;
+    a.kdim = np;
+    a.B = plan->Rtb.ptr;
+    a.b_groups = 1;
+    a.ndim = rp;
+    a.n_chunk = rows_chunk(rp, n_tiles, plan->num_sms);
+    a.row_identity = 1;
+    a.n_tiles = n_tiles;
+    a.m_rows = m_rows;
+    a.segs = segs;
+    a.n_segs = n_segs;
+    a.seg_tiles = n_tiles;
+    a.ldd = rp;
+    a.alpha = 1.0f;
+    a.Dp = qt ? nullptr : qb;
+    a.dp_piece_stride = qb_stride;
+    a.dp_pieces = qt ? 0 : plan->pieces;
+    a.Df = qt;
+    a.Z = pt;
+    a.n_products = 6;
+    a.hilo = 1;
+    a.core_drain = 1;  // one K-chunk per drained partial: the long K of these GEMMs
+    a.error_flag = plan->err_flag.ptr;
+    KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_SPLIT, a, plan->num_sms, s));
+    return KIFMM_OK;
+}
+
+int run_expand(kifmm_m2l_plan plan, const float* pt, int m_rows, const RowSeg* segs, int n_segs, int n_tiles,
+               __nv_bfloat16* split, float* y, float alpha, float beta, cudaStream_t s) {
+    if (n_tiles <= 0) return KIFMM_OK;
+    const int n = plan->n, np = plan->n_pad, rp = plan->rp;
+    const long sp_stride = (long)n_tiles * 128 * rp;
+    KIFMM_CUDA_TRY(launch_split_rows(pt, m_rows, rp, rp, rp, segs, n_segs, n_tiles, split, sp_stride, 3, s));
+    UmmaArgs a{};
+    a.A = split;
+    a.a_piece_stride = sp_stride;
+    a.kdim = rp;
+    a.B = plan->Ub.ptr;
+    a.b_groups = 1;
+    a.ndim = np;
+    a.n_chunk = rows_chunk(np, n_tiles, plan->num_sms);
+    a.row_identity = 1;
+    a.n_tiles = n_tiles;
+    a.m_rows = m_rows;
+    a.segs = segs;
+    a.n_segs = n_segs;
+    a.seg_tiles = n_tiles;
+    a.D = y;
+    a.ldd = n;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.n_valid = n;
+    a.n_products = 6;
+    a.hilo = 1;
+    a.core_drain = 1;  // one K-chunk per drained partial: the long K of these GEMMs
+    a.error_flag = plan->err_flag.ptr;
+    KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_STORE, a, plan->num_sms, s));
+    return KIFMM_OK;
 }
 
 int check_device(kifmm_m2l_plan plan) {

@@ -42,6 +42,7 @@ struct PlanGroup {
     DevBuf<float> scales;
     TileSet tiles;
     DevBuf<__nv_bfloat16> qb;     // pieces of q~ [pieces][rows_total + 1][r_pad]
+    DevBuf<__nv_bfloat16> sp;     // BF16 pieces of the compression / expansion inputs
     DevBuf<float> pt;             // p~ [rows_total][r_pad]
 };
 
@@ -112,6 +113,7 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     // expansion reads p~ rows [base, base + rows) of the group's scratch
     KIFMM_CUDA_TRY(g.pt.ensure((size_t)std::max<long>(rows, 1) * plan->rp));
     KIFMM_CUDA_TRY(g.qb.ensure((size_t)(rows + 1) * plan->rp * std::max(plan->pieces, 1)));
+    KIFMM_CUDA_TRY(g.sp.ensure(split_elems(plan, tiles_so_far)));
     for (size_t i = 0; i < seg_out.size(); ++i) seg_out[i].Af = g.pt.ptr + ip[i].base * plan->rp;
     KIFMM_CUDA_TRY(g.seg_in.upload(seg_in.data(), seg_in.size()));
     KIFMM_CUDA_TRY(g.seg_out.upload(seg_out.data(), seg_out.size()));
@@ -151,34 +153,17 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     return KIFMM_OK;
 }
 
-// Enqueue the three launches of one plan group on stream s.
+// Enqueue the five launches of one plan group on stream s: split and
+// compression, core, split and expansion.
 int enqueue_group(PlanGroup& g, cudaStream_t s) {
     kifmm_m2l_plan plan = g.plan;
     if (g.rows_total == 0) return KIFMM_OK;
     const int n = plan->n, rp = plan->rp;
     const long piece_stride = (g.rows_total + 1) * rp;
     {
-        UmmaArgs a{};
-        a.lda = n;
-        a.k_valid = n;
-        a.kdim = plan->n_pad;
-        a.B = plan->Rtb.ptr;
-        a.b_groups = 1;
-        a.ndim = rp;
-        a.n_chunk = chunk_for(rp);
-        a.ldd = rp;
-        a.alpha = 1.0f;
-        a.Dp = g.qb.ptr;
-        a.dp_piece_stride = piece_stride;
-        a.dp_pieces = plan->pieces;
-        a.Z = g.pt.ptr;
-        a.n_products = 6;
-        a.hilo = 1;
-        a.segs = g.seg_in.ptr;
-        a.n_segs = (int)g.items.size();
-        a.seg_tiles = g.in_tiles;
-        a.error_flag = plan->err_flag.ptr;
-        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_SPLIT, a, plan->num_sms, s));
+        const int st = run_compress(plan, nullptr, 0, g.seg_in.ptr, (int)g.items.size(), g.in_tiles, g.sp.ptr,
+                                    g.qb.ptr, piece_stride, nullptr, g.pt.ptr, s);
+        if (st != KIFMM_OK) return st;
     }
     for (int pc = 0; pc < plan->pieces; ++pc)
         KIFMM_CUDA_TRY(cudaMemsetAsync(g.qb.ptr + pc * piece_stride + g.rows_total * rp, 0,
@@ -214,24 +199,9 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     }
     {
-        UmmaArgs a{};
-        a.lda = rp;
-        a.k_valid = rp;
-        a.kdim = rp;
-        a.B = plan->Ub.ptr;
-        a.b_groups = 1;
-        a.ndim = plan->n_pad;
-        a.n_chunk = chunk_for(plan->n_pad);
-        a.ldd = n;
-        a.alpha = 1.0f;
-        a.n_valid = n;
-        a.n_products = 6;
-        a.hilo = 1;
-        a.segs = g.seg_out.ptr;
-        a.n_segs = (int)g.items.size();
-        a.seg_tiles = g.in_tiles;
-        a.error_flag = plan->err_flag.ptr;
-        KIFMM_CUDA_TRY(launch_umma(A_ROWS, E_STORE, a, plan->num_sms, s));
+        const int st = run_expand(plan, nullptr, 0, g.seg_out.ptr, (int)g.items.size(), g.in_tiles, g.sp.ptr,
+                                  nullptr, 1.0f, 0.0f, s);
+        if (st != KIFMM_OK) return st;
     }
     return KIFMM_OK;
 }

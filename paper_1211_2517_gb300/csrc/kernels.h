@@ -48,8 +48,11 @@ cudaError_t launch_scale(float* x, long count, float beta, cudaStream_t stream);
 // tcgen05 (UMMA) split-BF16 GEMM with fused gather / scatter, one kernel
 // template for the three products of the compressed M2L:
 //   core      D[dst row] += A_pieces[src row] K~_o^T          (A_GATHER, E_RED)
-//   compress  Dp = pieces(alpha A_f32 W^T), Z = 0             (A_ROWS,   E_SPLIT)
-//   expand    D = alpha A_f32 W^T + beta D                    (A_ROWS,   E_STORE)
+//   compress  Dp = pieces(alpha A W^T), Z = 0                 (E_SPLIT)
+//   expand    D = alpha A W^T + beta D                        (E_STORE)
+// Compress and expand take A either as BF16 pieces pre-split by
+// launch_split_rows (A_GATHER with row_identity, drained partials) or as FP32
+// rows split inside the kernel (A_ROWS).
 // B operands are BF16 pieces [pieces][b_groups][ndim][kdim] read by TMA.
 enum UmmaAMode { A_GATHER = 0, A_ROWS = 1 };
 
@@ -66,6 +69,12 @@ struct RowSeg {
     float alpha, beta;
 };
 enum UmmaEMode { E_RED = 0, E_STORE = 1, E_SPLIT = 2 };
+
+// FP32 rows -> BF16 pieces [pieces][n_tiles * 128][ldo] (see split_rows_kernel):
+// virtual tile t takes rows of the single input A (n_segs = 0: rows
+// [128 t, 128 t + 128) of m_rows) or of the segment that owns tile t.
+cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int ldo, const RowSeg* segs, int n_segs,
+                              int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream);
 
 struct UmmaArgs {
     // A operand
@@ -96,6 +105,8 @@ struct UmmaArgs {
     int n_segs;
     int seg_tiles;            // rows modes with segments: total virtual row tiles
     int contiguous;           // core: 1 = each CTA takes a contiguous run of tiles
+    int row_identity;         // A_GATHER with E_SPLIT / E_STORE: tile t's A rows are 128 t + i (pre-split pieces),
+                              // outputs follow the rows-mode conventions (m_rows or segments)
     int core_resident;        // core, split6 with hilo: 1 = A tile resident in shared memory, K~_o in N blocks
     int core_drain;           // core, split6: K-chunks per partial drained into registers by 8 epilogue warps (0: off)
     // core, stage 2 (Sec. 3.2): K~_o = Uhat_o Vhat_o with per-offset rank k_o

@@ -147,6 +147,57 @@ __global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int col
     }
 }
 
+// Block (t, s) covers rows [16 s, 16 s + 16) of 128-row virtual tile t: the
+// rows of one segment (or of the single input) split into BF16 pieces,
+// output row t * 128 + r <- input row
+// (t - tile_begin) * 128 + r of the tile's segment; columns [cols, ldo) and
+// rows past the segment's m_rows are written as zero.  x = x_0 + x_1 + x_2
+// with each piece rounded to nearest from the remaining residual.
+__global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int lda, int cols, int ldo,
+                                  const RowSeg* __restrict__ segs, int n_segs, __nv_bfloat16* __restrict__ out,
+                                  long piece_stride, int pieces) {
+    const int t = blockIdx.x;  // virtual tile; blockIdx.y: 16-row slab of it
+    __shared__ int s_seg;
+    const float* src = A;
+    int m = m_rows;
+    long r0 = (long)t * 128;
+    if (n_segs > 0) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n_segs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (segs[mid].tile_begin <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            s_seg = lo;
+        }
+        __syncthreads();
+        const RowSeg sg = segs[s_seg];
+        src = sg.Af;
+        m = sg.m_rows;
+        r0 = (long)(t - sg.tile_begin) * 128;
+    }
+    const int c4n = ldo / 4;
+    for (int e = threadIdx.x; e < 16 * c4n; e += blockDim.x) {
+        const int r = blockIdx.y * 16 + e / c4n, c = (e % c4n) * 4;
+        const long row = r0 + r;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < m && c < cols) x = __ldg(reinterpret_cast<const float4*>(src + row * lda + c));
+        __nv_bfloat16* o = out + ((long)t * 128 + r) * ldo + c;
+        for (int p = 0; p < pieces; ++p) {
+            const __nv_bfloat162 a = __floats2bfloat162_rn(x.x, x.y), b = __floats2bfloat162_rn(x.z, x.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t*>(&a);
+            pk.y = *reinterpret_cast<const uint32_t*>(&b);
+            *reinterpret_cast<uint2*>(o + p * piece_stride) = pk;
+            x.x -= __low2float(a);
+            x.y -= __high2float(a);
+            x.z -= __low2float(b);
+            x.w -= __high2float(b);
+        }
+    }
+}
+
 __global__ void zero_kernel(float4* __restrict__ x, long n4) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n4; e += (long)gridDim.x * blockDim.x)
         x[e] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -190,6 +241,15 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_b
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     split_bf16_kernel<<<blocks, 256, 0, stream>>>(x, rows, cols, ld, out, piece_stride, pieces);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int ldo, const RowSeg* segs, int n_segs,
+                              int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if ((lda & 3) || (cols & 3) || (ldo & 3) || cols > ldo || pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
+    split_rows_kernel<<<dim3((unsigned)n_tiles, 8), 256, 0, stream>>>(A, m_rows, lda, cols, ldo, segs, n_segs, out,
+                                                                      piece_stride, pieces);
     return cudaGetLastError();
 }
 

@@ -367,9 +367,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             int srow[NR], nrow[NR], ngroup = 0;
             auto load_rows = [&](int item) {
                 const int t = item_tile(item);
+                if (args.row_identity) {
 #pragma unroll
-                for (int i = 0; i < NR; ++i) nrow[i] = __ldg(args.row_src + (long)t * kTileM + rl + RPI * i);
-                ngroup = __ldg(args.tile_k + t) & 0xFFFF;
+                    for (int i = 0; i < NR; ++i) nrow[i] = t * kTileM + rl + RPI * i;
+                    ngroup = 0;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NR; ++i) nrow[i] = __ldg(args.row_src + (long)t * kTileM + rl + RPI * i);
+                    ngroup = __ldg(args.tile_k + t) & 0xFFFF;
+                }
             };
             if (pw < P && i_beg < i_end) load_rows(i_beg);
             for (int item = i_beg; item < i_end && ok; item += i_step) {
@@ -615,20 +621,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         int pcount = 0;
         int e_nxt_row = -1, e_nxt_k = 0;
-        if (i_beg < i_end) {
+        if (EMODE == E_RED && i_beg < i_end) {
             const int t0 = item_tile(i_beg);
             e_nxt_row = __ldg(args.row_dst + (long)t0 * kTileM + q * 32 + lane);
             e_nxt_k = __ldg(args.tile_k + t0);
         }
         bool ok = true;
         for (int item = i_beg; item < i_end && ok; item += i_step) {
-            const long orow = e_nxt_row;
-            const float oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
-                                                  : args.level_scale[(e_nxt_k >> 16) & 31];
-            if (item + i_step < i_end) {
-                const int tn = item_tile(item + i_step);
-                e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + q * 32 + lane);
-                e_nxt_k = __ldg(args.tile_k + tn);
+            long orow = e_nxt_row;
+            float oscale = 1.0f;
+            float* e_dbase = args.D;
+            float e_alpha = args.alpha, e_beta = args.beta;
+            if (EMODE == E_RED) {
+                oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
+                                          : args.level_scale[(e_nxt_k >> 16) & 31];
+                if (item + i_step < i_end) {
+                    const int tn = item_tile(item + i_step);
+                    e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + q * 32 + lane);
+                    e_nxt_k = __ldg(args.tile_k + tn);
+                }
+            } else {
+                // identity rows (compression / expansion): the tile's segment
+                // gives the row of this lane in its input and its output
+                const int tt = item_tile(item);
+                long r = (long)tt * kTileM + q * 32 + lane;
+                long mrows = args.m_rows, obase = 0;
+                if (args.n_segs > 0) {
+                    const RowSeg sg = args.segs[find_seg(tt)];
+                    r = (long)(tt - sg.tile_begin) * kTileM + q * 32 + lane;
+                    mrows = sg.m_rows;
+                    obase = sg.out_row;
+                    e_dbase = sg.D;
+                    e_alpha = sg.alpha;
+                    e_beta = sg.beta;
+                }
+                orow = r < mrows ? (EMODE == E_SPLIT ? obase + r : r) : -1;
             }
             const int n0 = item_n0(item), nthis = item_nthis(item);
             const int nch = (nthis + 31) / 32;
@@ -687,10 +714,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int rr = pass * 4 + lane / 8;
                         const long grow = prow[pass];
                         if (grow < 0 || 4 * c4 >= ncols) continue;
-                        const float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
-                        red_add_v4(args.D + grow * args.ldd + n0 + c + 4 * c4, __float_as_uint(oscale * x.x),
-                                   __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
-                                   __float_as_uint(oscale * x.w));
+                        float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
+                        const int col = n0 + c + 4 * c4;
+                        if (EMODE == E_RED) {
+                            red_add_v4(args.D + grow * args.ldd + col, __float_as_uint(oscale * x.x),
+                                       __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
+                                       __float_as_uint(oscale * x.w));
+                        } else if (EMODE == E_STORE) {
+                            if (col < args.n_valid) {
+                                float4* dp = reinterpret_cast<float4*>(e_dbase + grow * args.ldd + col);
+                                float4 y = make_float4(e_alpha * x.x, e_alpha * x.y, e_alpha * x.z, e_alpha * x.w);
+                                if (e_beta != 0.f) {
+                                    const float4 o = *dp;
+                                    y.x = fmaf(e_beta, o.x, y.x);
+                                    y.y = fmaf(e_beta, o.y, y.y);
+                                    y.z = fmaf(e_beta, o.z, y.z);
+                                    y.w = fmaf(e_beta, o.w, y.w);
+                                }
+                                *dp = y;
+                            }
+                        } else {  // E_SPLIT
+                            x.x *= e_alpha;
+                            x.y *= e_alpha;
+                            x.z *= e_alpha;
+                            x.w *= e_alpha;
+                            if (args.Df) *reinterpret_cast<float4*>(args.Df + grow * args.ldd + col) = x;
+                            if (args.Z)
+                                *reinterpret_cast<float4*>(args.Z + grow * args.ldd + col) = make_float4(0.f, 0.f, 0.f, 0.f);
+                            uint32_t lo[3], hi[3];
+                            split3x2(x.x, x.y, lo, args.dp_pieces);
+                            split3x2(x.z, x.w, hi, args.dp_pieces);
+#pragma unroll
+                            for (int pc = 0; pc < 3; ++pc) {
+                                if (pc >= args.dp_pieces) break;
+                                *reinterpret_cast<uint2*>(args.Dp + pc * args.dp_piece_stride + grow * args.ldd + col) =
+                                    make_uint2(lo[pc], hi[pc]);
+                            }
+                        }
                     }
                     __syncwarp();
                 }
@@ -1596,7 +1656,7 @@ EncodeTiledFn get_encode_fn() {
 // already granted to each kernel instantiation on each device, each device's
 // opt-in limit, and encoded tensor maps of the B operands.
 std::mutex g_cache_mutex;
-int g_smem_granted[8][64] = {};
+int g_smem_granted[10][64] = {};
 int g_max_smem[64] = {};
 struct MapKey {
     const void* ptr;
@@ -1646,7 +1706,7 @@ cudaError_t get_bmap(const UmmaArgs& a, cuuint64_t rows_total, int ch, int box_r
 template <int AM, int EM>
 cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L, size_t smem, int grid,
                      cudaStream_t stream, int dev) {
-    const int inst = AM == A_GATHER ? 0 : (EM == E_STORE ? 1 : 2);
+    const int inst = AM == A_GATHER ? (EM == E_RED ? 0 : (EM == E_STORE ? 7 : 8)) : (EM == E_STORE ? 1 : 2);
     {
         std::lock_guard<std::mutex> lock(g_cache_mutex);
         if (g_smem_granted[inst][dev] < (int)smem) {
@@ -1776,7 +1836,7 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
         return cudaErrorInvalidValue;
     if (a.n_products != 1 && a.n_products != 3 && a.n_products != 6) return cudaErrorInvalidValue;
     const bool gather = amode == A_GATHER;
-    if (!((gather && emode == E_RED) || (!gather && (emode == E_STORE || emode == E_SPLIT))))
+    if (!((gather && (emode == E_RED || a.row_identity)) || (!gather && (emode == E_STORE || emode == E_SPLIT))))
         return cudaErrorInvalidValue;
     if (!gather && (a.k_valid % 4 != 0 || a.lda % 4 != 0 || a.k_valid > a.kdim)) return cudaErrorInvalidValue;
     if (a.ldd % 4 != 0) return cudaErrorInvalidValue;
@@ -1809,6 +1869,8 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
         L.n_acc = 2;
     }
     const long row_tiles = gather ? a.n_tiles : (a.n_segs > 0 ? (long)a.seg_tiles : ((long)a.m_rows + kTileM - 1) / kTileM);
+    if (gather && a.row_identity && a.n_tiles != (a.n_segs > 0 ? a.seg_tiles : (a.m_rows + kTileM - 1) / kTileM))
+        return cudaErrorInvalidValue;
     if (row_tiles * L.n_chunks > INT32_MAX) return cudaErrorInvalidValue;
     L.n_items = (int)(row_tiles * L.n_chunks);
     if (L.n_items <= 0) return cudaSuccess;
@@ -1831,12 +1893,15 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     uint32_t trans_bytes = (L.drain ? 2 : 1) * kEpiWarps * 32 * kTransStride * 4;
     int avail = max_smem - 2048 - (int)trans_bytes;
     L.stages = avail / (int)L.stage_bytes;
-    if (L.drain && (L.stages > 3 || L.stages < 2)) {
+    if (L.drain && L.stages > 3) L.stages = 3;  // producers are warps 4-6 when warps 7-10 drain
+    if (L.drain && L.stages < 2) {
         L.drain = 0;
         trans_bytes = kEpiWarps * 32 * kTransStride * 4;
         avail = max_smem - 2048 - (int)trans_bytes;
         L.stages = avail / (int)L.stage_bytes;
     }
+    // identity-row gathers (compression / expansion) have only the drained epilogue
+    if (gather && emode != E_RED && !L.drain) return cudaErrorNotSupported;
     if (L.stages > 8) L.stages = 8;
     if (L.stages < 2) return cudaErrorInvalidConfiguration;
     // gather mode: one ring slot per producer warp
@@ -1851,6 +1916,8 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (ce != cudaSuccess) return ce;
 
     const int grid = num_sms < L.n_items ? num_sms : L.n_items;
+    if (gather && emode == E_STORE) return launch_t<A_GATHER, E_STORE>(bmap, a, L, smem, grid, stream, dev);
+    if (gather && emode == E_SPLIT) return launch_t<A_GATHER, E_SPLIT>(bmap, a, L, smem, grid, stream, dev);
     if (gather) return launch_t<A_GATHER, E_RED>(bmap, a, L, smem, grid, stream, dev);
     if (emode == E_STORE) return launch_t<A_ROWS, E_STORE>(bmap, a, L, smem, grid, stream, dev);
     return launch_t<A_ROWS, E_SPLIT>(bmap, a, L, smem, grid, stream, dev);

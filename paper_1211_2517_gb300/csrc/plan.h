@@ -156,7 +156,7 @@ struct kifmm_m2l_plan_s {
     }
     // scratch shared by all levels (apply calls on one plan are serialised)
     kifmm::DevBuf<float> qt, pt;
-    kifmm::DevBuf<__nv_bfloat16> qb;
+    kifmm::DevBuf<__nv_bfloat16> qb, sp;  // sp: BF16 pieces of the compression / expansion inputs
 };
 
 
@@ -175,5 +175,21 @@ int core_chunk_default(kifmm_m2l_plan plan);
 int get_multi_state(kifmm_m2l_plan plan, int instance, int lo, int hi, bool adjoint, MultiState** out);
 // Drop cached batches that use `plan` (on destroy).
 void forget_batches_of(kifmm_m2l_plan plan);
+
+// Compression (Step 3.1's q~ = R~^T q): the FP32 rows (one buffer of m_rows
+// rows, or row segments over n_tiles virtual tiles) are split into BF16
+// pieces in `split` (>= 3 * 128 * n_tiles * n_pad elements), then a
+// tensor-core GEMM writes q~ as `pieces` BF16 pieces into qb (piece stride
+// qb_stride; or FP32 into qt when qt != nullptr) and zeroes p~ rows of pt.
+int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* segs, int n_segs, int n_tiles,
+                 __nv_bfloat16* split, __nv_bfloat16* qb, long qb_stride, float* qt, float* pt, cudaStream_t s);
+// Expansion (p = alpha U~ p~ + beta p): the FP32 p~ rows (pt, ld r_pad, or
+// segments) are split into BF16 pieces in `split` (>= 3 * 128 * n_tiles *
+// r_pad elements), then a tensor-core GEMM writes y (ld n) or, with
+// segments, each segment's D with its own alpha and beta.
+int run_expand(kifmm_m2l_plan plan, const float* pt, int m_rows, const RowSeg* segs, int n_segs, int n_tiles,
+               __nv_bfloat16* split, float* y, float alpha, float beta, cudaStream_t s);
+// Elements the split buffer of run_compress / run_expand needs.
+size_t split_elems(kifmm_m2l_plan plan, long n_tiles);
 
 }  // namespace kifmm
