@@ -18,8 +18,12 @@ Modules:
                stage-2 per-offset low-rank factors (Eq. eq-lra).
   upward    -- S2M / M2M (Eqs. eq-s2m, eq-m2m) to make realistic M2L inputs,
                and direct summation (Eq. eq_eval) for brute-force checks.
+  fmm       -- the complete evaluation for point sources: near field (S2T),
+               far field through S2M, M2M, M2L, L2L, L2T (Eqs. eq-s2m ..
+               eq-tran0), uncompressed and with Sec. 3.3's compressed
+               operators S~, M~, L~, T~; direct summation.
 
 Every function here is pinned by a ``-m "not gpu"`` test against a closed
 form, an invariant, a bound or brute force; none is "parity unpinned".
 """
-from . import geometry, m2l, upward  # noqa: F401
+from . import fmm, geometry, m2l, upward  # noqa: F401

@@ -21,11 +21,12 @@ from . import geometry as geo
 PINV_RCOND = 1e-12
 
 
-def check_to_equivalent(p: int, d: float, h: float) -> np.ndarray:
-    """Truncated-SVD pseudo-inverse of K(x^u, y^u) for a box of half-width h."""
+def check_to_equivalent(p: int, d: float, h: float, rcond: float = PINV_RCOND) -> np.ndarray:
+    """Truncated-SVD pseudo-inverse of K(x^u, y^u) for a box of half-width h
+    (singular values below rcond * sigma_max dropped)."""
     x = geo.surface_points(p, np.zeros(3), (3.0 - 2.0 * d) * h)
     y = geo.surface_points(p, np.zeros(3), (1.0 + d) * h)
-    return np.linalg.pinv(geo.laplace_kernel(x, y), rcond=PINV_RCOND)
+    return np.linalg.pinv(geo.laplace_kernel(x, y), rcond=rcond)
 
 
 def s2m(tree, points: np.ndarray, p: int, d: float, q_points: np.ndarray) -> np.ndarray:
