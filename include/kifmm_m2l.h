@@ -325,6 +325,66 @@ typedef struct kifmm_m2l_tune_result {
 int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                        const float* q_up, float* p_down, int reps, kifmm_m2l_tune_result* result, void* stream);
 
+/* ---- complete potential evaluation for point sources ------------------- */
+
+/* The potential of a point cloud on itself, p_i = sum_{j != i} G(x_i, x_j) q_j
+ * (Eq. eq_eval), evaluated as in the complete algorithm of Sec. 4 with the
+ * compressed upward and downward passes of Sec. 3.3:
+ *   near field  direct sums over the leaves sharing at least one vertex
+ *               with the point's leaf, that leaf included (Sec. 2.1);
+ *   far field   S~ = R~^T S at the leaves, M~ = R~^T M R~ up the tree, the
+ *               plan's compressed M2L cores on levels 2..depth, L~ = U~^T L U~
+ *               down the tree, T~ = T U~ at the leaves (Eqs. eq-s2m ..
+ *               eq-l2t with Sec. 3.3's operators).
+ * S, M, L, T are the KIFMM check / equivalent surface translations of
+ * Sec. 2.1: upward equivalent and downward check surfaces at half-width
+ * (1+d) h, upward check and downward equivalent surfaces at (3-2d) h; the
+ * check-to-equivalent solves use the pseudo-inverse that drops singular
+ * values below 1e-9 of the largest.  Every leaf sits at `depth`; the passes
+ * run on the tensor cores in the split6 arithmetic, the M2L core in the
+ * plan's precision, the leaf sums on the CUDA cores in FP32 with point
+ * coordinates relative to their leaf's centre. */
+typedef struct kifmm_fmm_s* kifmm_fmm;
+
+#define KIFMM_FMM_NEAR 1  /* near-field part (S2T)          */
+#define KIFMM_FMM_FAR  2  /* far-field part (S2M .. L2T)    */
+#define KIFMM_FMM_ALL  3
+
+/* Build the octree of a point cloud for `plan` (tensor-core precisions;
+ * KIFMM_PREC_FP32: KIFMM_ERR_UNSUPPORTED; n > 512, i.e. p > 10:
+ * KIFMM_ERR_UNSUPPORTED).
+ *   points   HOST float64 [n_points][3], 1 <= n_points < 2^30; copied.
+ *   depth    2..20; every leaf is a box of this level.
+ *   centre   HOST float64 [3], root cube centre, with r0 > 0 its half-width;
+ *            r0 <= 0 (centre may be NULL) takes the bounding box's midpoint
+ *            and half-width max half-extent * (1 + 2^-20).
+ * A point's box per coordinate is min(max(floor((x - (c - r0)) / (2 r0)
+ * 2^depth), 0), 2^depth - 1); empty boxes are skipped.  The first call on a
+ * plan also computes the pass operators (host FP64, about a second).  The
+ * tree registers its levels on the plan under instances >= 2^30; destroy
+ * every tree of a plan before the plan.  Errors: KIFMM_ERR_INVALID_ARG
+ * (NULL pointer, sizes, non-finite coordinates), KIFMM_ERR_OOM,
+ * KIFMM_ERR_CUDA. */
+int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points, int depth,
+                     const double* centre, double r0, kifmm_fmm* out);
+
+/* potential[i] = the parts (KIFMM_FMM_NEAR | KIFMM_FMM_FAR) of the
+ * potential at point i from the densities q.  q and potential: DEVICE
+ * float32 [n_points] in the caller's point order; potential is overwritten.
+ * Asynchronous on `stream`; calls on one tree (and on trees of one plan)
+ * must be serialised.  Errors: KIFMM_ERR_INVALID_ARG (NULL, parts out of
+ * 1..3), KIFMM_ERR_CUDA. */
+int kifmm_fmm_evaluate(kifmm_fmm fmm, const float* q, float* potential, int parts, void* stream);
+
+/* Sizes of a tree: depth, leaves, boxes on levels 2..depth, M2L pairs over
+ * those levels, and (target point, source point) pairs of the near field
+ * (the point itself excluded).  Any output may be NULL. */
+int kifmm_fmm_info(kifmm_fmm fmm, int* depth, int64_t* n_leaves, int64_t* n_boxes, int64_t* n_m2l_pairs,
+                   int64_t* n_near_pairs);
+
+/* Release a tree and its levels on the plan.  NULL is a no-op. */
+int kifmm_fmm_destroy(kifmm_fmm fmm);
+
 /* ---- host-side introspection (no GPU needed) ----------------------------- */
 
 /* Run the FP64 precompute of kifmm_m2l_precompute on the host only and copy
@@ -335,6 +395,18 @@ int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_lo, int leve
  * Call once with the arrays NULL to learn n and r. */
 int kifmm_m2l_factors_host(const kifmm_m2l_params* params, int* n, int* r,
                            double* sigma, double* U, double* C);
+
+/* The compressed pass operators of Sec. 3.3 that kifmm_fmm_create uses,
+ * computed on the host in FP64 for a unit parent box with the basis U~ of
+ * kifmm_m2l_factors_host (R~ = U~):
+ *   Ws [r][n]      U~^T E_u, E_u the pseudo-inverse of K(x^u, y^u) keeping
+ *                  singular values >= rcond * sigma_0 (*kept of them);
+ *                  S~ of a leaf of half-width h is h Ws K(x^u, points)
+ *   Mt [8][r][r]   U~^T E_u K(x^u, y^u of child c) U~ = M~ of the child in
+ *                  octant c = 4 b_x + 2 b_y + b_z (centre (2b - 1)/2)
+ * The downward operators are the transposes (T~'s factor Ws^T, L~_c =
+ * Mt[c]^T).  Any output may be NULL.  0 < rcond < 1. */
+int kifmm_m2l_pass_ops_host(const kifmm_m2l_params* params, double rcond, int* kept, double* Ws, double* Mt);
 
 /* Interaction-list pairs of a box set on the host (Sec. 2.1): for every
  * target t and source s in I^t, one entry (t, s, offset index of t - s).

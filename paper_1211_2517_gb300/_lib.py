@@ -34,6 +34,7 @@ EXPORTED = (
     "kifmm_m2l_set_stage2", "kifmm_m2l_stage2_ranks", "kifmm_m2l_stage2_host",
     "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
     "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error", "kifmm_m2l_version",
+    "kifmm_fmm_create", "kifmm_fmm_evaluate", "kifmm_fmm_info", "kifmm_fmm_destroy", "kifmm_m2l_pass_ops_host",
 )
 
 
@@ -96,6 +97,11 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_stage2_host": [ctypes.POINTER(Params), ctypes.c_double, pint, vp],
         "kifmm_m2l_factors_host": [ctypes.POINTER(Params), pint, pint, vp, vp, vp],
         "kifmm_m2l_pairs_host": [i32, i32, vp, pi64, vp, vp, vp],
+        "kifmm_fmm_create": [vp, i64, vp, i32, vp, f64, ctypes.POINTER(vp)],
+        "kifmm_fmm_evaluate": [vp, vp, vp, i32, vp],
+        "kifmm_fmm_info": [vp, pint, pi64, pi64, pi64, pi64],
+        "kifmm_fmm_destroy": [vp],
+        "kifmm_m2l_pass_ops_host": [ctypes.POINTER(Params), f64, pint, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)

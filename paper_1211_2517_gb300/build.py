@@ -22,7 +22,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkifmm_m2l.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["api.cu", "batch.cu", "kernels_simt.cu", "kernels_umma.cu", "noalloc.cu", "tune.cu"]
+CUDA_SOURCES = ["api.cu", "batch.cu", "fmm.cu", "kernels_fmm.cu", "kernels_simt.cu", "kernels_umma.cu", "noalloc.cu",
+                "tune.cu"]
 CXX_SOURCES = ["precompute.cpp"]
 
 

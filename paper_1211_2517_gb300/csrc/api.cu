@@ -325,35 +325,9 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         for (int pc = 0; pc < plan->pieces; ++pc)
             KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
                                            rp * sizeof(__nv_bfloat16), s));
-        UmmaArgs a{};
-        a.A = plan->qb.ptr;
-        a.a_piece_stride = piece_stride;
-        a.kdim = rp;
-        a.B = plan->Cb.ptr;
-        a.b_groups = kOffsets;
-        a.ndim = rp;
-        a.n_chunk = core_chunk(plan);
-        a.contiguous = plan->tune_contig;
-        a.core_resident = plan->tune_variant == 1;
-        a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
-        a.s2_on = plan->s2_on;
-        a.s2_V = plan->s2V.ptr;
-        a.s2_U = plan->s2U.ptr;
-        a.s2_k16 = plan->s2_k16.ptr;
-        a.row_src = ts->row_src.ptr;
-        a.row_dst = ts->row_dst.ptr;
-        a.tile_k = ts->tile_k.ptr;
-        a.n_tiles = ts->n_tiles;
-        a.nrhs = nrhs;
-        a.zero_row = (int)rows;
-        for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i];
-        a.D = plan->pt.ptr;
-        a.ldd = rp;
-        a.n_products = plan->products;
-        a.hilo = plan->core_hilo;
-        a.error_flag = plan->err_flag.ptr;
         StageTimer timer(plan, s, 1, 1);
-        KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+        st = launch_core(plan, plan->qb.ptr, piece_stride, (int)rows, *ts, nrhs, scales, plan->pt.ptr, s);
+        if (st != KIFMM_OK) return st;
     }
     {
         StageTimer timer(plan, s, 2, 2);
@@ -366,6 +340,57 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
 }  // namespace
 
 namespace kifmm {
+
+int multi_tileset(MultiState& ms, int nrhs, TileSet** out) { return get_multi_tiles(ms, nrhs, out); }
+
+int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride, int zero_row, const TileSet& ts,
+                int nrhs, const ScaleTable& scales, float* pt, cudaStream_t s) {
+    UmmaArgs a{};
+    a.A = qb;
+    a.a_piece_stride = piece_stride;
+    a.kdim = plan->rp;
+    a.B = plan->Cb.ptr;
+    a.b_groups = kOffsets;
+    a.ndim = plan->rp;
+    a.n_chunk = core_chunk(plan);
+    a.contiguous = plan->tune_contig;
+    a.core_resident = plan->tune_variant == 1;
+    a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
+    a.s2_on = plan->s2_on;
+    a.s2_V = plan->s2V.ptr;
+    a.s2_U = plan->s2U.ptr;
+    a.s2_k16 = plan->s2_k16.ptr;
+    a.row_src = ts.row_src.ptr;
+    a.row_dst = ts.row_dst.ptr;
+    a.tile_k = ts.tile_k.ptr;
+    a.n_tiles = ts.n_tiles;
+    a.nrhs = nrhs;
+    a.zero_row = zero_row;
+    for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i];
+    a.D = pt;
+    a.ldd = plan->rp;
+    a.n_products = plan->products;
+    a.hilo = plan->core_hilo;
+    a.error_flag = plan->err_flag.ptr;
+    KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+    return KIFMM_OK;
+}
+
+int upload_pieces(DevBuf<__nv_bfloat16>& dst, size_t per, const std::function<double(size_t)>& value_at) {
+    std::vector<uint16_t> h(per * 3, 0);
+    for (size_t e = 0; e < per; ++e) {
+        double v = value_at(e);
+        if (v == 0.0) continue;
+        for (int pc = 0; pc < 3; ++pc) {
+            const uint16_t b = bf16_bits_rn((float)v);
+            h[pc * per + e] = b;
+            v -= (double)bf16_to_float(b);
+        }
+    }
+    KIFMM_CUDA_TRY(dst.ensure(h.size()));
+    KIFMM_CUDA_TRY(cudaMemcpy(dst.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
+    return KIFMM_OK;
+}
 
 // N per work item of the compression / expansion GEMMs: <= 64, so that the
 // partial sums of a row fit in registers next to a loaded TMEM chunk, and
@@ -389,7 +414,7 @@ int core_chunk_default(kifmm_m2l_plan plan) {
 // N per work item of the identity-row GEMMs: <= 192 (96 running sums per
 // thread in the drained epilogue), split further while the tiles would not
 // fill two waves of CTAs.
-static int rows_chunk(int ndim, long n_tiles, int num_sms) {
+int rows_chunk(int ndim, long n_tiles, int num_sms) {
     int c = (ndim + 191) / 192;
     while (n_tiles * c < 2L * num_sms && ndim / (c + 1) >= 64) ++c;
     return ((ndim + c - 1) / c + 15) / 16 * 16;
@@ -546,6 +571,61 @@ LevelState* find_level(kifmm_m2l_plan plan, int instance, int level) {
 
 }  // namespace kifmm
 
+namespace kifmm {
+
+int register_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth, int n_boxes,
+                   const int32_t* box_ijk) {
+    int st = KIFMM_OK;
+    try {
+        std::vector<int32_t> tg, sr, of;
+        st = build_pairs(level, n_boxes, box_ijk, tg, sr, of);
+        if (st != KIFMM_OK) return st;
+        auto ls = std::make_unique<LevelState>();
+        ls->level = level;
+        ls->n_boxes = n_boxes;
+        ls->r0 = root_halfwidth;
+        ls->n_pairs = (int64_t)tg.size();
+        st = build_pairset(tg, sr, of, ls->fwd);
+        if (st != KIFMM_OK) return st;
+        // adjoint: target' = s, source' = t, offset' = -o; regroup by offset'
+        int offs[kOffsets][3];
+        offsets316(offs);
+        std::vector<int> neg(kOffsets);
+        for (int k = 0; k < kOffsets; ++k) neg[k] = offset_index(-offs[k][0], -offs[k][1], -offs[k][2]);
+        std::vector<int32_t> atg(tg.size()), asr(tg.size()), aof(tg.size());
+        // regroup by reversed offset, each group sorted by its new target
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> grp(kOffsets);
+        for (size_t i = 0; i < tg.size(); ++i) grp[neg[of[i]]].push_back({sr[i], tg[i]});
+        size_t w = 0;
+        for (int k = 0; k < kOffsets; ++k) {
+            std::sort(grp[k].begin(), grp[k].end());
+            for (auto& ts : grp[k]) {
+                atg[w] = ts.first;
+                asr[w] = ts.second;
+                aof[w] = k;
+                ++w;
+            }
+        }
+        st = build_pairset(atg, asr, aof, ls->adj);
+        if (st != KIFMM_OK) return st;
+        forget_batches_of(plan);
+        plan->levels[{instance, level}] = std::move(ls);
+        for (auto it = plan->multi.begin(); it != plan->multi.end();) {
+            const auto& key = it->first;
+            if (std::get<0>(key) == instance && std::get<1>(key) <= level && level <= std::get<2>(key))
+                it = plan->multi.erase(it);
+            else
+                ++it;
+        }
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    return KIFMM_OK;
+}
+
+}  // namespace kifmm
+
 extern "C" {
 
 const char* kifmm_m2l_last_error(void) { return kifmm::last_error(); }
@@ -642,20 +722,9 @@ int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out) {
         KIFMM_CUDA_TRY(plan->C.upload(h_c.data(), h_c.size()));
         // 3-piece BF16 splits of the FP64 factors: piece j = RN(x - earlier pieces)
         auto split_upload = [&](DevBuf<__nv_bfloat16>& dst, size_t per, auto value_at) -> int {
-            std::vector<uint16_t> h(per * 3, 0);
-            for (size_t e = 0; e < per; ++e) {
-                double v = value_at(e);
-                if (v == 0.0) continue;
-                for (int pc = 0; pc < 3; ++pc) {
-                    const uint16_t b = bf16_bits_rn((float)v);
-                    h[pc * per + e] = b;
-                    v -= (double)bf16_to_float(b);
-                }
-            }
-            KIFMM_CUDA_TRY(dst.ensure(h.size()));
-            KIFMM_CUDA_TRY(cudaMemcpy(dst.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
-            return KIFMM_OK;
+            return upload_pieces(dst, per, value_at);
         };
+        plan->U64 = f.U;
         // K~_o as [316][rp][rp]
         st = split_upload(plan->Cb, (size_t)kOffsets * rp * rp, [&](size_t e) -> double {
             const size_t k = e / ((size_t)rp * rp), a = (e / rp) % rp, b = e % rp;
@@ -690,7 +759,10 @@ int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out) {
 }
 
 int kifmm_m2l_destroy(kifmm_m2l_plan plan) {
-    if (plan) forget_batches_of(plan);
+    if (plan) {
+        forget_batches_of(plan);
+        detach_fmms(plan);
+    }
     delete plan;
     return KIFMM_OK;
 }
@@ -838,54 +910,13 @@ int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double roo
         set_error("instance must be >= 0 and root_halfwidth > 0");
         return KIFMM_ERR_INVALID_ARG;
     }
+    if (instance >= kReservedInstance) {
+        set_error("instances >= 2^30 are reserved for point-source evaluations");
+        return KIFMM_ERR_INVALID_ARG;
+    }
     int st = check_device(plan);
     if (st != KIFMM_OK) return st;
-    try {
-        std::vector<int32_t> tg, sr, of;
-        st = build_pairs(level, n_boxes, box_ijk, tg, sr, of);
-        if (st != KIFMM_OK) return st;
-        auto ls = std::make_unique<LevelState>();
-        ls->level = level;
-        ls->n_boxes = n_boxes;
-        ls->r0 = root_halfwidth;
-        ls->n_pairs = (int64_t)tg.size();
-        st = build_pairset(tg, sr, of, ls->fwd);
-        if (st != KIFMM_OK) return st;
-        // adjoint: target' = s, source' = t, offset' = -o; regroup by offset'
-        int offs[kOffsets][3];
-        offsets316(offs);
-        std::vector<int> neg(kOffsets);
-        for (int k = 0; k < kOffsets; ++k) neg[k] = offset_index(-offs[k][0], -offs[k][1], -offs[k][2]);
-        std::vector<int32_t> atg(tg.size()), asr(tg.size()), aof(tg.size());
-        // regroup by reversed offset, each group sorted by its new target
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> grp(kOffsets);
-        for (size_t i = 0; i < tg.size(); ++i) grp[neg[of[i]]].push_back({sr[i], tg[i]});
-        size_t w = 0;
-        for (int k = 0; k < kOffsets; ++k) {
-            std::sort(grp[k].begin(), grp[k].end());
-            for (auto& ts : grp[k]) {
-                atg[w] = ts.first;
-                asr[w] = ts.second;
-                aof[w] = k;
-                ++w;
-            }
-        }
-        st = build_pairset(atg, asr, aof, ls->adj);
-        if (st != KIFMM_OK) return st;
-        forget_batches_of(plan);
-        plan->levels[{instance, level}] = std::move(ls);
-        for (auto it = plan->multi.begin(); it != plan->multi.end();) {
-            const auto& key = it->first;
-            if (std::get<0>(key) == instance && std::get<1>(key) <= level && level <= std::get<2>(key))
-                it = plan->multi.erase(it);
-            else
-                ++it;
-        }
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return KIFMM_ERR_OOM;
-    }
-    return KIFMM_OK;
+    return register_level(plan, instance, level, root_halfwidth, n_boxes, box_ijk);
 }
 
 int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream) {

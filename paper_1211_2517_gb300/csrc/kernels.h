@@ -39,6 +39,24 @@ cudaError_t launch_pairs_gemm_fp32(const float* A, int lda, const float* W, int 
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* out, long piece_stride,
                               int pieces, cudaStream_t stream);
 
+// Point-source evaluation (kernels_fmm.cu).  Points in leaf order, leaf b
+// holding [leaf_start[b], leaf_start[b+1]), in leaf units s = (x - c_b) / h
+// split as hi (a multiple of 2^-12, w = density) + lo; usurf: the n points
+// of the [-1,1]^3 cube surface.
+// hi[i].w = q[perm[i]].
+cudaError_t launch_gather_density(const float* q, const int* perm, float4* hi, int n_points, cudaStream_t stream);
+// out[b][i] = scale * sum_{j in leaf b} q_j / |a u_i - s_j| (i < n <= 512),
+// out[b][n..ld) = 0.
+cudaError_t launch_leaf_check(const float4* hi, const float4* lo, const int* leaf_start, int n_leaves,
+                              const float4* usurf, int n, float a, float scale, float* out, int ld,
+                              cudaStream_t stream);
+// out[perm[i]] = scale * ((L2T from e[b][0..n) on a u, parts & 2) + (near
+// field over near_idx[near_start[b]..near_start[b+1]), parts & 1)).
+cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const int* leaf_start, const int4* leaf_ijk,
+                             const int* near_start, const int* near_idx, int n_leaves, const float4* usurf, int n,
+                             float a, float scale, const float* e, int lde, const int* perm, float* out, int parts,
+                             cudaStream_t stream);
+
 // Zero `count` floats.
 cudaError_t launch_zero(float* x, long count, cudaStream_t stream);
 
@@ -73,8 +91,11 @@ enum UmmaEMode { E_RED = 0, E_STORE = 1, E_SPLIT = 2 };
 // FP32 rows -> BF16 pieces [pieces][n_tiles * 128][ldo] (see split_rows_kernel):
 // virtual tile t takes rows of the single input A (n_segs = 0: rows
 // [128 t, 128 t + 128) of m_rows) or of the segment that owns tile t.
+// Output rows past the input's rows are zeroed, or left alone when
+// pad_rows == 0.
 cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int ldo, const RowSeg* segs, int n_segs,
-                              int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream);
+                              int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream,
+                              int pad_rows = 1);
 
 struct UmmaArgs {
     // A operand

@@ -151,11 +151,12 @@ __global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int col
 // rows of one segment (or of the single input) split into BF16 pieces,
 // output row t * 128 + r <- input row
 // (t - tile_begin) * 128 + r of the tile's segment; columns [cols, ldo) and
-// rows past the segment's m_rows are written as zero.  x = x_0 + x_1 + x_2
+// rows past the segment's m_rows are written as zero (skipped when
+// pad_rows == 0).  x = x_0 + x_1 + x_2
 // with each piece rounded to nearest from the remaining residual.
 __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int lda, int cols, int ldo,
                                   const RowSeg* __restrict__ segs, int n_segs, __nv_bfloat16* __restrict__ out,
-                                  long piece_stride, int pieces) {
+                                  long piece_stride, int pieces, int pad_rows) {
     const int t = blockIdx.x;  // virtual tile; blockIdx.y: 16-row slab of it
     __shared__ int s_seg;
     const float* src = A;
@@ -181,6 +182,7 @@ __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int l
     for (int e = threadIdx.x; e < 16 * c4n; e += blockDim.x) {
         const int r = blockIdx.y * 16 + e / c4n, c = (e % c4n) * 4;
         const long row = r0 + r;
+        if (!pad_rows && row >= m) continue;
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < m && c < cols) x = __ldg(reinterpret_cast<const float4*>(src + row * lda + c));
         __nv_bfloat16* o = out + ((long)t * 128 + r) * ldo + c;
@@ -245,11 +247,12 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_b
 }
 
 cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int ldo, const RowSeg* segs, int n_segs,
-                              int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream) {
+                              int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream,
+                              int pad_rows) {
     if (n_tiles <= 0) return cudaSuccess;
     if ((lda & 3) || (cols & 3) || (ldo & 3) || cols > ldo || pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
     split_rows_kernel<<<dim3((unsigned)n_tiles, 8), 256, 0, stream>>>(A, m_rows, lda, cols, ldo, segs, n_segs, out,
-                                                                      piece_stride, pieces);
+                                                                      piece_stride, pieces, pad_rows);
     return cudaGetLastError();
 }
 

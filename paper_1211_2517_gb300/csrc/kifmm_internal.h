@@ -56,6 +56,24 @@ struct Stage2 {
 };
 int compute_stage2(const Factors& f, double c2, Stage2& s2);
 
+// Compressed pass operators of Sec. 3.3 for a unit parent box, with the
+// basis U (n x r row-major) serving as both R~ and U~:
+//   Ws    = U~^T E_u                (r x n)   S~ of a leaf of half-width h is h Ws K(x^u, points)
+//   Mt[c] = U~^T E_u K(x^u, y^u_c) U~  (r x r)   M~ of the child in octant c
+// E_u is the pseudo-inverse of K(x^u, y^u) keeping the singular values
+// >= rcond * sigma_0 (their count in `kept`); octant c = 4 b_x + 2 b_y + b_z
+// puts the child's centre at (2 b - 1) / 2.  The downward operators are the
+// transposes: the downward check / equivalent surfaces are the upward
+// equivalent / check ones (Sec. 2.1), so K(x^d, y^d) = K(x^u, y^u)^T and
+// T~'s factor E_d U~ = Ws^T, L~_c = Mt[c]^T.
+struct PassOps {
+    double rcond = 0;
+    int kept = 0;
+    std::vector<double> Ws;  // [r][n]
+    std::vector<double> Mt;  // [8][r][r]
+};
+int compute_pass_ops(int p, double d, int r, const std::vector<double>& U, double rcond, PassOps& out);
+
 // Validate a params struct; returns a status and sets the error message.
 int check_params(const kifmm_m2l_params* prm);
 

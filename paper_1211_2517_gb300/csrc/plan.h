@@ -6,8 +6,10 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -18,6 +20,8 @@
 namespace kifmm {
 
 constexpr int kTileRows = 128;
+// Instances from 2^30 up hold the levels of point-source evaluations.
+constexpr int kReservedInstance = 1 << 30;
 
 #define KIFMM_CUDA_TRY(expr)                                                                        \
     do {                                                                                            \
@@ -118,6 +122,14 @@ struct kifmm_m2l_plan_s {
     int tune_variant = 2;
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
+    std::vector<double> U64;                   // [n][r] FP64 basis U~ (= R~)
+    // compressed pass operators of Sec. 3.3 (point-source evaluation), on first use:
+    // Ws [rp][n_pad] (S~ factor), Wt [n_pad][rp] (T~ factor), M~ and L~ [8][rp][rp]
+    double pass_rcond = 0;
+    int pass_kept = 0;
+    kifmm::DevBuf<__nv_bfloat16> Wsb, Wtb, Mb, Lb;  // 3 BF16 pieces each
+    int next_fmm_instance = 0;
+    std::set<kifmm_fmm_s*> fmms;  // live point-source trees on this plan
     // stage 2 (Sec. 3.2): per-offset low-rank cores, off until kifmm_m2l_set_stage2
     int s2_on = 0;
     double s2_c2 = 0;
@@ -175,6 +187,9 @@ int core_chunk_default(kifmm_m2l_plan plan);
 int get_multi_state(kifmm_m2l_plan plan, int instance, int lo, int hi, bool adjoint, MultiState** out);
 // Drop cached batches that use `plan` (on destroy).
 void forget_batches_of(kifmm_m2l_plan plan);
+// Unlink the point-source trees of `plan` (on destroy); their later calls
+// fail with KIFMM_ERR_STATE and their destroy only frees them.
+void detach_fmms(kifmm_m2l_plan plan);
 
 // Compression (Step 3.1's q~ = R~^T q): the FP32 rows (one buffer of m_rows
 // rows, or row segments over n_tiles virtual tiles) are split into BF16
@@ -191,5 +206,21 @@ int run_expand(kifmm_m2l_plan plan, const float* pt, int m_rows, const RowSeg* s
                __nv_bfloat16* split, float* y, float alpha, float beta, cudaStream_t s);
 // Elements the split buffer of run_compress / run_expand needs.
 size_t split_elems(kifmm_m2l_plan plan, long n_tiles);
+// N per work item of the identity-row GEMMs over n_tiles row tiles.
+int rows_chunk(int ndim, long n_tiles, int num_sms);
+// Tile set of a multi-level state for nrhs (built on first use).
+int multi_tileset(MultiState& ms, int nrhs, TileSet** out);
+// The tensor-core core over a tile set: pt[dst] += scale K~_o qb[src], with
+// qb the plan's BF16 pieces (piece stride piece_stride, zero row zero_row);
+// stage 2 and the autotuned variant as set on the plan.
+int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride, int zero_row, const TileSet& ts,
+                int nrhs, const ScaleTable& scales, float* pt, cudaStream_t s);
+// Upload value_at(e), e < per, as 3 BF16 pieces [3][per] (piece j = RN of
+// the remainder of the earlier pieces).
+int upload_pieces(DevBuf<__nv_bfloat16>& dst, size_t per, const std::function<double(size_t)>& value_at);
+// Interaction state of one level of one instance (kifmm_m2l_set_level
+// without its argument checks).
+int register_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth, int n_boxes,
+                   const int32_t* box_ijk);
 
 }  // namespace kifmm

@@ -258,8 +258,10 @@ std::vector<double> tsqr_kfat_t(int p, double d, const std::vector<double>& u, T
 
 // One-sided Jacobi on A (n x n column-major, n even).  On return V holds
 // the right singular vectors (column-major) and sig the singular values,
-// both sorted by descending singular value.
-void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& sig, ThreadTeam& team) {
+// both sorted by descending singular value; when AV is given it receives
+// the rotated columns A v_j = sigma_j u_j in the same order.
+void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& sig, ThreadTeam& team,
+                std::vector<double>* AV = nullptr) {
     V.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) V[i + (size_t)i * n] = 1.0;
     const double tol = 1e-15;
@@ -322,9 +324,13 @@ void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& V, std::vect
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return s[x] > s[y]; });
     std::vector<double> Vs((size_t)n * n);
     sig.resize(n);
+    if (AV) AV->resize((size_t)n * n);
     for (int j = 0; j < n; ++j) {
         sig[j] = s[ord[j]];
         std::copy(V.begin() + (size_t)ord[j] * n, V.begin() + (size_t)(ord[j] + 1) * n, Vs.begin() + (size_t)j * n);
+        if (AV)
+            std::copy(A.begin() + (size_t)ord[j] * n, A.begin() + (size_t)(ord[j] + 1) * n,
+                      AV->begin() + (size_t)j * n);
     }
     V.swap(Vs);
 }
@@ -537,6 +543,92 @@ int compute_stage2(const Factors& f, double c2, Stage2& s2) {
         });
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed in the stage-2 precompute");
+        return KIFMM_ERR_OOM;
+    }
+    return KIFMM_OK;
+}
+
+int compute_pass_ops(int p, double d, int r, const std::vector<double>& U, double rcond, PassOps& out) {
+    const int n = surface_count(p);
+    if (r < 1 || (int)U.size() != n * r || !(rcond > 0) || !(rcond < 1)) {
+        set_error("pass operators need the stage-1 basis and 0 < rcond < 1");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    const std::vector<double> u = unit_surface(p);
+    constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+    auto G = [&](const double* x, const double* y) {
+        const double a = x[0] - y[0], b = x[1] - y[1], c = x[2] - y[2];
+        return kInv4Pi / std::sqrt(a * a + b * b + c * c);
+    };
+    try {
+        ThreadTeam team(team_size());
+        // upward check surface x^u ((3-2d) u) and equivalent surface y^u ((1+d) u) of a unit box
+        std::vector<double> xu((size_t)3 * n), yu((size_t)3 * n);
+        for (int i = 0; i < 3 * n; ++i) {
+            xu[i] = (3.0 - 2.0 * d) * u[i];
+            yu[i] = (1.0 + d) * u[i];
+        }
+        // A = K(x^u, y^u), column-major
+        std::vector<double> A((size_t)n * n), V, sig, AV;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) A[(size_t)j * n + i] = G(&xu[3 * i], &yu[3 * j]);
+        jacobi_svd(n, A, V, sig, team, &AV);
+        int kept = 0;
+        while (kept < n && sig[kept] >= rcond * sig[0] && sig[kept] > 0) ++kept;
+        // E_u = pinv(A) = sum_k v_k (A v_k)^T / sigma_k^2, row-major [n][n]
+        std::vector<double> E((size_t)n * n, 0.0);
+        team.run([&](int tid, int nt) {
+            for (int i = tid; i < n; i += nt) {
+                double* ei = E.data() + (size_t)i * n;
+                for (int k = 0; k < kept; ++k) {
+                    const double w = V[(size_t)k * n + i] / (sig[k] * sig[k]);
+                    const double* ak = AV.data() + (size_t)k * n;
+                    for (int j = 0; j < n; ++j) ei[j] += w * ak[j];
+                }
+            }
+        });
+        // Ws = U~^T E_u  [r][n]
+        out.Ws.assign((size_t)r * n, 0.0);
+        team.run([&](int tid, int nt) {
+            for (int a = tid; a < r; a += nt) {
+                double* wa = out.Ws.data() + (size_t)a * n;
+                for (int i = 0; i < n; ++i) {
+                    const double uia = U[(size_t)i * r + a];
+                    const double* ei = E.data() + (size_t)i * n;
+                    for (int j = 0; j < n; ++j) wa[j] += uia * ei[j];
+                }
+            }
+        });
+        // Mt[c] = U~^T E_u K(x^u, y^u of child c) U~ = Ws K_c U~; child c of a
+        // unit parent: centre (2 b - 1) / 2 with c = 4 b_x + 2 b_y + b_z,
+        // half-width 1/2
+        out.Mt.assign((size_t)8 * r * r, 0.0);
+        team.run([&](int tid, int nt) {
+            std::vector<double> yc((size_t)3 * n), T((size_t)r * n);
+            for (int c = tid; c < 8; c += nt) {
+                const double ctr[3] = {((c >> 2) & 1) - 0.5, ((c >> 1) & 1) - 0.5, (c & 1) - 0.5};
+                for (int j = 0; j < n; ++j)
+                    for (int t = 0; t < 3; ++t) yc[3 * j + t] = ctr[t] + 0.5 * (1.0 + d) * u[3 * j + t];
+                // T = Ws K_c  [r][n]
+                std::fill(T.begin(), T.end(), 0.0);
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) {
+                        const double kij = G(&xu[3 * i], &yc[3 * j]);
+                        for (int a = 0; a < r; ++a) T[(size_t)a * n + j] += out.Ws[(size_t)a * n + i] * kij;
+                    }
+                double* m = out.Mt.data() + (size_t)c * r * r;
+                for (int a = 0; a < r; ++a)
+                    for (int j = 0; j < n; ++j) {
+                        const double taj = T[(size_t)a * n + j];
+                        const double* uj = U.data() + (size_t)j * r;
+                        for (int b = 0; b < r; ++b) m[(size_t)a * r + b] += taj * uj[b];
+                    }
+            }
+        });
+        out.rcond = rcond;
+        out.kept = kept;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed in the pass-operator precompute");
         return KIFMM_ERR_OOM;
     }
     return KIFMM_OK;

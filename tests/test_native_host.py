@@ -32,7 +32,7 @@ def native():
 
 def test_library_exports_every_header_symbol(native):
     hdr = open(os.path.join(ROOT, "include", "kifmm_m2l.h")).read()
-    declared = set(re.findall(r"^(?:int|const char\*)\s+(kifmm_m2l_\w+)\(", hdr, flags=re.M))
+    declared = set(re.findall(r"^(?:int|const char\*)\s+(kifmm_\w+)\(", hdr, flags=re.M))
     assert declared == set(native.EXPORTED)
     L = native.lib()
     for name in declared:
@@ -158,3 +158,32 @@ def test_stage2_host_matches_oracle(native, oracle_factors, p, eps, c2):
         a = U @ core[o] @ U.T
         b = f.U @ (uh @ vh) @ f.R.T
         assert np.abs(a - b).max() < 1e-10 * kmax, o
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_pass_ops_host_matches_oracle(native, p):
+    """The library's FP64 pass operators of Sec. 3.3 against the oracle's,
+    compared through the basis: U~ Ws = P E_u and U~ M~_c U~^T = P M_c P with
+    P the projector on the M2L basis (the two precomputes pick different
+    bases of the same subspace).  The pseudo-inverse with the 1e-9 cutoff
+    carries noise of about 1e-9 relative along the cut directions."""
+    from oracle import fmm as ofmm
+
+    eps = 1e-7
+    kept, Ws, Mt = native.pass_ops_host(p, eps, 0.1, ofmm.FMM_RCOND)
+    _, U, _ = native.factors_host(p, eps, 0.1)
+    f = om.svd_factors(p, 0.1, eps)
+    ops = ofmm.pass_operators(f, p, 0.1)
+    n = U.shape[0]
+    assert 0 < kept <= n
+    a, b = U @ Ws, f.R @ ops.Ws
+    assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(b)
+    for c in range(8):
+        a = U @ Mt[c] @ U.T
+        b = f.R @ ops.Mt[c] @ f.R.T
+        assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(b), c
+    # L~_c = M~_c^T: the oracle forms L from the downward surfaces itself
+    for c in (1, 6):
+        a = U @ Mt[c].T @ U.T
+        b = f.U @ ops.Lt[c] @ f.U.T
+        assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(b), c
