@@ -328,15 +328,18 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
             h_lo[s] = make_float4(lv[0], lv[1], lv[2], 0.f);
         }
         const int64_t nt = leaf_start[b + 1] - leaf_start[b];
+        // the leaf itself first, then its neighbours
+        near_idx.push_back(b);
+        f->n_near += nt * (nt - 1);
         for (int dx = -1; dx <= 1; ++dx)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dz = -1; dz <= 1; ++dz) {
                     const int64_t x = lijk[3 * b] + dx, y = lijk[3 * b + 1] + dy, z = lijk[3 * b + 2] + dz;
                     if (x < 0 || y < 0 || z < 0 || x >= m || y >= m || z >= m) continue;
                     const int s = find(L, morton((uint32_t)x, (uint32_t)y, (uint32_t)z));
-                    if (s < 0) continue;
+                    if (s < 0 || s == b) continue;
                     near_idx.push_back(s);
-                    f->n_near += nt * (leaf_start[s + 1] - leaf_start[s]) - (s == b ? nt : 0);
+                    f->n_near += nt * (leaf_start[s + 1] - leaf_start[s]);
                 }
         near_start[b + 1] = (int32_t)near_idx.size();
     }
