@@ -2,7 +2,7 @@
 """Benchmark of the SVD-compressed M2L translation on GB300.
 
 One step = one batched compressed M2L apply (V^T compression, offset-grouped
-core products over the interaction lists, U expansion; three kernel
+core products over the interaction lists, U expansion; five kernel
 launches) over every level 2..6 of the synthetic 2,097,152-point sphere
 workload (depth 6, p = 8, n = 296,
 eps = 1e-7, d = 0.1, one right-hand side), i.e. 1,158,296 box-pair
@@ -12,8 +12,10 @@ L2 is flushed (a 256 MB write) before every timed step.
 Prints ONE JSON line (rank 0).  Besides the throughput it reports the
 tensor roofline of the core kernel (tracing with CUDA events), an end-to-end
 number through the public API with pinned host buffers, the plain FP32
-dense M2L on the same GPU, the adjoint, SM clocks sampled during the timed
-region, and the FP64 oracle timed on the host cores (cpu_baseline).
+dense M2L on the same GPU, the adjoint, stage 2 (Sec. 3.2), the complete
+evaluation of the workload's point potentials with the compressed passes
+(Sec. 3.3; key "fmm"), SM clocks sampled during the timed region, and the
+FP64 oracle timed on the host cores (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -400,6 +402,35 @@ def run_ours(args, rank, world, local_rank):
                   "core_ms_per_step": s2_stage["core"] / min(k_s2, 20),
                   "parity": "tests/test_gpu_m2l.py::test_stage2_parity against the oracle's two-product M2L"}
 
+    # ---- complete evaluation for the workload's points (Sec. 4 with the
+    # compressed passes of Sec. 3.3): near field + S~, M~, M2L, L~, T~ ------
+    fmm = None
+    if args.precision != "fp32":
+        from paper_1211_2517_gb300 import PointFMM
+
+        ftree = PointFMM(plan, wl.points, wl.depth)
+        qd = torch.tensor(wl.densities, dtype=torch.float32, device=dev)
+        pot = torch.empty_like(qd)
+        for parts in (3, 1, 2):
+            for _ in range(3):
+                ftree.evaluate(qd, parts, out=pot)
+        k_f = min(args.steps, 20)
+        torch.cuda.nvtx.range_push("fmm_evaluate")
+        f_ms = timed(lambda: ftree.evaluate(qd, 3, out=pot), k_f)
+        torch.cuda.nvtx.range_pop()
+        near_ms = timed(lambda: ftree.evaluate(qd, 1, out=pot), k_f)
+        far_ms = timed(lambda: ftree.evaluate(qd, 2, out=pot), k_f)
+        info = ftree.info()
+        npts = wl.points.shape[0]
+        fmm = {"value": npts * k_f / (f_ms / 1e3), "unit": "points/s (potential at every point from all others)",
+               "ms_per_evaluate": f_ms / k_f, "near_ms": near_ms / k_f, "far_ms": far_ms / k_f,
+               "points": npts, "depth": info["depth"], "leaves": info["leaves"], "m2l_pairs": info["m2l_pairs"],
+               "near_pairs": info["near_pairs"],
+               "near_pairs_per_s": info["near_pairs"] * k_f / (near_ms / 1e3),
+               "parity": "tests/test_gpu_fmm.py: within 1e-6 relative L2 of the FP64 oracle's compressed FMM and "
+                         "of the direct sum"}
+        ftree.close()
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -414,6 +445,7 @@ def run_ours(args, rank, world, local_rank):
                                 "speedup_compressed_over_dense": per_gpu_value / dense_value},
         "adjoint": {"value": total_pairs * k_small / (adj_ms / 1e3), "unit": UNIT},
         "stage2": stage2,
+        "fmm": fmm,
         "parity": "tests/test_gpu_m2l.py: split6 and fp32 within 1e-6 relative L2 of the FP64 oracle",
     }
 
