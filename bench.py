@@ -324,7 +324,8 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     plan.sync()
     value, max_ms, job_pairs = job_throughput(total_ms, total_pairs, args.steps, dev, world)
-    launches_per_step = 5  # split + compression, core, split + expansion, over all levels
+    # split + compression (+ the scaled FP16 split for f16x3), core, split + expansion, over all levels
+    launches_per_step = 6 if args.precision == "f16x3" else 5
 
     # ---- roofline of the core kernel (traced pass, same conditions) -----
     k_prof = min(args.steps, 20)
@@ -335,21 +336,27 @@ def run_ours(args, rank, world, local_rank):
     core_ms = stage_ms["core"] / k_prof
     flops_step = 2.0 * r * r * total_pairs
     achieved = flops_step / (core_ms / 1e3) / 1e12
-    issued = {"split6": 6, "split3": 3, "bf16": 1}.get(args.precision, 0) * 2.0 * rp * rp * total_pairs
+    issued = {"split6": 6, "split3": 3, "bf16": 1, "f16x3": 3}.get(args.precision, 0) * 2.0 * rp * rp * total_pairs
     traffic = recorded_traffic()
     roofline = {
         "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
         "frac": achieved / bf16_peak, "traffic": traffic,
         "kernel": {1: "core_resident_kernel (A-resident split6 core, K~_o in column blocks)",
-                   2: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, per-K-chunk partials drained)"}.get(
+                   2: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 2 K-chunks drained)",
+                   3: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 1 K-chunk drained)",
+                   6: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks drained)"}.get(
                        (tune or {}).get("variant"), "umma_kernel<A_GATHER,E_RED> (offset-grouped core)"),
+        "core_dtype": {"f16x3": "fp16 pieces x fp16 pieces, fp32 accumulate (3 products)",
+                       "split6": "bf16 pieces, fp32 accumulate (6 products)"}.get(args.precision, args.precision),
         "algorithmic_flops_per_step": flops_step,
         "flops_per_unit": f"2 r^2 = {2 * r * r} per box pair (r = {r})",
         "launches_per_step": 1,
         "core_ms_per_step": core_ms,
         "stage_ms_per_step": {k: v / k_prof for k, v in stage_ms.items()},
         "issued_tensor_tflops": issued / (core_ms / 1e3) / 1e12 if issued else None,
-        "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
+        "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops); dense fp16 has the same "
+                       "nominal rate (ratio 1)" if args.precision == "f16x3" else
+                       f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
     }
 
     # ---- end to end through the public API with pinned host buffers ---
@@ -380,9 +387,38 @@ def run_ours(args, rank, world, local_rank):
     per_gpu_value = total_pairs * args.steps / (total_ms / 1e3)
     plan.sync()
 
+    # ---- the BF16 split (split6) on the same workload: the FP16 split's
+    # counterpart, and the plan that stage 2 and the point-source evaluation
+    # (BF16 modes) run on ----------------------------------------------------
+    plan6, split6 = plan, None
+    if args.precision == "f16x3":
+        plan6 = M2LPlan(wl.p, wl.eps, wl.d, "split6")
+        for l in LEVELS:
+            plan6.set_level(l, tree.levels[l], tree.r0)
+        if not args.no_autotune:
+            plan6.autotune(q_all, lo, hi, reps=5, out=out_all)
+        for _ in range(3):
+            plan6.apply_levels(q_all, lo, hi, out=out_all)
+        plan6.sync()
+        k6 = min(args.steps, 50)
+        s6_ms = timed(lambda: plan6.apply_levels(q_all, lo, hi, out=out_all), k6)
+        plan6.profile(True)
+        timed(lambda: plan6.apply_levels(q_all, lo, hi, out=out_all), min(k6, 20))
+        s6_stage, _ = plan6.profile_read()
+        plan6.profile(False)
+        split6 = {"value": total_pairs * k6 / (s6_ms / 1e3), "unit": UNIT, "ms_per_step": s6_ms / k6,
+                  "stage_ms_per_step": {k: v / min(k6, 20) for k, v in s6_stage.items()},
+                  "core_tflops_algorithmic": flops_step / (s6_stage["core"] / min(k6, 20) / 1e3) / 1e12}
+
+    def step6():
+        plan6.apply_levels(q_all, lo, hi, out=out_all)
+
     # ---- stage 2 (Sec. 3.2): per-offset low-rank cores, c2 = 10 ----------
     stage2 = None
     if args.precision != "fp32":
+        plan, plan_main = plan6, plan
+        step_main = step
+        step = step6
         c2 = 10.0
         plan.set_stage2(c2)
         ranks = plan.stage2_ranks()
@@ -399,8 +435,9 @@ def run_ours(args, rank, world, local_rank):
         stage2 = {"c2": c2, "eps2": c2 * wl.eps / r, "ranks_min_mean_max": [int(ranks.min()), float(ranks.mean()),
                                                                          int(ranks.max())],
                   "value": total_pairs * k_s2 / (s2_ms / 1e3), "unit": UNIT, "ms_per_step": s2_ms / k_s2,
-                  "core_ms_per_step": s2_stage["core"] / min(k_s2, 20),
+                  "core_ms_per_step": s2_stage["core"] / min(k_s2, 20), "precision": "split6",
                   "parity": "tests/test_gpu_m2l.py::test_stage2_parity against the oracle's two-product M2L"}
+        plan, step = plan_main, step_main
 
     # ---- complete evaluation for the workload's points (Sec. 4 with the
     # compressed passes of Sec. 3.3): near field + S~, M~, M2L, L~, T~ ------
@@ -408,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
     if args.precision != "fp32":
         from paper_1211_2517_gb300 import PointFMM
 
-        ftree = PointFMM(plan, wl.points, wl.depth)
+        ftree = PointFMM(plan6, wl.points, wl.depth)
         qd = torch.tensor(wl.densities, dtype=torch.float32, device=dev)
         pot = torch.empty_like(qd)
         for parts in (3, 1, 2):
@@ -434,7 +471,7 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"f16x3": "f16", "fp32": "f32"}.get(args.precision, "bf16"), "data": "synthetic",
         "config": dict(workload_desc(total_pairs, r, rp, args.precision),
                        core_variant=({k: tune[k] for k in ("n_chunk", "contiguous", "variant")} if tune else "default")),
         "roofline": roofline,
@@ -444,9 +481,10 @@ def run_ours(args, rank, world, local_rank):
         "dense_fp32_baseline": {"value": dense_value, "unit": UNIT,
                                 "speedup_compressed_over_dense": per_gpu_value / dense_value},
         "adjoint": {"value": total_pairs * k_small / (adj_ms / 1e3), "unit": UNIT},
+        "split6": split6,
         "stage2": stage2,
         "fmm": fmm,
-        "parity": "tests/test_gpu_m2l.py: split6 and fp32 within 1e-6 relative L2 of the FP64 oracle",
+        "parity": "tests/test_gpu_m2l.py: f16x3, split6 and fp32 within 1e-6 relative L2 of the FP64 oracle",
     }
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -455,6 +493,8 @@ def run_ours(args, rank, world, local_rank):
                                 "sample": cdesc}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if plan6 is not plan:
+        plan6.close()
     plan.close()
 
 
@@ -548,7 +588,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("split6", "split3", "bf16", "fp32"), default="split6")
+    ap.add_argument("--precision", choices=("f16x3", "split6", "split3", "bf16", "fp32"), default="f16x3")
     ap.add_argument("--no-autotune", action="store_true", help="use the plan's default core variant")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle leg")
     ap.add_argument("--workload", choices=("sphere2m_p8", "batch64"), default="sphere2m_p8",

@@ -70,6 +70,12 @@ extern "C" {
 #define KIFMM_PREC_BF16        1    /* tcgen05 BF16 x BF16, FP32 accumulate (1 product)    */
 #define KIFMM_PREC_SPLIT3      2    /* 2-piece BF16 split, 3 products (hi*hi+hi*lo+lo*hi)  */
 #define KIFMM_PREC_SPLIT6      3    /* 3-piece BF16 split, 6 products (all terms <= 2^-16)  */
+#define KIFMM_PREC_F16X3       4    /* 2-piece FP16 split with per-box scaling, 3 products:
+                                       every q~ row is scaled by the power of two that puts
+                                       its largest entry in [2^14, 2^15), the cores by one
+                                       that puts theirs in [2^13, 2^14), so both FP16 pieces
+                                       stay normal where they matter; dropped terms <= 2^-22.
+                                       apply / apply_adjoint / apply_levels(_adjoint) only */
 
 #define KIFMM_N_OFFSETS        316  /* unique M2L offsets per level, Sec. 3.1 */
 
@@ -288,13 +294,16 @@ int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
 
 /* The choice kifmm_m2l_autotune kept: n_chunk = N columns of K~_o per core
  * work item, contiguous = 1 if each CTA takes one contiguous run of work
- * items (0: items dealt round-robin), variant = the split6 core variant
- * (0: hi and lo accumulators per tile, epilogue after the tile's MMAs;
- * 1: each tile's rows of q~ resident in shared memory, K~_o streamed in
- * column blocks, n_chunk then does not apply; 2 / 3: partial sums of
- * two / one K-chunks drained into registers while the next partial's MMAs
- * run; other precisions: 0), core_ms = the core launch's mean time (ms) under that
- * choice, from_cache = 1 if read back from the cache file. */
+ * items (0: items dealt round-robin), variant = the split6 / f16x3 core
+ * variant (0: hi and lo accumulators per tile, epilogue after the tile's
+ * MMAs; 1 (split6 only): each tile's rows of q~ resident in shared memory,
+ * K~_o streamed in column blocks, n_chunk then does not apply; 2 / 3:
+ * partial sums of two / one K-chunks drained into registers while the next
+ * partial's MMAs run; 4 / 5: as 2 / 3 with the output rows reduced into p~
+ * by TMA bulk reductions; 6 (f16x3 only): partials of three K-chunks;
+ * other precisions: 0), core_ms = the core launch's
+ * mean time (ms) under that choice, from_cache = 1 if read back from the
+ * cache file. */
 typedef struct kifmm_m2l_tune_result {
     int n_chunk;
     int contiguous;
@@ -306,8 +315,9 @@ typedef struct kifmm_m2l_tune_result {
 /* Tile autotuner of the core GEMM (Step 3.1's per-offset products, on the
  * tensor cores).  The paper fixes no launch shape; the candidates here
  * change how the core's work is tiled and spread over the persistent CTAs
- * (N per work item, round-robin or contiguous work) and, for split6, where
- * partial sums are kept (the three variants above).  The piece products
+ * (N per work item, round-robin or contiguous work) and, for split6 and
+ * f16x3, where partial sums are kept and how rows reach p~ (the variants
+ * above).  The piece products
  * are the same for every candidate; the split6 variants differ in how the
  * FP32 partial sums are grouped (each stays within the split6 tolerance),
  * the others only in atomic accumulation order, which is never fixed.  Runs

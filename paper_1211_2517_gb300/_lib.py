@@ -22,7 +22,7 @@ ERR_NAMES = {
     -6: "KIFMM_ERR_STATE",
 }
 
-PREC = {"fp32": 0, "bf16": 1, "split3": 2, "split6": 3}
+PREC = {"fp32": 0, "bf16": 1, "split3": 2, "split6": 3, "f16x3": 4}
 N_OFFSETS = 316
 
 # every symbol include/kifmm_m2l.h declares

@@ -38,6 +38,7 @@ int pieces_for(int precision) {
         case KIFMM_PREC_BF16: return 1;
         case KIFMM_PREC_SPLIT3: return 2;
         case KIFMM_PREC_SPLIT6: return 3;
+        case KIFMM_PREC_F16X3: return 2;
         default: return 0;
     }
 }
@@ -46,8 +47,37 @@ int products_for(int precision) {
         case KIFMM_PREC_BF16: return 1;
         case KIFMM_PREC_SPLIT3: return 3;
         case KIFMM_PREC_SPLIT6: return 6;
+        case KIFMM_PREC_F16X3: return 3;
         default: return 0;
     }
+}
+
+// IEEE 754 binary16 of v, round to nearest even (the host side of the FP16
+// split of the cores): 10 fraction bits, exponent bias 15, subnormals in
+// steps of 2^-24, |v| >= 65520 -> infinity.
+uint16_t f16_bits_rn(double v) {
+    const uint16_t sign = std::signbit(v) ? 0x8000u : 0u;
+    const double a = std::fabs(v);
+    if (a == 0.0) return sign;
+    if (a >= 65520.0) return sign | 0x7C00u;
+    int e2 = 0;
+    std::frexp(a, &e2);        // a = f 2^e2, f in [0.5, 1)
+    int E = e2 - 1;            // a in [2^E, 2^(E+1))
+    if (E < -14) {             // subnormal: multiples of 2^-24 (1024 rounds up to the smallest normal)
+        return sign | (uint16_t)std::nearbyint(std::ldexp(a, 24));
+    }
+    double m = std::nearbyint(std::ldexp(a, 10 - E));  // in [1024, 2048]
+    if (m == 2048.0) {
+        m = 1024.0;
+        ++E;
+    }
+    if (E > 15) return sign | 0x7C00u;
+    return sign | (uint16_t)((E + 15) << 10) | (uint16_t)(m - 1024.0);
+}
+double f16_bits_to_double(uint16_t b) {
+    const int E = (b >> 10) & 0x1F, f = b & 0x3FF;
+    const double mag = E == 0 ? std::ldexp((double)f, -24) : std::ldexp(1024.0 + f, E - 25);
+    return (b & 0x8000u) ? -mag : mag;
 }
 
 // host split of FP64 into BF16 pieces (round to nearest even at each step)
@@ -160,20 +190,26 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
     }
     const float scale = (float)std::ldexp(1.0 / ls->r0, level);  // (r0 / 2^l)^-1
     const bool fp32_core = plan->prm.precision == KIFMM_PREC_FP32;
+    const bool f16_core = plan->prm.precision == KIFMM_PREC_F16X3;
     const long piece_stride = (rows + 1) * rp;
     KIFMM_CUDA_TRY(plan->pt.ensure((size_t)rows * rp));
-    if (fp32_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
-    else KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
+    if (fp32_core || f16_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
+    if (!fp32_core) KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
+    if (f16_core) KIFMM_CUDA_TRY(plan->qs.ensure((size_t)rows + 1));
 
     // 1. compression  q~ = R~^T q  (adjoint: U~^T pbar; R~ = U~, so one factor
     //    serves both directions), written as the core's operand; p~ = 0
     const long vtiles = (rows + 127) / 128;
     KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, 2);
+        StageTimer timer(plan, s, 0, f16_core ? 3 : 2);
         st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
-                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
+                          (fp32_core || f16_core) ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
         if (st != KIFMM_OK) return st;
+        if (f16_core) {
+            st = split_core_operand_f16(plan, plan->qt.ptr, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
+            if (st != KIFMM_OK) return st;
+        }
     }
 
     // 2. core over offset-grouped pairs
@@ -186,38 +222,16 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
         KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp,
                                               ts->tiles.ptr, ts->n_tiles, ps.src.ptr, ps.dst.ptr, nrhs, 1.0f, s));
     } else {
-        for (int pc = 0; pc < plan->pieces; ++pc)
-            KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
-                                           rp * sizeof(__nv_bfloat16), s));
-        UmmaArgs a{};
-        a.A = plan->qb.ptr;
-        a.a_piece_stride = piece_stride;
-        a.kdim = rp;
-        a.B = plan->Cb.ptr;
-        a.b_groups = kOffsets;
-        a.ndim = rp;
-        a.n_chunk = core_chunk(plan);
-        a.contiguous = plan->tune_contig;
-        a.core_resident = plan->tune_variant == 1;
-        a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
-        a.s2_on = plan->s2_on;
-        a.s2_V = plan->s2V.ptr;
-        a.s2_U = plan->s2U.ptr;
-        a.s2_k16 = plan->s2_k16.ptr;
-        a.row_src = ts->row_src.ptr;
-        a.row_dst = ts->row_dst.ptr;
-        a.tile_k = ts->tile_k.ptr;
-        a.n_tiles = ts->n_tiles;
-        a.nrhs = nrhs;
-        a.zero_row = (int)rows;
-        a.level_scale[0] = 1.0f;  // the level scale is applied by the expansion
-        a.D = plan->pt.ptr;
-        a.ldd = rp;
-        a.n_products = plan->products;
-        a.hilo = plan->core_hilo;
-        a.error_flag = plan->err_flag.ptr;
+        if (!f16_core)
+            for (int pc = 0; pc < plan->pieces; ++pc)
+                KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
+                                               rp * sizeof(__nv_bfloat16), s));
+        ScaleTable unit{};
+        unit.s[0] = 1.0f;  // the level scale is applied by the expansion
         StageTimer timer(plan, s, 1, 1);
-        KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+        st = launch_core(plan, plan->qb.ptr, piece_stride, (int)rows, *ts, nrhs, unit, plan->pt.ptr, s,
+                         f16_core ? plan->qs.ptr : nullptr);
+        if (st != KIFMM_OK) return st;
     }
 
     // 3. expansion  y = beta y + s_l U~ p~   (adjoint: R~ q~bar; R~ = U~)
@@ -297,20 +311,26 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         return KIFMM_ERR_INVALID_ARG;
     }
     const bool fp32_core = plan->prm.precision == KIFMM_PREC_FP32;
+    const bool f16_core = plan->prm.precision == KIFMM_PREC_F16X3;
     const long piece_stride = (rows + 1) * rp;
     KIFMM_CUDA_TRY(plan->pt.ensure((size_t)rows * rp));
-    if (fp32_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
-    else KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
+    if (fp32_core || f16_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
+    if (!fp32_core) KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
+    if (f16_core) KIFMM_CUDA_TRY(plan->qs.ensure((size_t)rows + 1));
     TileSet* ts = nullptr;
     st = get_multi_tiles(*ms, nrhs, &ts);
     if (st != KIFMM_OK) return st;
     const long vtiles = (rows + 127) / 128;
     KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, 2);
+        StageTimer timer(plan, s, 0, f16_core ? 3 : 2);
         st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
-                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
+                          (fp32_core || f16_core) ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
         if (st != KIFMM_OK) return st;
+        if (f16_core) {
+            st = split_core_operand_f16(plan, plan->qt.ptr, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
+            if (st != KIFMM_OK) return st;
+        }
     }
     ScaleTable scales{};
     for (int l = lo; l <= hi; ++l) {
@@ -322,11 +342,13 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         KIFMM_CUDA_TRY(launch_pairs_gemm_fp32(plan->qt.ptr, rp, plan->C.ptr, rp, rp, plan->pt.ptr, rp, ts->tiles.ptr,
                                               ts->n_tiles, ms->src.ptr, ms->dst.ptr, nrhs, scales, s));
     } else {
-        for (int pc = 0; pc < plan->pieces; ++pc)
-            KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
-                                           rp * sizeof(__nv_bfloat16), s));
+        if (!f16_core)
+            for (int pc = 0; pc < plan->pieces; ++pc)
+                KIFMM_CUDA_TRY(cudaMemsetAsync(plan->qb.ptr + pc * piece_stride + rows * rp, 0,
+                                               rp * sizeof(__nv_bfloat16), s));
         StageTimer timer(plan, s, 1, 1);
-        st = launch_core(plan, plan->qb.ptr, piece_stride, (int)rows, *ts, nrhs, scales, plan->pt.ptr, s);
+        st = launch_core(plan, plan->qb.ptr, piece_stride, (int)rows, *ts, nrhs, scales, plan->pt.ptr, s,
+                         f16_core ? plan->qs.ptr : nullptr);
         if (st != KIFMM_OK) return st;
     }
     {
@@ -344,8 +366,16 @@ namespace kifmm {
 int multi_tileset(MultiState& ms, int nrhs, TileSet** out) { return get_multi_tiles(ms, nrhs, out); }
 
 int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride, int zero_row, const TileSet& ts,
-                int nrhs, const ScaleTable& scales, float* pt, cudaStream_t s) {
+                int nrhs, const ScaleTable& scales, float* pt, cudaStream_t s, const float* row_scale) {
     UmmaArgs a{};
+    if (plan->prm.precision == KIFMM_PREC_F16X3) {
+        if (!row_scale) {
+            set_error("the FP16 core needs the per-row factors of its operand");
+            return KIFMM_ERR_INVALID_ARG;
+        }
+        a.f16 = 1;
+        a.row_scale = row_scale;
+    }
     a.A = qb;
     a.a_piece_stride = piece_stride;
     a.kdim = plan->rp;
@@ -355,7 +385,8 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     a.n_chunk = core_chunk(plan);
     a.contiguous = plan->tune_contig;
     a.core_resident = plan->tune_variant == 1;
-    a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
+    a.core_drain = plan->variant_drain();
+    a.red_bulk = plan->variant_bulk();
     a.s2_on = plan->s2_on;
     a.s2_V = plan->s2V.ptr;
     a.s2_U = plan->s2U.ptr;
@@ -366,13 +397,24 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     a.n_tiles = ts.n_tiles;
     a.nrhs = nrhs;
     a.zero_row = zero_row;
-    for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i];
+    for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i] * plan->core_inv_scale;
     a.D = pt;
     a.ldd = plan->rp;
     a.n_products = plan->products;
     a.hilo = plan->core_hilo;
     a.error_flag = plan->err_flag.ptr;
     KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+    return KIFMM_OK;
+}
+
+int split_core_operand_f16(kifmm_m2l_plan plan, const float* qt, long rows, __nv_bfloat16* qb, long piece_stride,
+                           float* qs, cudaStream_t s) {
+    const int rp = plan->rp;
+    KIFMM_CUDA_TRY(launch_split_rows_f16_scaled(qt, (int)rows, rp, rp, rp, reinterpret_cast<__half*>(qb), piece_stride,
+                                                qs, s));
+    for (int pc = 0; pc < 2; ++pc)
+        KIFMM_CUDA_TRY(cudaMemsetAsync(qb + pc * piece_stride + rows * rp, 0, rp * sizeof(__nv_bfloat16), s));
+    KIFMM_CUDA_TRY(cudaMemsetAsync(qs + rows, 0, sizeof(float), s));
     return KIFMM_OK;
 }
 
@@ -743,11 +785,32 @@ int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out) {
             return (a < (size_t)r && i < (size_t)n) ? f.U[i * r + a] : 0.0;
         });
         if (st != KIFMM_OK) return st;
+        if (params->precision == KIFMM_PREC_F16X3) {
+            // K~_o as two FP16 pieces of tau K~_o, tau the power of two that puts
+            // max |K~| in [2^13, 2^14); the core divides by tau in its output scale
+            double cmax = 0;
+            for (double v : f.C) cmax = std::max(cmax, std::fabs(v));
+            int e2 = 0;
+            std::frexp(cmax > 0 ? cmax : 1.0, &e2);  // cmax in [2^(e2-1), 2^e2)
+            const double tau = std::ldexp(1.0, 14 - e2);
+            plan->core_inv_scale = (float)(1.0 / tau);
+            const size_t per = (size_t)kOffsets * rp * rp;
+            std::vector<uint16_t> h(per * 2, 0);
+            for (size_t e = 0; e < per; ++e) {
+                const size_t k = e / ((size_t)rp * rp), a = (e / rp) % rp, b = e % rp;
+                if (a >= (size_t)r || b >= (size_t)r) continue;
+                const double v = tau * f.C[(k * r + a) * r + b];
+                h[e] = f16_bits_rn(v);
+                h[per + e] = f16_bits_rn(v - f16_bits_to_double(h[e]));
+            }
+            KIFMM_CUDA_TRY(plan->Cb.ensure(h.size()));
+            KIFMM_CUDA_TRY(cudaMemcpy(plan->Cb.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
+        }
         // SPLIT6 keeps the (0,0) product in its own accumulator: the tensor
         // core's accumulation error grows with the number of MMA steps that
         // round at the full magnitude, and the 5 small products would
-        // otherwise add 5 such steps per K step.
-        plan->core_hilo = params->precision == KIFMM_PREC_SPLIT6 ? 1 : 0;
+        // otherwise add 5 such steps per K step.  F16X3 likewise.
+        plan->core_hilo = (params->precision == KIFMM_PREC_SPLIT6 || params->precision == KIFMM_PREC_F16X3) ? 1 : 0;
         KIFMM_CUDA_TRY(plan->err_flag.ensure(1));
         KIFMM_CUDA_TRY(cudaMemset(plan->err_flag.ptr, 0, sizeof(int)));
     } catch (const std::bad_alloc&) {
@@ -789,8 +852,8 @@ int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2) {
         plan->s2_k.clear();
         return KIFMM_OK;
     }
-    if (plan->prm.precision == KIFMM_PREC_FP32) {
-        set_error("stage 2 runs on the tensor-core precisions only (FP32 plans use the SIMT core)");
+    if (plan->prm.precision == KIFMM_PREC_FP32 || plan->prm.precision == KIFMM_PREC_F16X3) {
+        set_error("stage 2 runs on the BF16 tensor-core precisions only (FP32 plans use the SIMT core)");
         return KIFMM_ERR_UNSUPPORTED;
     }
     if (plan->rp > 512 - 2 * 96) {

@@ -179,7 +179,8 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.n_chunk = core_chunk(plan);
         a.contiguous = plan->tune_contig;
         a.core_resident = plan->tune_variant == 1;
-        a.core_drain = plan->tune_variant == 2 ? 2 : (plan->tune_variant == 3 ? 1 : 0);
+        a.core_drain = plan->variant_drain();
+        a.red_bulk = plan->variant_bulk();
         a.s2_on = plan->s2_on;
         a.s2_V = plan->s2V.ptr;
         a.s2_U = plan->s2U.ptr;
@@ -244,8 +245,9 @@ extern "C" int kifmm_m2l_apply_batch(int n_items, const kifmm_m2l_batch_item* it
             set_error("batch item " + std::to_string(i) + ": plan is NULL");
             return KIFMM_ERR_INVALID_ARG;
         }
-        if (x.plan->prm.precision == KIFMM_PREC_FP32) {
-            set_error("batch item " + std::to_string(i) + ": batches run the tensor-core modes (not KIFMM_PREC_FP32)");
+        if (x.plan->prm.precision == KIFMM_PREC_FP32 || x.plan->prm.precision == KIFMM_PREC_F16X3) {
+            set_error("batch item " + std::to_string(i) +
+                      ": batches run the BF16 tensor-core modes (not KIFMM_PREC_FP32 or KIFMM_PREC_F16X3)");
             return KIFMM_ERR_UNSUPPORTED;
         }
         if (x.nrhs < 1 || x.level_lo < 0 || x.level_hi < x.level_lo || x.level_hi - x.level_lo >= 32) {

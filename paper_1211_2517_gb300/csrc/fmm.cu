@@ -530,8 +530,8 @@ int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points
             set_error("non-finite point coordinate at index " + std::to_string(i / 3));
             return KIFMM_ERR_INVALID_ARG;
         }
-    if (plan->prm.precision == KIFMM_PREC_FP32) {
-        set_error("point-source evaluation runs its passes on the tensor cores: use a BF16 / split precision");
+    if (plan->prm.precision == KIFMM_PREC_FP32 || plan->prm.precision == KIFMM_PREC_F16X3) {
+        set_error("point-source evaluation runs its passes on the BF16 tensor cores: use a BF16 / split precision");
         return KIFMM_ERR_UNSUPPORTED;
     }
     if (plan->n > 512) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 namespace kifmm {
@@ -56,6 +57,12 @@ cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const int* leaf
                              const int* near_start, const int* near_idx, int n_leaves, const float4* usurf, int n,
                              float a, float scale, const float* e, int lde, const int* perm, float* out, int parts,
                              cudaStream_t stream);
+
+// Rows of A (FP32, m_rows x cols, ld lda) -> two FP16 pieces [2][m_rows][ldo]
+// (piece stride piece_stride) of sigma_r x with sigma_r the power of two that
+// puts row r's largest |x| in [2^14, 2^15), and inv[r] = 1 / sigma_r.  ldo <= 512.
+cudaError_t launch_split_rows_f16_scaled(const float* A, int m_rows, int lda, int cols, int ldo, __half* out,
+                                         long piece_stride, float* inv, cudaStream_t stream);
 
 // Zero `count` floats.
 cudaError_t launch_zero(float* x, long count, cudaStream_t stream);
@@ -148,6 +155,9 @@ struct UmmaArgs {
     // arithmetic
     int n_products;           // 1, 3 or 6 piece products
     int hilo;                 // 1: the (0,0) product accumulates apart from the others
+    int f16;                  // A_GATHER: A and B pieces are FP16 (else BF16)
+    const float* row_scale;   // E_RED: when set, output row r is scaled by row_scale[row_src[r]]
+    int red_bulk;             // E_RED, drained partials: reduce rows into D with TMA bulk reductions
     int* error_flag;          // device int, set when a bounded wait times out
 };
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& args, int num_sms, cudaStream_t stream);

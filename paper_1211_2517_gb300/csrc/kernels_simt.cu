@@ -12,6 +12,7 @@
 // 8 x 8 register block (8 contiguous rows, two groups of 4 columns).
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "kernels.h"
 
@@ -200,6 +201,45 @@ __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int l
     }
 }
 
+// One warp per row r < m_rows: with e = floor(log2 max_c |A[r][c]|) read from
+// the FP32 exponent field (clamped to [-112, 127]; a zero row takes e = 0),
+// sigma = 2^(14 - e) puts the row's largest entry in [2^14, 2^15), inside
+// FP16's normal range.  out[0][r][c] = fp16(sigma x), out[1][r][c] =
+// fp16(sigma x - out[0][r][c]) (round to nearest), zero for c in
+// [cols, ldo); inv[r] = 2^(e - 14).
+constexpr int kF16SplitCols = 16;  // columns per lane: ldo <= 512
+__global__ void split_rows_f16_scaled_kernel(const float* __restrict__ A, int m_rows, int lda, int cols, int ldo,
+                                             __half* __restrict__ out, long piece_stride, float* __restrict__ inv) {
+    const int lane = threadIdx.x & 31;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m_rows; row += warps) {
+        float v[kF16SplitCols];
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < kF16SplitCols; ++k) {
+            const int c = lane + 32 * k;
+            v[k] = c < cols ? __ldg(A + row * lda + c) : 0.f;
+            m = fmaxf(m, fabsf(v[k]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        int e = m > 0.f ? ((__float_as_int(m) >> 23) & 0xFF) - 127 : 0;
+        e = max(-112, min(127, e));  // sigma and 1 / sigma both normal powers of two
+        const float sigma = __int_as_float((127 + 14 - e) << 23);
+#pragma unroll
+        for (int k = 0; k < kF16SplitCols; ++k) {
+            const int c = lane + 32 * k;
+            if (c < ldo) {
+                const float x = v[k] * sigma;
+                const __half h = __float2half_rn(x);
+                out[row * ldo + c] = h;
+                out[piece_stride + row * ldo + c] = __float2half_rn(x - __half2float(h));
+            }
+        }
+        if (lane == 0) inv[row] = __int_as_float((127 + e - 14) << 23);
+    }
+}
+
 __global__ void zero_kernel(float4* __restrict__ x, long n4) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n4; e += (long)gridDim.x * blockDim.x)
         x[e] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -253,6 +293,17 @@ cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int
     if ((lda & 3) || (cols & 3) || (ldo & 3) || cols > ldo || pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
     split_rows_kernel<<<dim3((unsigned)n_tiles, 8), 256, 0, stream>>>(A, m_rows, lda, cols, ldo, segs, n_segs, out,
                                                                       piece_stride, pieces, pad_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_rows_f16_scaled(const float* A, int m_rows, int lda, int cols, int ldo, __half* out,
+                                         long piece_stride, float* inv, cudaStream_t stream) {
+    if (m_rows <= 0) return cudaSuccess;
+    if (cols > ldo || ldo > 32 * kF16SplitCols) return cudaErrorInvalidValue;
+    long blocks = ((long)m_rows + 7) / 8;  // 8 warps per block, one row per warp
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    split_rows_f16_scaled_kernel<<<(unsigned)blocks, 256, 0, stream>>>(A, m_rows, lda, cols, ldo, out, piece_stride,
+                                                                      inv);
     return cudaGetLastError();
 }
 

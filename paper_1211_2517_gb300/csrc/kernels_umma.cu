@@ -35,6 +35,8 @@
 // flight are waited for (bounded), and TMEM is freed before exit.
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -129,6 +131,24 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Bulk reduction of `bytes` (a multiple of 16) FP32 values from shared
+// memory into global memory by the TMA unit: dst[i] += src[i].
+__device__ __forceinline__ void bulk_reduce_add_f32(float* dst, uint32_t src, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst), "r"(src),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The sources of this thread's committed bulk operations have been read.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// This thread's committed bulk operations are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Arrive on `bar` once every cp.async this thread issued so far has landed
+// (the arrival counts against the barrier's expected count).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 // wait until at most n (1..7) groups are pending
@@ -171,6 +191,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
 // Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128.
 __device__ __forceinline__ uint32_t umma_idesc_bf16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+// The same with A=B=F16 (format code 0 in both operand fields) when f16 != 0.
+__device__ __forceinline__ uint32_t umma_idesc(int n, int f16) {
+    return f16 ? (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24) : umma_idesc_bf16(n);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
@@ -350,13 +374,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         if (AMODE == A_GATHER) {
-            // Stage it belongs to producer warp it % P (P = L.prod_warps = S,
-            // one ring slot per warp: its barriers see one waiter and one
-            // arriver, in order).  That warp gathers all 128 rows of the stage
-            // (lane l copies 16-byte chunk l % CPR of rows l / CPR + RPI i: one
-            // instruction covers RPI rows of CH * 2 contiguous bytes), waits
-            // for its own copies only and arrives; P warps keep P stages in
-            // flight.
+            // Stage it belongs to producer warp it % P (P = L.prod_warps <= S
+            // ring slots).  That warp gathers all 128 rows of the stage (lane
+            // l copies 16-byte chunk l % CPR of rows l / CPR + RPI i: one
+            // instruction covers RPI rows of CH * 2 contiguous bytes); every
+            // lane's copies arrive on the stage's full barrier when they land,
+            // so a warp has as many stages in flight as the ring allows.  A
+            // warp waiting on a slot's empty barrier is at most one phase
+            // ahead of it: its previous stage (it - P) already waited for the
+            // consumption of it - P - S, which is at or after it - 2 S when
+            // P <= S.
             const int P = L.prod_warps;
             constexpr int CPR = CH / 8;          // 16-byte chunks per row and stage
             constexpr int RPI = 32 / CPR;        // rows per warp instruction
@@ -403,11 +430,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int i = 0; i < NR; ++i)
                             cp_async16(sbase + swz<CH>(rl + RPI * i, cch), base + (long)srow[i] * args.kdim, bytes);
                     }
-                    cp_async_commit();
                     if (lane == 0) issue_b(s, item, kc);
-                    cp_async_wait_0();
-                    fence_proxy_async();
-                    mbar_arrive(&sm->full[s]);
+                    // the stage is full once every lane's copies land; the warp
+                    // moves on without waiting (the MMA thread fences the
+                    // generic-proxy writes before its tensor-core reads)
+                    cp_async_mbar_arrive(&sm->full[s]);
                 }
             }
             cp_async_wait_0();
@@ -515,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int nthis = item_nthis(item);
                     const int nA = nthis <= 256 ? nthis : ((nthis / 2 + 15) / 16) * 16;
                     const int nB = nthis - nA;
-                    const uint32_t idA = umma_idesc_bf16(nA), idB = nB > 0 ? umma_idesc_bf16(nB) : 0u;
+                    const uint32_t idA = umma_idesc(nA, args.f16), idB = nB > 0 ? umma_idesc(nB, args.f16) : 0u;
                     const uint32_t nB_off = (uint32_t)(nA * RB) >> 4;
                     uint32_t d_hi, d_lo;
                     if (AMODE == A_ROWS) {
@@ -544,6 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             ok = false;
                             break;
                         }
+                        if (AMODE == A_GATHER) fence_proxy_async();  // cp.async data -> tensor-core reads
                         tc_fence_after();
                         const bool two = args.kdim - kc * CH >= 32;  // K steps of 16 in this chunk: 2 or 1
                         const uint64_t sd = desc0 + (uint64_t)((uint32_t)s * stage_u);
@@ -621,24 +649,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         int pcount = 0;
         int e_nxt_row = -1, e_nxt_k = 0;
+        float e_nxt_rs = 1.f;  // per-row factor of the A row (row_scale), this lane's row
+        auto row_factor = [&](int t) -> float {
+            if (!args.row_scale) return 1.f;
+            const int sr = __ldg(args.row_src + (long)t * kTileM + q * 32 + lane);
+            return sr >= 0 ? __ldg(args.row_scale + sr) : 0.f;
+        };
         if (EMODE == E_RED && i_beg < i_end) {
             const int t0 = item_tile(i_beg);
             e_nxt_row = __ldg(args.row_dst + (long)t0 * kTileM + q * 32 + lane);
             e_nxt_k = __ldg(args.tile_k + t0);
+            e_nxt_rs = row_factor(t0);
         }
         bool ok = true;
         for (int item = i_beg; item < i_end && ok; item += i_step) {
             long orow = e_nxt_row;
-            float oscale = 1.0f;
+            float oscale = 1.0f, rsc = 1.0f;
             float* e_dbase = args.D;
             float e_alpha = args.alpha, e_beta = args.beta;
             if (EMODE == E_RED) {
                 oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
                                           : args.level_scale[(e_nxt_k >> 16) & 31];
+                rsc = e_nxt_rs;
                 if (item + i_step < i_end) {
                     const int tn = item_tile(item + i_step);
                     e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + q * 32 + lane);
                     e_nxt_k = __ldg(args.tile_k + tn);
+                    e_nxt_rs = row_factor(tn);
                 }
             } else {
                 // identity rows (compression / expansion): the tile's segment
@@ -694,6 +731,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ++pcount;
             }
             if (!ok) break;
+            if (EMODE == E_RED && args.red_bulk) {
+                // every lane hands its own row segment to the TMA unit: one bulk
+                // reduction of 32 (or 16) FP32 values per chunk, staged in the
+                // lane's row of the transpose buffer
+                float* my = trans + lane * kTransStride;
+                const float f = oscale * rsc;
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    const int c = (c_beg + jj) * 32;
+                    if (c_beg + jj < c_end) {
+                        const int ncols = c + 32 <= nthis ? 32 : 16;
+                        bulk_wait_read_all();  // the previous chunk has left the buffer
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq)
+                            if (4 * qq < ncols)
+                                *reinterpret_cast<float4*>(my + 4 * qq) =
+                                    make_float4(f * sums[jj * 32 + 4 * qq], f * sums[jj * 32 + 4 * qq + 1],
+                                                f * sums[jj * 32 + 4 * qq + 2], f * sums[jj * 32 + 4 * qq + 3]);
+                        fence_proxy_async();
+                        if (orow >= 0) {
+                            bulk_reduce_add_f32(args.D + orow * args.ldd + n0 + c, smem_u32(my), (uint32_t)ncols * 4u);
+                            bulk_commit();
+                        }
+                    }
+                }
+                continue;
+            }
             long prow[8];
 #pragma unroll
             for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
@@ -705,8 +769,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq)
                         *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * qq) =
-                            make_float4(sums[jj * 32 + 4 * qq], sums[jj * 32 + 4 * qq + 1], sums[jj * 32 + 4 * qq + 2],
-                                        sums[jj * 32 + 4 * qq + 3]);
+                            make_float4(rsc * sums[jj * 32 + 4 * qq], rsc * sums[jj * 32 + 4 * qq + 1],
+                                        rsc * sums[jj * 32 + 4 * qq + 2], rsc * sums[jj * 32 + 4 * qq + 3]);
                     __syncwarp();
                     const int ncols = c + 32 <= nthis ? 32 : 16;
 #pragma unroll
@@ -756,6 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        if (EMODE == E_RED && args.red_bulk) bulk_wait_all();  // reductions complete before teardown
     } else {
         // ================= epilogue =================
         float* trans = reinterpret_cast<float*>(smem_raw + L.trans_off) + warp * 32 * kTransStride;
@@ -763,10 +828,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool has_lo = args.hilo && args.n_products > 1;
         int tcount = 0, pcount = 0;
         int e_nxt_row = -1, e_nxt_k = 0;
+        float e_nxt_rs = 1.f;  // per-row factor of the A row (row_scale), this lane's row
+        auto row_factor = [&](int t) -> float {
+            if (!args.row_scale) return 1.f;
+            const int sr = __ldg(args.row_src + (long)t * kTileM + warp * 32 + lane);
+            return sr >= 0 ? __ldg(args.row_scale + sr) : 0.f;
+        };
         if (AMODE == A_GATHER && i_beg < i_end) {
             const int t0 = item_tile(i_beg);
             e_nxt_row = __ldg(args.row_dst + (long)t0 * kTileM + warp * 32 + lane);
             e_nxt_k = __ldg(args.tile_k + t0);
+            e_nxt_rs = row_factor(t0);
         }
         for (int item = i_beg; item < i_end; item += i_step, ++tcount) {
             const int acc = tcount % L.n_acc;
@@ -774,17 +846,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int n0 = item_n0(item), nthis = item_nthis(item);
             // this lane's output row (tile row warp*32 + lane); -1 = none
             long orow = -1;
-            float oscale = 1.0f;
+            float oscale = 1.0f, rsc = 1.0f;
             float* e_dbase = args.D;
             float e_alpha = args.alpha, e_beta = args.beta;
             if (AMODE == A_GATHER) {
                 orow = e_nxt_row;
                 oscale = args.scale_table ? __ldg(args.scale_table + (e_nxt_k >> 16))
                                           : args.level_scale[(e_nxt_k >> 16) & 31];
+                rsc = e_nxt_rs;
                 if (item + i_step < i_end) {  // prefetch the next item's rows
                     const int tn = item_tile(item + i_step);
                     e_nxt_row = __ldg(args.row_dst + (long)tn * kTileM + warp * 32 + lane);
                     e_nxt_k = __ldg(args.tile_k + tn);
+                    e_nxt_rs = row_factor(tn);
                 }
             } else if (args.n_segs > 0) {
                 const RowSeg sg = args.segs[find_seg(item_tile(item))];
@@ -882,7 +956,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * q) =
-                        make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+                        make_float4(rsc * val[4 * q], rsc * val[4 * q + 1], rsc * val[4 * q + 2], rsc * val[4 * q + 3]);
                 __syncwarp();
                 const int ncols = full32 ? 32 : 16;
 #pragma unroll
@@ -1842,8 +1916,10 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (a.ldd % 4 != 0) return cudaErrorInvalidValue;
     EncodeTiledFn encode = get_encode_fn();
     if (!encode) return cudaErrorNotSupported;
+    // FP16 operands and per-row factors: the gather kernel's classic and drain paths only
+    if ((a.f16 || a.row_scale) && (!gather || a.s2_on || (a.row_scale && emode != E_RED))) return cudaErrorNotSupported;
     if (gather && a.s2_on) return launch_core_stage2(a, num_sms, stream, encode);
-    if (gather && a.core_resident) {
+    if (gather && a.core_resident && !a.f16 && !a.row_scale) {
         const cudaError_t e = launch_core_resident(a, num_sms, stream, encode);
         if (e != cudaErrorNotSupported) return e;
     }
@@ -1889,11 +1965,12 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     }
     // drain mode (split6 core): 8 epilogue warps, which needs at most 3
     // producer warps (= stages) and N <= 192 per item (96 sums per thread)
-    L.drain = gather && a.core_drain > 0 && a.n_products == 6 && a.n_chunk <= 192 ? (a.core_drain > 1 ? 2 : 1) : 0;
+    L.drain = gather && a.core_drain > 0 && (a.n_products == 6 || a.n_products == 3) && a.n_chunk <= 192
+                  ? std::min(a.core_drain, 3)
+                  : 0;
     uint32_t trans_bytes = (L.drain ? 2 : 1) * kEpiWarps * 32 * kTransStride * 4;
     int avail = max_smem - 2048 - (int)trans_bytes;
     L.stages = avail / (int)L.stage_bytes;
-    if (L.drain && L.stages > 3) L.stages = 3;  // producers are warps 4-6 when warps 7-10 drain
     if (L.drain && L.stages < 2) {
         L.drain = 0;
         trans_bytes = kEpiWarps * 32 * kTransStride * 4;
@@ -1904,9 +1981,9 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (gather && emode != E_RED && !L.drain) return cudaErrorNotSupported;
     if (L.stages > 8) L.stages = 8;
     if (L.stages < 2) return cudaErrorInvalidConfiguration;
-    // gather mode: one ring slot per producer warp
-    if (gather && L.stages > kProdWarps) L.stages = kProdWarps;
-    L.prod_warps = L.stages;
+    // gather mode: producer warps 4-10 (4-6 when warps 7-10 drain), each
+    // taking every P-th ring slot with its copies in flight asynchronously
+    L.prod_warps = gather ? std::min(L.stages, L.drain ? 3 : kProdWarps) : L.stages;
     L.trans_off = 1024 + (uint32_t)L.stages * L.stage_bytes;
     const size_t smem = 1024 + (size_t)L.trans_off + trans_bytes;
 

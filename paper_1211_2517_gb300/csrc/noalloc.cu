@@ -122,6 +122,10 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
         set_error("density pointers must be 16-byte aligned");
         return KIFMM_ERR_INVALID_ARG;
     }
+    if (plan->prm.precision == KIFMM_PREC_F16X3) {
+        set_error("the allocation-free apply runs the FP32 and BF16 modes (not KIFMM_PREC_F16X3)");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
     int st = check_device(plan);
     if (st != KIFMM_OK) return st;
     unsigned char* base = nullptr;

@@ -117,11 +117,26 @@ struct kifmm_m2l_plan_s {
     // core launch choices picked by kifmm_m2l_autotune (0: defaults)
     int tune_chunk = 0;
     int tune_contig = 0;
-    // core variant (split6): 0 classic, 1 A-resident (where it fits),
-    // 2 / 3 partials of two / one K-chunks drained into registers
+    // core variant (split6, f16x3): 0 classic, 1 A-resident (where it fits),
+    // 2 / 3 partials of two / one K-chunks drained into registers, 4 / 5 the
+    // same with TMA bulk reductions
     int tune_variant = 2;
+    // core launch fields of a variant: 1 A-resident; 2 / 4 partials of two
+    // K-chunks drained into registers, 3 / 5 of one, 6 of three (f16x3);
+    // 4 / 5 reduce the rows into p~ with TMA bulk reductions instead of
+    // vector atomics
+    int variant_drain() const {
+        switch (tune_variant) {
+            case 2: case 4: return 2;
+            case 3: case 5: return 1;
+            case 6: return 3;
+            default: return 0;
+        }
+    }
+    int variant_bulk() const { return (tune_variant == 4 || tune_variant == 5) ? 1 : 0; }
     kifmm::DevBuf<float> C, K;
-    kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each
+    kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each (Cb: 2 FP16 pieces of tau K~ for F16X3)
+    float core_inv_scale = 1.0f;               // 1 / tau (F16X3), else 1
     std::vector<double> U64;                   // [n][r] FP64 basis U~ (= R~)
     // compressed pass operators of Sec. 3.3 (point-source evaluation), on first use:
     // Ws [rp][n_pad] (S~ factor), Wt [n_pad][rp] (T~ factor), M~ and L~ [8][rp][rp]
@@ -169,6 +184,7 @@ struct kifmm_m2l_plan_s {
     // scratch shared by all levels (apply calls on one plan are serialised)
     kifmm::DevBuf<float> qt, pt;
     kifmm::DevBuf<__nv_bfloat16> qb, sp;  // sp: BF16 pieces of the compression / expansion inputs
+    kifmm::DevBuf<float> qs;                // F16X3: 1 / sigma of every q~ row
 };
 
 
@@ -214,7 +230,12 @@ int multi_tileset(MultiState& ms, int nrhs, TileSet** out);
 // qb the plan's BF16 pieces (piece stride piece_stride, zero row zero_row);
 // stage 2 and the autotuned variant as set on the plan.
 int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride, int zero_row, const TileSet& ts,
-                int nrhs, const ScaleTable& scales, float* pt, cudaStream_t s);
+                int nrhs, const ScaleTable& scales, float* pt, cudaStream_t s, const float* row_scale = nullptr);
+// F16X3 operand of the core: q~ (FP32 rows [rows][rp] in qt) -> two scaled
+// FP16 pieces in qb (piece stride piece_stride, row `rows` zero) and the
+// row factors 1 / sigma in qs[0..rows] (qs[rows] = 0).
+int split_core_operand_f16(kifmm_m2l_plan plan, const float* qt, long rows, __nv_bfloat16* qb, long piece_stride,
+                           float* qs, cudaStream_t s);
 // Upload value_at(e), e < per, as 3 BF16 pieces [3][per] (piece j = RN of
 // the remainder of the earlier pieces).
 int upload_pieces(DevBuf<__nv_bfloat16>& dst, size_t per, const std::function<double(size_t)>& value_at);

@@ -130,7 +130,7 @@ int check_params(const kifmm_m2l_params* prm) {
         set_error("eps must be <= 0 (no truncation) or in [1e-12, 1)");
         return KIFMM_ERR_INVALID_ARG;
     }
-    if (prm->precision < KIFMM_PREC_FP32 || prm->precision > KIFMM_PREC_SPLIT6) {
+    if (prm->precision < KIFMM_PREC_FP32 || prm->precision > KIFMM_PREC_F16X3) {
         set_error("precision must be one of KIFMM_PREC_*");
         return KIFMM_ERR_INVALID_ARG;
     }

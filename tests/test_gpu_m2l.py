@@ -24,7 +24,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-6, "split6": 1e-6, "split3": 3e-5, "bf16": 1e-2}
+TOL = {"fp32": 1e-6, "split6": 1e-6, "split3": 3e-5, "bf16": 1e-2, "f16x3": 1e-6}
 
 
 def rel(a, b):
@@ -68,7 +68,7 @@ def make_plan(g, p, eps, precision, tree, levels):
     return plan
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split6", "split3", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "split6", "split3", "bf16", "f16x3"])
 def test_compressed_parity_cube(g, oracle_factors, cube, precision):
     wl, qup = cube
     f = oracle_factors(wl.p, wl.d, wl.eps)
@@ -84,7 +84,7 @@ def test_compressed_parity_cube(g, oracle_factors, cube, precision):
         assert err <= TOL[precision], err
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split6", "split3"])
+@pytest.mark.parametrize("precision", ["fp32", "split6", "split3", "f16x3"])
 def test_compressed_parity_multi_rhs(g, oracle_factors, sphere_small, precision):
     tree, qs = sphere_small
     f = oracle_factors(8, 0.1, 1e-7)
@@ -111,7 +111,7 @@ def test_dense_parity(g, cube):
         assert err <= 1e-6, err
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split6"])
+@pytest.mark.parametrize("precision", ["fp32", "split6", "f16x3"])
 def test_adjoint_parity_and_dot_product(g, oracle_factors, sphere_small, precision):
     tree, qs = sphere_small
     f = oracle_factors(8, 0.1, 1e-7)
@@ -302,7 +302,7 @@ def test_full_size_sphere_sampled(g, oracle_factors):
         assert err <= 1e-6, err
 
 
-@pytest.mark.parametrize("precision", ["split6", "fp32"])
+@pytest.mark.parametrize("precision", ["split6", "fp32", "f16x3"])
 def test_levels_batch_parity(g, oracle_factors, sphere_small, precision):
     """kifmm_m2l_apply_levels (levels 2..4 in one batch, 3 rhs) against the
     oracle on every level, forward and adjoint."""
@@ -332,6 +332,70 @@ def test_levels_batch_parity(g, oracle_factors, sphere_small, precision):
     assert rel(out2.cpu().numpy(), ref_all.cpu().numpy().astype(np.float64)) < 1e-6
 
 
+def test_full_size_sphere_f16x3_sampled(g, oracle_factors):
+    """The benchmark workload (2M-point sphere, depth 6, p = 8, eps = 1e-7) in
+    the FP16 split with per-box scaling, all levels in one batch, forward and
+    adjoint, on sampled targets the oracle computes one by one."""
+    wl = synth.workload("sphere2m_p8")
+    tree = wl.tree
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, "f16x3", tree, range(2, 7))
+    qs = {l: synth.random_box_densities(tree.levels[l].shape[0], 1, 296, 900 + l)[:, 0] for l in range(2, 7)}
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in range(2, 7)])).cuda()
+    rng = np.random.default_rng(6)
+    out = plan.apply_levels(x_all, 2, 6).cpu().numpy()
+    plan.sync()
+    row = 0
+    for l in range(2, 7):
+        nb = tree.levels[l].shape[0]
+        tg = np.sort(rng.choice(nb, size=min(24, nb), replace=False))
+        ref = om.m2l_svd_targets(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64), tg)[:, 0, :]
+        err = rel(out[row:row + nb][tg], ref)
+        print(f"sphere2m f16x3 level {l}: sampled rel L2 {err:.3e}")
+        assert err <= 1e-6, err
+        row += nb
+
+
+def test_f16x3_scaling_extremes(g, oracle_factors, sphere_small):
+    """Per-box scaling keeps FP16 accuracy when box densities span 30 orders
+    of magnitude (and for all-zero boxes): each level's rows are scaled by
+    10^k, k from -15 to 15, some rows zero."""
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, "f16x3", tree, (3,))
+    q = qs[3].astype(np.float64).copy()
+    rng = np.random.default_rng(12)
+    q *= 10.0 ** rng.integers(-15, 16, size=(q.shape[0], 1, 1))
+    q[::17] = 0.0
+    out = plan.apply(torch.from_numpy(q.astype(np.float32)).cuda(), 3).cpu().numpy()
+    plan.sync()
+    ref = om.m2l_svd(tree.levels[3], 3, tree.r0, f, q.astype(np.float32).astype(np.float64))
+    # judge each target against the size of its own potential: the scales differ by 1e30
+    for t in rng.choice(q.shape[0], 64, replace=False):
+        if np.linalg.norm(ref[t]) > 0:
+            assert rel(out[t], ref[t]) <= 1e-5, t
+    err = rel(out, ref)
+    print(f"f16x3 with 1e-15..1e15 box scales: rel L2 {err:.3e}")
+    assert err <= 1e-6
+
+
+def test_f16x3_unsupported_paths(g):
+    from paper_1211_2517_gb300 import KifmmError
+
+    plan = g.M2LPlan(6, 1e-7, 0.1, "f16x3")
+    with pytest.raises(KifmmError, match="UNSUPPORTED"):
+        plan.set_stage2(10.0)
+    with pytest.raises(KifmmError, match="UNSUPPORTED"):
+        g.PointFMM(plan, synth.points_uniform_cube(100, 1), 3)
+    box = np.array([[0, 0, 0], [3, 0, 0]], dtype=np.int32)
+    plan.set_level(2, box, 0.5)
+    x = torch.zeros((2, 1, plan.n), dtype=torch.float32, device="cuda")
+    with pytest.raises(KifmmError, match="UNSUPPORTED"):
+        g.apply_batch([{"plan": plan, "instance": 0, "level_lo": 2, "level_hi": 2, "x": x,
+                        "out": torch.zeros_like(x)}])
+    plan.close()
+
+
 @pytest.fixture(scope="module")
 def torus_mid():
     """Torus R=1, r=0.3, 300000 points, depth 5, p = 10, eps = 1e-8 (r = 271 > 256:
@@ -342,7 +406,7 @@ def torus_mid():
     return tree, qs
 
 
-@pytest.mark.parametrize("precision", ["split6", "fp32"])
+@pytest.mark.parametrize("precision", ["split6", "fp32", "f16x3"])
 def test_p10_parity_levels_batch(g, oracle_factors, torus_mid, precision):
     tree, qs = torus_mid
     f = oracle_factors(10, 0.1, 1e-8)
@@ -401,6 +465,45 @@ def test_autotune_keeps_parity_and_caches(g, oracle_factors, torus_mid, monkeypa
     plan.close()
 
 
+def test_f16x3_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch, tmp_path):
+    """The core variants an FP16-split plan can run (drained partials of two
+    or one K-chunks, the classic kernel with N = 192 or 96, round-robin or
+    contiguous tiles) against the oracle, forward and adjoint."""
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("KIFMM_M2L_AUTOTUNE_CACHE", str(cache))
+    plan = make_plan(g, 8, 1e-7, "f16x3", tree, (2, 3, 4))
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in (2, 3, 4)])).cuda()
+    res = plan.autotune(x_all, 2, 4, reps=2)
+    print("autotune f16x3", res)
+    assert res["variant"] in (0, 2, 3, 4, 5, 6)
+    import json
+
+    key = list(json.loads(cache.read_text()))[0]
+    refs = {(l, adj): (om.m2l_svd_adjoint if adj else om.m2l_svd)(tree.levels[l], l, tree.r0, f,
+                                                                   qs[l].astype(np.float64))
+            for l in (2, 3, 4) for adj in (False, True)}
+    for chunk, contig, variant in [(192, 0, 2), (192, 1, 2), (192, 0, 3), (192, 0, 4), (192, 1, 5), (192, 0, 6),
+                                   (192, 1, 6), (192, 0, 0), (96, 1, 0)]:
+        cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "variant": %d, "core_ms": 1.0}\n}\n'
+                         % (key, chunk, contig, variant))
+        got = plan.autotune(x_all, 2, 4, reps=1)
+        assert got["from_cache"]
+        for adj in (False, True):
+            out = plan.apply_levels(x_all, 2, 4, adjoint=adj).cpu().numpy()
+            plan.sync()
+            row = 0
+            for l in (2, 3, 4):
+                nb = tree.levels[l].shape[0]
+                err = rel(out[row:row + nb], refs[(l, adj)])
+                print(f"f16x3 chunk {chunk} contiguous {contig} variant {variant} adjoint {adj} level {l}: "
+                      f"rel L2 {err:.3e}")
+                assert err <= TOL["f16x3"], (chunk, contig, variant, adj, l, err)
+                row += nb
+    plan.close()
+
+
 def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch, tmp_path):
     """Every core variant the autotuner can pick for a p = 8 split6 plan
     (partials of two or one K-chunks drained into registers; the A-resident kernel, which
@@ -421,8 +524,8 @@ def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch
     refs = {(l, adj): (om.m2l_svd_adjoint if adj else om.m2l_svd)(tree.levels[l], l, tree.r0, f,
                                                                    qs[l].astype(np.float64))
             for l in (2, 3, 4) for adj in (False, True)}
-    for chunk, contig, variant in [(192, 0, 2), (192, 1, 2), (192, 0, 3), (192, 0, 1), (192, 1, 1), (192, 0, 0),
-                                   (192, 1, 0), (96, 0, 0)]:
+    for chunk, contig, variant in [(192, 0, 2), (192, 1, 2), (192, 0, 3), (192, 0, 4), (192, 1, 4), (192, 0, 5),
+                                   (192, 0, 1), (192, 1, 1), (192, 0, 0), (192, 1, 0), (96, 0, 0)]:
         cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "variant": %d, "core_ms": 1.0}\n}\n'
                          % (key, chunk, contig, variant))
         got = plan.autotune(x_all, 2, 4, reps=1)
