@@ -564,7 +564,8 @@ def run_batch64(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f16x3": "f16", "fp32": "f32"}.get(args.precision, "bf16"), "data": "synthetic",
         "config": {"workload": "batch64: 64 ellipsoid instances (axes U[0.5,2], N log-uniform 5e4-1e6, depth "
                                "U{3..6}, p U{6,8,10}, eps 1e-7, d 0.1), 16 rhs each, N(0,1) upward-equivalent "
                                "densities, all M2L levels in one grouped batch replayed from a CUDA graph",
@@ -574,7 +575,8 @@ def run_batch64(args, rank, world, local_rank):
                      "frac": achieved / bf16_peak, "traffic": None,
                      "kernel": "whole batch (compression, core and expansion of three operators)",
                      "flops_per_unit": "2 r^2 per box pair and rhs"},
-        "clocks": clocks, "e2e": None, "gpu_launches": 15 * args.steps, "cpu_baseline": None,
+        "clocks": clocks, "e2e": None, "gpu_launches": (18 if args.precision == "f16x3" else 15) * args.steps,
+        "cpu_baseline": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -44,6 +44,7 @@ struct PlanGroup {
     DevBuf<__nv_bfloat16> qb;     // pieces of q~ [pieces][rows_total + 1][r_pad]
     DevBuf<__nv_bfloat16> sp;     // BF16 pieces of the compression / expansion inputs
     DevBuf<float> pt;             // p~ [rows_total][r_pad]
+    DevBuf<float> qt, qs;         // f16x3: q~ in FP32 [rows_total][r_pad], row factors [rows_total + 1]
 };
 
 struct BatchEntry {
@@ -94,7 +95,7 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
         if (st != KIFMM_OK) return st;
         ItemPairs p{ms, x.nrhs, rows, (int)scales.size()};
         for (int l = x.level_lo; l <= x.level_hi; ++l)
-            scales.push_back((float)std::ldexp(1.0 / find_level(plan, x.instance, l)->r0, l));
+            scales.push_back((float)(std::ldexp(1.0 / find_level(plan, x.instance, l)->r0, l) * plan->core_inv_scale));
         const long item_rows = ms->total_boxes * x.nrhs;
         g.row_base.push_back(rows);
         RowSeg si{x.q_up, nullptr, (int)item_rows, tiles_so_far, (int)rows, 1.0f, 0.0f};
@@ -114,6 +115,10 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     KIFMM_CUDA_TRY(g.pt.ensure((size_t)std::max<long>(rows, 1) * plan->rp));
     KIFMM_CUDA_TRY(g.qb.ensure((size_t)(rows + 1) * plan->rp * std::max(plan->pieces, 1)));
     KIFMM_CUDA_TRY(g.sp.ensure(split_elems(plan, tiles_so_far)));
+    if (plan->prm.precision == KIFMM_PREC_F16X3) {
+        KIFMM_CUDA_TRY(g.qt.ensure((size_t)std::max<long>(rows, 1) * plan->rp));
+        KIFMM_CUDA_TRY(g.qs.ensure((size_t)rows + 1));
+    }
     for (size_t i = 0; i < seg_out.size(); ++i) seg_out[i].Af = g.pt.ptr + ip[i].base * plan->rp;
     KIFMM_CUDA_TRY(g.seg_in.upload(seg_in.data(), seg_in.size()));
     KIFMM_CUDA_TRY(g.seg_out.upload(seg_out.data(), seg_out.size()));
@@ -153,21 +158,28 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     return KIFMM_OK;
 }
 
-// Enqueue the five launches of one plan group on stream s: split and
-// compression, core, split and expansion.
+// Enqueue the launches of one plan group on stream s: split and
+// compression (plus the scaled FP16 split for f16x3), core, split and
+// expansion.
 int enqueue_group(PlanGroup& g, cudaStream_t s) {
     kifmm_m2l_plan plan = g.plan;
     if (g.rows_total == 0) return KIFMM_OK;
     const int n = plan->n, rp = plan->rp;
+    const bool f16 = plan->prm.precision == KIFMM_PREC_F16X3;
     const long piece_stride = (g.rows_total + 1) * rp;
     {
         const int st = run_compress(plan, nullptr, 0, g.seg_in.ptr, (int)g.items.size(), g.in_tiles, g.sp.ptr,
-                                    g.qb.ptr, piece_stride, nullptr, g.pt.ptr, s);
+                                    g.qb.ptr, piece_stride, f16 ? g.qt.ptr : nullptr, g.pt.ptr, s);
         if (st != KIFMM_OK) return st;
     }
-    for (int pc = 0; pc < plan->pieces; ++pc)
-        KIFMM_CUDA_TRY(cudaMemsetAsync(g.qb.ptr + pc * piece_stride + g.rows_total * rp, 0,
-                                       rp * sizeof(__nv_bfloat16), s));
+    if (f16) {
+        const int st = split_core_operand_f16(plan, g.qt.ptr, g.rows_total, g.qb.ptr, piece_stride, g.qs.ptr, s);
+        if (st != KIFMM_OK) return st;
+    } else {
+        for (int pc = 0; pc < plan->pieces; ++pc)
+            KIFMM_CUDA_TRY(cudaMemsetAsync(g.qb.ptr + pc * piece_stride + g.rows_total * rp, 0,
+                                           rp * sizeof(__nv_bfloat16), s));
+    }
     {
         UmmaArgs a{};
         a.A = g.qb.ptr;
@@ -196,6 +208,8 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.ldd = rp;
         a.n_products = plan->products;
         a.hilo = plan->core_hilo;
+        a.f16 = f16 ? 1 : 0;
+        a.row_scale = f16 ? g.qs.ptr : nullptr;
         a.error_flag = plan->err_flag.ptr;
         KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     }
@@ -245,9 +259,8 @@ extern "C" int kifmm_m2l_apply_batch(int n_items, const kifmm_m2l_batch_item* it
             set_error("batch item " + std::to_string(i) + ": plan is NULL");
             return KIFMM_ERR_INVALID_ARG;
         }
-        if (x.plan->prm.precision == KIFMM_PREC_FP32 || x.plan->prm.precision == KIFMM_PREC_F16X3) {
-            set_error("batch item " + std::to_string(i) +
-                      ": batches run the BF16 tensor-core modes (not KIFMM_PREC_FP32 or KIFMM_PREC_F16X3)");
+        if (x.plan->prm.precision == KIFMM_PREC_FP32) {
+            set_error("batch item " + std::to_string(i) + ": batches run the tensor-core modes (not KIFMM_PREC_FP32)");
             return KIFMM_ERR_UNSUPPORTED;
         }
         if (x.nrhs < 1 || x.level_lo < 0 || x.level_hi < x.level_lo || x.level_hi - x.level_lo >= 32) {
