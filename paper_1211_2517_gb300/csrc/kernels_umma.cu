@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t c0_u = (uint32_t)L.na * a_u;
                 // drain (core): every product into one per-K-chunk partial
                 const bool drain = AMODE == A_GATHER && L.drain;
+                const bool pair_ok = drain && args.mma_pair && S >= 3;
                 const bool split_lo = AMODE == A_ROWS || (args.hilo && !drain);
                 int s = 0, tcount = 0, pcount = 0;
                 uint32_t ph = 0;
@@ -567,47 +568,62 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (drain) d_lo = d_hi;
                             hi_on = false;
                         }
-                        if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag)) {
+                        // with mma_pair the next chunk of the same partial is issued in
+                        // the same step (its stage waited for here as well)
+                        const bool pair = pair_ok && kc + 1 < KC && (kc + 1) % L.drain != 0;
+                        const int s1 = s + 1 == S ? 0 : s + 1;
+                        const uint32_t ph1 = s + 1 == S ? (ph ^ 1u) : ph;
+                        if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag) ||
+                            (pair && !mbar_wait(&sm->full[s1], ph1, sm, args.error_flag))) {
                             ok = false;
                             break;
                         }
                         if (AMODE == A_GATHER) fence_proxy_async();  // cp.async data -> tensor-core reads
                         tc_fence_after();
-                        const bool two = args.kdim - kc * CH >= 32;  // K steps of 16 in this chunk: 2 or 1
-                        const uint64_t sd = desc0 + (uint64_t)((uint32_t)s * stage_u);
                         constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
-                        if (two && nB == 0) {
-                            // common case, kept free of branches between the MMAs
+                        auto issue_chunk = [&](int ss, int kk) {
+                            const bool two = args.kdim - kk * CH >= 32;  // K steps of 16 in this chunk: 2 or 1
+                            const uint64_t sd = desc0 + (uint64_t)((uint32_t)ss * stage_u);
+                            if (two && nB == 0) {
+                                // common case, kept free of branches between the MMAs
 #pragma unroll
-                            for (int pi = P0; pi < 6; ++pi) {
-                                const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !split_lo;
-                                const uint32_t d = to_hi ? d_hi : d_lo;
-                                const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
-                                const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
-                                umma_bf16(d, ad, bd, idA, (to_hi ? hi_on : lo_on) ? 1u : 0u);
-                                umma_bf16(d, ad + 2, bd + 2, idA, 1u);
-                                hi_on = hi_on || to_hi;
-                                lo_on = lo_on || !to_hi;
-                            }
-                        } else {
-#pragma unroll
-                            for (int pi = P0; pi < 6; ++pi) {
-                                const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !split_lo;
-                                const uint32_t d = to_hi ? d_hi : d_lo;
-                                const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
-                                const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
-                                const uint32_t en0 = (to_hi ? hi_on : lo_on) ? 1u : 0u;
-                                umma_bf16(d, ad, bd, idA, en0);
-                                if (nB > 0) umma_bf16(d + (uint32_t)nA, ad, bd + nB_off, idB, en0);
-                                if (two) {
+                                for (int pi = P0; pi < 6; ++pi) {
+                                    const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !split_lo;
+                                    const uint32_t d = to_hi ? d_hi : d_lo;
+                                    const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
+                                    const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
+                                    umma_bf16(d, ad, bd, idA, (to_hi ? hi_on : lo_on) ? 1u : 0u);
                                     umma_bf16(d, ad + 2, bd + 2, idA, 1u);
-                                    if (nB > 0) umma_bf16(d + (uint32_t)nA, ad + 2, bd + nB_off + 2, idB, 1u);
+                                    hi_on = hi_on || to_hi;
+                                    lo_on = lo_on || !to_hi;
                                 }
-                                hi_on = hi_on || to_hi;
-                                lo_on = lo_on || !to_hi;
+                            } else {
+#pragma unroll
+                                for (int pi = P0; pi < 6; ++pi) {
+                                    const bool to_hi = (kA[pi] == 0 && kB[pi] == 0) || !split_lo;
+                                    const uint32_t d = to_hi ? d_hi : d_lo;
+                                    const uint64_t ad = sd + (uint64_t)(kA[pi] * a_u);
+                                    const uint64_t bd = sd + (uint64_t)(c0_u + kB[pi] * c_u);
+                                    const uint32_t en0 = (to_hi ? hi_on : lo_on) ? 1u : 0u;
+                                    umma_bf16(d, ad, bd, idA, en0);
+                                    if (nB > 0) umma_bf16(d + (uint32_t)nA, ad, bd + nB_off, idB, en0);
+                                    if (two) {
+                                        umma_bf16(d, ad + 2, bd + 2, idA, 1u);
+                                        if (nB > 0) umma_bf16(d + (uint32_t)nA, ad + 2, bd + nB_off + 2, idB, 1u);
+                                    }
+                                    hi_on = hi_on || to_hi;
+                                    lo_on = lo_on || !to_hi;
+                                }
                             }
+                            umma_commit(&sm->empty[ss]);
+                        };
+                        issue_chunk(s, kc);
+                        if (pair) {
+                            issue_chunk(s1, kc + 1);
+                            s = s1;
+                            ph = ph1;
+                            ++kc;
                         }
-                        umma_commit(&sm->empty[s]);
                         if ((AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) ||
                             (drain && (kc % L.drain == L.drain - 1 || kc == KC - 1))) {
                             umma_commit(&sm->part_full[ps]);
