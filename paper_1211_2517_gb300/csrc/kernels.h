@@ -158,7 +158,7 @@ struct UmmaArgs {
     int f16;                  // A_GATHER: A and B pieces are FP16 (else BF16)
     const float* row_scale;   // E_RED: when set, output row r is scaled by row_scale[row_src[r]]
     int red_bulk;             // E_RED, drained partials: reduce rows into D with TMA bulk reductions
-    int mma_pair;             // drained partials: the MMA thread takes two K-chunks of a partial per step
+    int mma_pair;             // drained partials: K-chunks of a partial the MMA thread takes per step (<= 1: one)
     int* error_flag;          // device int, set when a bounded wait times out
 };
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& args, int num_sms, cudaStream_t stream);

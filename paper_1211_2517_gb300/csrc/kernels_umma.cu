@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t c0_u = (uint32_t)L.na * a_u;
                 // drain (core): every product into one per-K-chunk partial
                 const bool drain = AMODE == A_GATHER && L.drain;
-                const bool pair_ok = drain && args.mma_pair && S >= 3;
+                const int group_max = drain && args.mma_pair > 1 ? (args.mma_pair < S - 1 ? args.mma_pair : S - 1) : 1;
                 const bool split_lo = AMODE == A_ROWS || (args.hilo && !drain);
                 int s = 0, tcount = 0, pcount = 0;
                 uint32_t ph = 0;
@@ -568,13 +568,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (drain) d_lo = d_hi;
                             hi_on = false;
                         }
-                        // with mma_pair the next chunk of the same partial is issued in
-                        // the same step (its stage waited for here as well)
-                        const bool pair = pair_ok && kc + 1 < KC && (kc + 1) % L.drain != 0;
-                        const int s1 = s + 1 == S ? 0 : s + 1;
-                        const uint32_t ph1 = s + 1 == S ? (ph ^ 1u) : ph;
-                        if (!mbar_wait(&sm->full[s], ph, sm, args.error_flag) ||
-                            (pair && !mbar_wait(&sm->full[s1], ph1, sm, args.error_flag))) {
+                        // with mma_pair > 1 the next chunks of the same partial (up to
+                        // mma_pair in all, leaving a ring slot to the producers) are
+                        // issued in the same step, their stages waited for here as well
+                        int grp = 1;
+                        while (grp < group_max && kc + grp < KC && (kc + grp) % L.drain != 0) ++grp;
+                        bool got_all = true;
+                        {
+                            int ss = s;
+                            uint32_t pp = ph;
+                            for (int gi = 0; gi < grp && got_all; ++gi) {
+                                got_all = mbar_wait(&sm->full[ss], pp, sm, args.error_flag);
+                                if (++ss == S) {
+                                    ss = 0;
+                                    pp ^= 1u;
+                                }
+                            }
+                        }
+                        if (!got_all) {
                             ok = false;
                             break;
                         }
@@ -618,11 +629,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                             umma_commit(&sm->empty[ss]);
                         };
                         issue_chunk(s, kc);
-                        if (pair) {
-                            issue_chunk(s1, kc + 1);
-                            s = s1;
-                            ph = ph1;
+                        for (int gi = 1; gi < grp; ++gi) {
+                            if (++s == S) {
+                                s = 0;
+                                ph ^= 1u;
+                            }
                             ++kc;
+                            issue_chunk(s, kc);
                         }
                         if ((AMODE == A_ROWS && (kc % kPartChunks == kPartChunks - 1 || kc == KC - 1)) ||
                             (drain && (kc % L.drain == L.drain - 1 || kc == KC - 1))) {

@@ -124,17 +124,18 @@ struct kifmm_m2l_plan_s {
     // core launch fields of a variant: 1 A-resident; 2 / 4 / 9 partials of
     // two K-chunks drained into registers, 3 / 5 of one, 6 / 10 of three
     // (f16x3); 4 / 5 reduce the rows into p~ with TMA bulk reductions
-    // instead of vector atomics; 9 / 10 issue two K-chunks per MMA step
+    // instead of vector atomics; 9 / 10 issue two K-chunks per MMA step,
+    // 11 (f16x3) a whole partial of three
     int variant_drain() const {
         switch (tune_variant) {
             case 2: case 4: return 2;
             case 3: case 5: return 1;
-            case 6: case 10: return 3;
+            case 6: case 10: case 11: return 3;
             case 9: return 2;
             default: return 0;
         }
     }
-    int variant_pair() const { return (tune_variant == 9 || tune_variant == 10) ? 1 : 0; }
+    int variant_pair() const { return tune_variant == 11 ? 3 : (tune_variant == 9 || tune_variant == 10) ? 2 : 1; }
     int variant_bulk() const { return (tune_variant == 4 || tune_variant == 5) ? 1 : 0; }
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each (Cb: 2 FP16 pieces of tau K~ for F16X3)
