@@ -448,7 +448,7 @@ def run_ours(args, rank, world, local_rank):
     if args.precision != "fp32":
         from paper_1211_2517_gb300 import PointFMM
 
-        ftree = PointFMM(plan6, wl.points, wl.depth)
+        ftree = PointFMM(plan_main, wl.points, wl.depth)
         qd = torch.tensor(wl.densities, dtype=torch.float32, device=dev)
         pot = torch.empty_like(qd)
         for parts in (3, 1, 2):
@@ -464,6 +464,7 @@ def run_ours(args, rank, world, local_rank):
         npts = wl.points.shape[0]
         fmm = {"value": npts * k_f / (f_ms / 1e3), "unit": "points/s (potential at every point from all others)",
                "ms_per_evaluate": f_ms / k_f, "near_ms": near_ms / k_f, "far_ms": far_ms / k_f,
+               "m2l_precision": args.precision,
                "points": npts, "depth": info["depth"], "leaves": info["leaves"], "m2l_pairs": info["m2l_pairs"],
                "near_pairs": info["near_pairs"],
                "near_pairs_per_s": info["near_pairs"] * k_f / (near_ms / 1e3),

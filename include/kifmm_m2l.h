@@ -75,8 +75,8 @@ extern "C" {
                                        its largest entry in [2^14, 2^15), the cores by one
                                        that puts theirs in [2^13, 2^14), so both FP16 pieces
                                        stay normal where they matter; dropped terms <= 2^-22.
-                                       apply, apply_levels (and adjoints), apply_batch; not
-                                       stage 2, apply_noalloc or point-source evaluation */
+                                       apply, apply_levels (and adjoints), apply_batch and
+                                       point-source evaluation; not stage 2 or apply_noalloc */
 
 #define KIFMM_N_OFFSETS        316  /* unique M2L offsets per level, Sec. 3.1 */
 

@@ -24,7 +24,8 @@
 // Layout (rows = boxes of levels 2..depth back to back, level order):
 //   qb3  BF16 [3][rows + 1][rp]  q~ pieces, last row zero
 //   pt   FP32 [rows][rp]         p~
-//   qf   FP32 [max boxes of a level][rp]   one level's q~ before its split
+//   qf   FP32 [rows][rp]          q~ of every level (M~ accumulates into it)
+//   qh, qs  f16x3 plans: the core's FP16 pieces [2][rows + 1][rp] of qf, row factors
 //   sl   BF16 [3][(tiles + 1) * 128][rp]   one level's p~ pieces (L~ input)
 //   pc   FP32 [leaves][n_pad]    check potentials, then e_leaf
 //   sp   BF16 split scratch of the S~ and T~ GEMMs
@@ -132,7 +133,8 @@ struct kifmm_fmm_s {
     DevBuf<int> perm, leaf_start, near_start, near_idx;
     DevBuf<int4> leaf_ijk;
     DevBuf<__nv_bfloat16> qb3, sl, sp;
-    DevBuf<float> qf, pt, pc;
+    DevBuf<float> qf, pt, pc, qs;
+    DevBuf<__nv_bfloat16> qh;
     int max_level_boxes = 0, max_down_tiles = 0;
 };
 
@@ -360,7 +362,11 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
     KIFMM_CUDA_TRY(f->qb3.ensure((size_t)3 * (f->rows + 1) * rp));
     KIFMM_CUDA_TRY(cudaMemset(f->qb3.ptr, 0, f->qb3.count * sizeof(__nv_bfloat16)));
     KIFMM_CUDA_TRY(f->pt.ensure((size_t)f->rows * rp));
-    KIFMM_CUDA_TRY(f->qf.ensure((size_t)std::max(f->max_level_boxes, 1) * rp));
+    KIFMM_CUDA_TRY(f->qf.ensure((size_t)std::max<int64_t>(f->rows, 1) * rp));
+    if (plan->prm.precision == KIFMM_PREC_F16X3) {
+        KIFMM_CUDA_TRY(f->qh.ensure((size_t)2 * (f->rows + 1) * rp));
+        KIFMM_CUDA_TRY(f->qs.ensure((size_t)f->rows + 1));
+    }
     KIFMM_CUDA_TRY(f->sl.ensure((size_t)3 * (f->max_down_tiles + 1) * kTileRows * rp));
     KIFMM_CUDA_TRY(f->sp.ensure((size_t)3 * leaf_tiles * kTileRows * std::max(rp, np)));
     KIFMM_CUDA_TRY(f->pc.ensure((size_t)B * np));
@@ -401,6 +407,8 @@ int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s)
             a.Dp = f->qb3.ptr + f->off[L] * rp;
             a.dp_piece_stride = qstride;
             a.dp_pieces = 3;
+            // f16x3: the leaves' FP32 q~ joins the array the core's FP16 split reads
+            if (plan->prm.precision == KIFMM_PREC_F16X3) a.Df = f->qf.ptr + f->off[L] * rp;
             a.n_products = 6;
             a.hilo = 1;
             a.core_drain = 1;
@@ -411,11 +419,12 @@ int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s)
         for (int lp = L - 1; lp >= 2; --lp) {
             const auto& ps = f->up[lp];
             const int nb = f->nbox[lp];
-            KIFMM_CUDA_TRY(launch_zero(f->qf.ptr, (long)nb * rp, s));
+            float* ql = f->qf.ptr + f->off[lp] * rp;
+            KIFMM_CUDA_TRY(launch_zero(ql, (long)nb * rp, s));
             int st = pass_gemm(plan, f->qb3.ptr, qstride, (int)f->rows, plan->Mb.ptr, f->up_src.ptr + ps.tile0 * kTileRows,
-                               f->up_dst.ptr + ps.tile0 * kTileRows, f->up_k.ptr + ps.tile0, ps.n_tiles, f->qf.ptr, s);
+                               f->up_dst.ptr + ps.tile0 * kTileRows, f->up_k.ptr + ps.tile0, ps.n_tiles, ql, s);
             if (st != KIFMM_OK) return st;
-            KIFMM_CUDA_TRY(launch_split_rows(f->qf.ptr, nb, rp, rp, rp, nullptr, 0, (nb + kTileRows - 1) / kTileRows,
+            KIFMM_CUDA_TRY(launch_split_rows(ql, nb, rp, rp, rp, nullptr, 0, (nb + kTileRows - 1) / kTileRows,
                                              f->qb3.ptr + f->off[lp] * rp, qstride, 3, s, /*pad_rows=*/0));
         }
         // M2L: p~ = s_l sum K~_o q~ over every level's pairs
@@ -429,7 +438,14 @@ int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s)
             if (st != KIFMM_OK) return st;
             ScaleTable scales{};
             for (int l = 2; l <= L; ++l) scales.s[l - 2] = (float)std::ldexp(1.0 / f->r0, l);
-            st = launch_core(plan, f->qb3.ptr, qstride, (int)f->rows, *ts, 1, scales, f->pt.ptr, s);
+            if (plan->prm.precision == KIFMM_PREC_F16X3) {
+                // the core's operand: every level's q~ as scaled FP16 pieces
+                st = split_core_operand_f16(plan, f->qf.ptr, f->rows, f->qh.ptr, qstride, f->qs.ptr, s);
+                if (st != KIFMM_OK) return st;
+                st = launch_core(plan, f->qh.ptr, qstride, (int)f->rows, *ts, 1, scales, f->pt.ptr, s, f->qs.ptr);
+            } else {
+                st = launch_core(plan, f->qb3.ptr, qstride, (int)f->rows, *ts, 1, scales, f->pt.ptr, s);
+            }
             if (st != KIFMM_OK) return st;
         }
         // L~: p~_child += L~_c p~_parent, level by level away from the root
@@ -530,8 +546,8 @@ int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points
             set_error("non-finite point coordinate at index " + std::to_string(i / 3));
             return KIFMM_ERR_INVALID_ARG;
         }
-    if (plan->prm.precision == KIFMM_PREC_FP32 || plan->prm.precision == KIFMM_PREC_F16X3) {
-        set_error("point-source evaluation runs its passes on the BF16 tensor cores: use a BF16 / split precision");
+    if (plan->prm.precision == KIFMM_PREC_FP32) {
+        set_error("point-source evaluation runs its passes on the tensor cores: use a BF16 / split / f16x3 precision");
         return KIFMM_ERR_UNSUPPORTED;
     }
     if (plan->n > 512) {

@@ -10,7 +10,8 @@ Tolerances (relative L2 over the compared points):
                    entries up to ~3e6 (p = 8) from the check-to-equivalent
                    pseudo-inverse; an FP32 evaluation of them was simulated
                    at 3e-7 of the total potential
-    total          1e-6   (split6; split3 3e-5, bf16 1e-2 as for the M2L)
+    total          1e-6   (split6 and f16x3; split3 3e-5, bf16 1e-2 as for the
+                          M2L)
   against the direct sum (Eq. eq_eval): the method's own error (p = 8,
   eps = 1e-7: ~1e-7 in FP64) plus the above, 1e-6.
 """
@@ -29,7 +30,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 D = 0.1
-TOL = {"split6": 1e-6, "split3": 3e-5, "bf16": 1e-2}
+TOL = {"split6": 1e-6, "f16x3": 1e-6, "split3": 3e-5, "bf16": 1e-2}
 
 
 def rel(a, b):
@@ -109,6 +110,18 @@ def test_sphere_ragged_matches_oracle(g, sphere_case):
     assert e_far < 2e-6 and e_all < 1e-6
 
 
+def test_sphere_f16x3_matches_oracle(g, sphere_case):
+    """The f16x3 core (per-box scaled FP16 pieces of every level's q~) on the
+    ragged sphere tree: far field and total against the oracle."""
+    pts, q, _, near, far = sphere_case
+    plan = g.M2LPlan(8, 1e-7, D, "f16x3")
+    _, got = run(g, plan, pts, q, 5)
+    _, got_far = run(g, plan, pts, q, 5, parts=2)
+    e_all, e_far = rel(got, near + far), rel(got_far, far)
+    print(f"sphere65k p=8 f16x3: total {e_all:.3e} far {e_far:.3e}")
+    assert e_far < 2e-6 and e_all < TOL["f16x3"]
+
+
 def test_sphere_matches_direct_sum(g, sphere_case):
     pts, q, _, _, _ = sphere_case
     plan = g.M2LPlan(8, 1e-7, D, "split6")
@@ -120,7 +133,7 @@ def test_sphere_matches_direct_sum(g, sphere_case):
     assert e < 1e-6
 
 
-@pytest.mark.parametrize("precision", ["split3", "bf16"])
+@pytest.mark.parametrize("precision", ["f16x3", "split3", "bf16"])
 def test_core_precisions(g, cube_case, precision):
     wl, near, far = cube_case
     plan = g.M2LPlan(6, 1e-7, D, precision)

@@ -385,8 +385,6 @@ def test_f16x3_unsupported_paths(g):
     plan = g.M2LPlan(6, 1e-7, 0.1, "f16x3")
     with pytest.raises(KifmmError, match="UNSUPPORTED"):
         plan.set_stage2(10.0)
-    with pytest.raises(KifmmError, match="UNSUPPORTED"):
-        g.PointFMM(plan, synth.points_uniform_cube(100, 1), 3)
     plan.close()
 
 
