@@ -63,6 +63,16 @@ extern "C" {
 
 /* ---- enums ------------------------------------------------------------- */
 #define KIFMM_KERNEL_LAPLACE   0    /* G(x,y) = 1 / (4 pi |x - y|), Sec. 4 */
+#define KIFMM_KERNEL_YUKAWA    1    /* G(x,y) = exp(-kappa |x - y|) / (4 pi |x - y|): radial
+                                       (translation invariant, K_o^T = K_{-o}) but not
+                                       homogeneous, so its compressed operators depend on the
+                                       box size (Sec. 3.1's O(L) case): a plan serves the boxes
+                                       of one half-width, box_halfwidth, and L levels take L
+                                       plans.  The plan's unit operator is
+                                       h G(h (2 o + (1+d)(u_i - u_j))) = exp(-kappa h r) /
+                                       (4 pi r), so the level scale 2^l / r0 = 1 / h applies as
+                                       for the Laplace kernel.  M2L only: point-source
+                                       evaluation and the pass operators are Laplace. */
 
 /* Arithmetic of the core products sum_o K~_o q~ (Sec. 3.1).  Vt compression
  * and U expansion are FP32 in every mode. */
@@ -82,12 +92,18 @@ extern "C" {
 
 /* ---- types ------------------------------------------------------------- */
 typedef struct kifmm_m2l_params {
-    int    kernel_id;  /* KIFMM_KERNEL_LAPLACE (others: KIFMM_ERR_UNSUPPORTED)          */
+    int    kernel_id;  /* KIFMM_KERNEL_LAPLACE or KIFMM_KERNEL_YUKAWA                  */
     int    p;          /* points per cube edge, 2 <= p <= 12; n = 6(p-1)^2+2             */
     double eps;        /* rank cutoff eps_1: keep sigma_i >= eps * sigma_0 (Sec. 3.1);
                           1e-12 <= eps < 1, or eps <= 0 to keep all n                    */
     double d;          /* surface ratio: surfaces at half-width (1+d) h, 0 <= d <= 2/3   */
     int    precision;  /* KIFMM_PREC_*                                                   */
+    double kappa;      /* KIFMM_KERNEL_YUKAWA: screening constant, kappa > 0 (1 / length);
+                          ignored for the Laplace kernel                                 */
+    double box_halfwidth; /* KIFMM_KERNEL_YUKAWA: half-width h of the boxes the plan serves,
+                          h > 0, kappa h <= 64; kifmm_m2l_set_level accepts only levels
+                          with root_halfwidth / 2^level = h (relative 1e-12); ignored for
+                          the Laplace kernel                                             */
 } kifmm_m2l_params;
 
 typedef struct kifmm_m2l_plan_s* kifmm_m2l_plan;   /* opaque; owned by the library */
@@ -102,7 +118,7 @@ typedef struct kifmm_m2l_plan_s* kifmm_m2l_plan;   /* opaque; owned by the libra
  * radial kernel, so the thin SVD's right basis spans U~'s space), forms
  * K~_o = U~^T K_o U~ in FP64 and uploads FP32 / BF16-split copies to the
  * current CUDA device.  The FP64 factors are cached on disk under
- * $KIFMM_M2L_CACHE (default: no cache) keyed by (kernel, p, d, eps).
+ * $KIFMM_M2L_CACHE (default: no cache) keyed by (kernel, p, d, eps, kappa h).
  * On success *out owns device memory until kifmm_m2l_destroy(). */
 int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out);
 
@@ -123,7 +139,9 @@ int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n);
  * half-width r0 / 2^level.  Builds the interaction-list pairs grouped by
  * offset on the host and uploads them.  Replaces an earlier registration of
  * the same (instance, level).  0 <= level <= 20, n_boxes >= 0, coordinates
- * in [0, 2^level), instance >= 0. */
+ * in [0, 2^level), instance >= 0.  A KIFMM_KERNEL_YUKAWA plan accepts only
+ * levels whose boxes have its box_halfwidth (KIFMM_ERR_INVALID_ARG
+ * otherwise). */
 int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth,
                         int n_boxes, const int32_t* box_ijk);
 
@@ -386,6 +404,21 @@ int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points
  * must be serialised.  Errors: KIFMM_ERR_INVALID_ARG (NULL, parts out of
  * 1..3), KIFMM_ERR_CUDA. */
 int kifmm_fmm_evaluate(kifmm_fmm fmm, const float* q, float* potential, int parts, void* stream);
+
+/* Double layer (Sec. 4, Eq. eq-doubles2m): with normals set, the sources are
+ * dipoles and evaluate computes
+ *   p_i = sum_{j != i} dG(x_i, x_j)/dn(x_j) q_j,
+ *   dG(x, y)/dn(y) = n(y) . (x - y) / (4 pi |x - y|^3),
+ * with dG/dn in the near field (S2T) and in the leaf check potentials (the
+ * first step of S2M); the equivalent densities and every later step are
+ * single layer, as for point charges.  The adjoint is a different operator
+ * (the evaluation is not symmetric in this mode).
+ *   normals  HOST float64 [n_points][3] in the caller's point order (n_j as
+ *            given: unit normals for a double-layer integral); copied to the
+ *            device in leaf order.  NULL returns the tree to single layer.
+ * Errors: KIFMM_ERR_INVALID_ARG (NULL fmm, non-finite entries),
+ * KIFMM_ERR_OOM, KIFMM_ERR_CUDA. */
+int kifmm_fmm_set_normals(kifmm_fmm fmm, const double* normals);
 
 /* Sizes of a tree: depth, leaves, boxes on levels 2..depth, M2L pairs over
  * those levels, and (target point, source point) pairs of the near field

@@ -30,6 +30,10 @@ these are the KIFMM ones it cites):
   potentials at the leaf's points.
 * The near field of a leaf is every leaf sharing at least one vertex with it,
   itself included (Sec. 2.1); a point does not act on itself.
+* Double layer (Sec. 4, Eq. eq-doubles2m): with normals n(y_j) given, the
+  sources are dipoles of density q_j, and G is replaced by dG/dn(y) in S2T
+  and in the leaf check potentials (the first step of S2M); the equivalent
+  densities and every later step stay single layer.
 * All leaves lie at the tree's depth.  Levels 0 and 1 have empty interaction
   lists, so M2L runs on levels 2..depth and L2L starts from level 2.
 * Octant of a child: c = 4 (i & 1) + 2 (j & 1) + (k & 1) from its integer
@@ -145,21 +149,31 @@ def near_leaves(tree, b: int) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # direct summation and near field (Eq. eq_eval)
 # ---------------------------------------------------------------------------
-def direct_sum(points, q, targets=None) -> np.ndarray:
-    """p_i = sum_{j != i} G(x_i, x_j) q_j for the listed targets (all by default)."""
+def source_kernel(x, pts, src, normals=None) -> np.ndarray:
+    """Kernel from the sources pts[src] to the points x: G, or dG/dn(y) with
+    the sources' normals for a double layer."""
+    if normals is None:
+        return geo.laplace_kernel(x, pts[src])
+    return geo.laplace_double_layer_kernel(x, pts[src], np.asarray(normals, dtype=np.float64)[src])
+
+
+def direct_sum(points, q, targets=None, normals=None) -> np.ndarray:
+    """p_i = sum_{j != i} G(x_i, x_j) q_j for the listed targets (all by
+    default); with ``normals``, dG(x_i, x_j)/dn(x_j) in place of G."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     idx = np.arange(pts.shape[0]) if targets is None else np.asarray(targets)
     out = np.zeros(idx.size)
+    every = np.arange(pts.shape[0])
     for c0 in range(0, idx.size, 256):
         t = idx[c0:c0 + 256]
-        k = geo.laplace_kernel(pts[t], pts)
+        k = source_kernel(pts[t], pts, every, normals)
         k[np.arange(t.size), t] = 0.0
         out[c0:c0 + 256] = k @ q
     return out
 
 
-def near_field(tree, points, q) -> np.ndarray:
+def near_field(tree, points, q, normals=None) -> np.ndarray:
     """S2T: potential at every point from the points of its leaf's near field."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
@@ -170,7 +184,7 @@ def near_field(tree, points, q) -> np.ndarray:
         if tgt.size == 0:
             continue
         src = np.concatenate([order[bounds[s]:bounds[s + 1]] for s in near_leaves(tree, b)])
-        k = geo.laplace_kernel(pts[tgt], pts[src])
+        k = source_kernel(pts[tgt], pts, src, normals)
         k[tgt[:, None] == src[None, :]] = 0.0
         out[tgt] = k @ q[src]
     return out
@@ -179,7 +193,7 @@ def near_field(tree, points, q) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # uncompressed far field (Eqs. eq-s2m .. eq-l2t)
 # ---------------------------------------------------------------------------
-def _upward(tree, points, p, d, q, rcond):
+def _upward(tree, points, p, d, q, rcond, normals=None):
     """Upward equivalent densities of levels 2..depth (S2M, M2M), every
     operator formed at the box's own half-width."""
     pts = np.asarray(points, dtype=np.float64)
@@ -192,7 +206,7 @@ def _upward(tree, points, p, d, q, rcond):
     for b in range(centres.shape[0]):
         idx = order[bounds[b]:bounds[b + 1]]
         x = geo.surface_points(p, centres[b], (3.0 - 2.0 * d) * h)
-        qu[L][b] = E @ (geo.laplace_kernel(x, pts[idx]) @ q[idx])
+        qu[L][b] = E @ (source_kernel(x, pts, idx, normals) @ q[idx])
     for level in range(L - 1, 1, -1):
         hp = tree.halfwidth(level)
         M = [m2m_matrix(p, d, hp, c, rcond) for c in range(8)]
@@ -204,13 +218,13 @@ def _upward(tree, points, p, d, q, rcond):
     return qu
 
 
-def fmm_uncompressed_far(tree, points, p: int, d: float, q, rcond: float = FMM_RCOND) -> np.ndarray:
+def fmm_uncompressed_far(tree, points, p: int, d: float, q, rcond: float = FMM_RCOND, normals=None) -> np.ndarray:
     """Far-field potential at every point: T L K M S q (Eq. eq-tran0) summed
     over the levels, each translating matrix formed at its box size."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     L = tree.depth
-    qu = _upward(tree, pts, p, d, q, rcond)
+    qu = _upward(tree, pts, p, d, q, rcond, normals)
     pd = {}
     for level in range(2, L + 1):
         pd[level] = m2l_mod.m2l_dense(tree.levels[level], level, tree.r0, p, d, qu[level],
@@ -237,9 +251,9 @@ def fmm_uncompressed_far(tree, points, p: int, d: float, q, rcond: float = FMM_R
 # ---------------------------------------------------------------------------
 # compressed far field (Sec. 3.3)
 # ---------------------------------------------------------------------------
-def leaf_check_potentials(tree, points, p: int, d: float, q) -> np.ndarray:
+def leaf_check_potentials(tree, points, p: int, d: float, q, normals=None) -> np.ndarray:
     """K(x^u, points in the leaf) q for every leaf, [B_depth, n]: the part of
-    S that depends on the points."""
+    S that depends on the points (double-layer kernel with ``normals``)."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     L = tree.depth
@@ -250,14 +264,14 @@ def leaf_check_potentials(tree, points, p: int, d: float, q) -> np.ndarray:
     for b in range(centres.shape[0]):
         idx = order[bounds[b]:bounds[b + 1]]
         x = geo.surface_points(p, centres[b], (3.0 - 2.0 * d) * h)
-        out[b] = geo.laplace_kernel(x, pts[idx]) @ q[idx]
+        out[b] = source_kernel(x, pts, idx, normals) @ q[idx]
     return out
 
 
-def compressed_upward(tree, points, f, ops: PassOperators, p: int, d: float, q) -> dict:
+def compressed_upward(tree, points, f, ops: PassOperators, p: int, d: float, q, normals=None) -> dict:
     """q~ of levels 2..depth: q~ = S~ q at the leaves, q~_C = sum_c M~_c q~_c."""
     L = tree.depth
-    qt = {L: tree.halfwidth(L) * leaf_check_potentials(tree, points, p, d, q) @ ops.Ws.T}
+    qt = {L: tree.halfwidth(L) * leaf_check_potentials(tree, points, p, d, q, normals) @ ops.Ws.T}
     for level in range(L - 1, 1, -1):
         par = parent_rows(tree, level + 1)
         oc = octant(tree.levels[level + 1])
@@ -308,9 +322,9 @@ def leaf_l2t(tree, points, p: int, d: float, e_leaf) -> np.ndarray:
     return out
 
 
-def fmm_compressed_far(tree, points, f, ops: PassOperators, p: int, d: float, q) -> np.ndarray:
+def fmm_compressed_far(tree, points, f, ops: PassOperators, p: int, d: float, q, normals=None) -> np.ndarray:
     """Far-field potential with Sec. 3.3's operators: T~ L~ K~ M~ S~ q."""
-    qt = compressed_upward(tree, points, f, ops, p, d, q)
+    qt = compressed_upward(tree, points, f, ops, p, d, q, normals)
     pt = compressed_downward(tree, f, ops, qt)
     L = tree.depth
     e_leaf = tree.halfwidth(L) * pt[L] @ ops.Wt.T
@@ -318,12 +332,13 @@ def fmm_compressed_far(tree, points, f, ops: PassOperators, p: int, d: float, q)
 
 
 def fmm_potential(tree, points, q, p: int, d: float, f=None, ops: PassOperators | None = None,
-                  rcond: float = FMM_RCOND) -> np.ndarray:
-    """Near field plus far field; compressed (Sec. 3.3) when ``f`` is given."""
+                  rcond: float = FMM_RCOND, normals=None) -> np.ndarray:
+    """Near field plus far field; compressed (Sec. 3.3) when ``f`` is given;
+    a double layer with ``normals``."""
     if f is None:
-        far = fmm_uncompressed_far(tree, points, p, d, q, rcond)
+        far = fmm_uncompressed_far(tree, points, p, d, q, rcond, normals)
     else:
         if ops is None:
             ops = pass_operators(f, p, d, rcond)
-        far = fmm_compressed_far(tree, points, f, ops, p, d, q)
-    return near_field(tree, points, q) + far
+        far = fmm_compressed_far(tree, points, f, ops, p, d, q, normals)
+    return near_field(tree, points, q, normals) + far

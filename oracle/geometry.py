@@ -21,6 +21,34 @@ def laplace_kernel(x: np.ndarray, y: np.ndarray) -> np.ndarray:
         return 1.0 / (FOUR_PI * np.sqrt(np.einsum("mnk,mnk->mn", diff, diff)))
 
 
+def yukawa_kernel(x: np.ndarray, y: np.ndarray, kappa: float) -> np.ndarray:
+    """G(x, y) = exp(-kappa |x - y|) / (4 pi |x - y|), the screened Coulomb
+    (Yukawa, modified Helmholtz) kernel: radial, so translation invariant
+    with K^T = K for swapped surfaces, but not homogeneous (Sec. 3.1's
+    O(L) case).  ``kappa = 0`` is ``laplace_kernel``.
+
+    ``x`` [m,3], ``y`` [n,3] -> [m,n] float64.
+    """
+    diff = x[:, None, :] - y[None, :, :]
+    r = np.sqrt(np.einsum("mnk,mnk->mn", diff, diff))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.exp(-kappa * r) / (FOUR_PI * r)
+
+
+def laplace_double_layer_kernel(x: np.ndarray, y: np.ndarray, n: np.ndarray) -> np.ndarray:
+    """dG(x, y)/dn(y) = n(y) . (x - y) / (4 pi |x - y|^3): the double-layer
+    kernel that replaces G in S2T and in the first step of S2M for a double
+    layer integral (Sec. 4, Eq. eq-doubles2m).  Gradient of G = 1/(4 pi |x - y|)
+    with respect to y, projected on the normal n(y) at the source.
+
+    ``x`` [m,3], ``y`` [k,3], ``n`` [k,3] -> [m,k] float64.
+    """
+    diff = x[:, None, :] - y[None, :, :]
+    r2 = np.einsum("mnk,mnk->mn", diff, diff)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.einsum("mnk,nk->mn", diff, n) / (FOUR_PI * r2 * np.sqrt(r2))
+
+
 def surface_grid(p: int) -> np.ndarray:
     """Integer grid points (i,j,k) in {0..p-1}^3 on the cube boundary.
 

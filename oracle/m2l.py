@@ -13,6 +13,12 @@ Conventions
   K_{l,o} = (r0 / 2**l)^(-1) K_o (Sec. 3.1).
 * Densities are laid out [boxes, n] (one right-hand side) or
   [boxes, nrhs, n].
+* Non-homogeneous kernels (the Yukawa kernel exp(-kappa r) / (4 pi r)) have
+  no such scaling: Sec. 3.1 compresses the translation matrices of every
+  level separately.  ``svd_factors(..., kappa=, h=)`` forms the 316 matrices
+  of boxes of half-width h from their coordinates and compresses them; the
+  result carries ``h`` and the M2L of a level with that box size applies it
+  with no level scale.
 """
 from __future__ import annotations
 
@@ -26,20 +32,26 @@ from . import geometry as geo
 # ---------------------------------------------------------------------------
 # translation matrices
 # ---------------------------------------------------------------------------
-def m2l_matrix_geometric(p: int, d: float, centre_t, centre_s, h: float) -> np.ndarray:
+def kernel_matrix(x, y, kappa: float = 0.0) -> np.ndarray:
+    """G(x_i, y_j): Laplace, or Yukawa with screening ``kappa`` > 0."""
+    return geo.laplace_kernel(x, y) if kappa == 0.0 else geo.yukawa_kernel(x, y, kappa)
+
+
+def m2l_matrix_geometric(p: int, d: float, centre_t, centre_s, h: float, kappa: float = 0.0) -> np.ndarray:
     """K_ij = G(x_i, y_j), x on the target's downward check surface and y on
     the source's upward equivalent surface, both at half-width (1+d) h
     (Eq. eq-m2l with the surfaces of Sec. 2.1).  Formed from coordinates."""
     x = geo.surface_points(p, centre_t, (1.0 + d) * h)
     y = geo.surface_points(p, centre_s, (1.0 + d) * h)
-    return geo.laplace_kernel(x, y)
+    return kernel_matrix(x, y, kappa)
 
 
-def unit_m2l_matrices(p: int, d: float) -> np.ndarray:
-    """The 316 translation matrices K_o of unit-half-width boxes, [316, n, n]."""
+def unit_m2l_matrices(p: int, d: float, kappa: float = 0.0, h: float = 1.0) -> np.ndarray:
+    """The 316 translation matrices K_o of boxes of half-width h (unit by
+    default) with centres 2 o h apart, [316, n, n]."""
     offs = geo.m2l_offsets()
     zero = np.zeros(3)
-    return np.stack([m2l_matrix_geometric(p, d, 2.0 * o.astype(np.float64), zero, 1.0)
+    return np.stack([m2l_matrix_geometric(p, d, 2.0 * h * o.astype(np.float64), zero, h, kappa)
                      for o in offs])
 
 
@@ -65,6 +77,8 @@ class SvdFactors:
     lam: np.ndarray
     r: int
     K: np.ndarray
+    h: float | None = None   # box half-width of per-level factors (non-homogeneous kernels)
+    kappa: float = 0.0
 
 
 def truncation_rank(sigma: np.ndarray, eps: float, tie_tol: float = 1e-13) -> int:
@@ -94,15 +108,19 @@ def _fix_signs(m: np.ndarray) -> np.ndarray:
     return m * s[None, :]
 
 
-def svd_factors(p: int, d: float, eps: float, r: int | None = None) -> SvdFactors:
+def svd_factors(p: int, d: float, eps: float, r: int | None = None, kappa: float = 0.0,
+                h: float | None = None) -> SvdFactors:
     """Fat and thin SVDs, truncation, compressed cores (Eqs. eq-kfat..eq-cmpM2Ls).
 
     K_fat = [K_1 ... K_316] = U Sigma [V_1^T ... V_316^T]   (Eq. fat)
     K_thin = [K_1; ...; K_316] = [Q_1; ...; Q_316] Lambda R^T  (Eq. thin)
     U~, R~ keep the columns whose singular value is >= eps * Sigma_00, and
-    K~_o = U~^T K_o R~.  ``r`` overrides the rank when given.
+    K~_o = U~^T K_o R~.  ``r`` overrides the rank when given.  With ``h``
+    (needed for kappa > 0) the matrices are those of boxes of half-width h.
     """
-    K = unit_m2l_matrices(p, d)
+    if kappa != 0.0 and h is None:
+        raise ValueError("a non-homogeneous kernel needs the box half-width h")
+    K = unit_m2l_matrices(p, d, kappa, 1.0 if h is None else h)
     n = K.shape[1]
     k_fat = np.concatenate(list(K), axis=1)          # n x 316n
     k_thin = np.concatenate(list(K), axis=0)         # 316n x n
@@ -115,12 +133,24 @@ def svd_factors(p: int, d: float, eps: float, r: int | None = None) -> SvdFactor
     Ut = _fix_signs(U[:, :r])
     Rr = _fix_signs(R[:, :r])
     C = np.matmul(np.matmul(Ut.T[None, :, :], K), Rr[None, :, :])   # U~^T K_o R~
-    return SvdFactors(U=Ut, R=Rr, C=C, sigma=sigma, lam=lam, r=r, K=K)
+    return SvdFactors(U=Ut, R=Rr, C=C, sigma=sigma, lam=lam, r=r, K=K, h=h, kappa=kappa)
 
 
 def level_scale(level: int, r0: float) -> float:
     """(r0 / 2**l)^m with m = -1 for the Laplace kernel (Sec. 3.1)."""
     return (1 << level) / r0
+
+
+def factors_scale(f: SvdFactors, level: int, r0: float) -> float:
+    """Scale that takes f's cores to boxes of this level: Sec. 3.1's
+    homogeneity for unit-size factors, 1 for per-level factors (which must
+    have been formed at this level's half-width)."""
+    if f.h is None:
+        return level_scale(level, r0)
+    h = r0 / (1 << level)
+    if abs(h - f.h) > 1e-12 * f.h:
+        raise ValueError(f"factors formed for half-width {f.h}, level {level} has {h}")
+    return 1.0
 
 
 # ---------------------------------------------------------------------------
@@ -132,12 +162,13 @@ def _as3(q):
 
 
 def m2l_dense(box_ijk, level: int, r0: float, p: int, d: float, q_up, centre=None,
-              targets=None) -> np.ndarray:
+              targets=None, kappa: float = 0.0) -> np.ndarray:
     """Uncompressed M2L, p^{t,d} = sum_{s in I^t} K(t,s) q^{s,u} (Eq. eq-m2l).
 
     Every pair's K(t,s)_ij = G(x_i^t, y_j^s) is formed from that pair's own
     surface coordinates at this level (no homogeneity shortcut); pairs are
     only batched by offset to keep NumPy busy.  q_up [B, n] or [B, nrhs, n].
+    ``kappa`` > 0: the Yukawa kernel exp(-kappa r) / (4 pi r).
     ``targets`` restricts the work to those target boxes (other rows stay 0).
     """
     q, squeeze = _as3(q_up)
@@ -159,7 +190,8 @@ def m2l_dense(box_ijk, level: int, r0: float, p: int, d: float, q_up, centre=Non
             x = centres[tg[idx]][:, None, :] + u[None, :, :]          # [P, n, 3]
             y = centres[sr[idx]][:, None, :] + u[None, :, :]
             diff = x[:, :, None, :] - y[:, None, :, :]                # [P, n, n, 3]
-            kts = 1.0 / (geo.FOUR_PI * np.sqrt(np.einsum("pijk,pijk->pij", diff, diff)))
+            dist = np.sqrt(np.einsum("pijk,pijk->pij", diff, diff))
+            kts = np.exp(-kappa * dist) / (geo.FOUR_PI * dist)
             out[tg[idx]] += np.einsum("pij,prj->pri", kts, q[sr[idx]])
     return out[:, 0, :] if squeeze else out
 
@@ -183,6 +215,8 @@ def m2l_svd(box_ijk, level: int, r0: float, f: SvdFactors, q_up, lists=None) -> 
         q~^s = R~^T q^{s,u}
         p~^t = (r0/2**l)^(-1) sum_{s in I^t} K~_{t-s} q~^s
         p^{t,d} = U~ p~^t
+
+    (no (r0/2**l)^(-1) for per-level factors of a non-homogeneous kernel).
     """
     q, squeeze = _as3(q_up)
     tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
@@ -191,7 +225,7 @@ def m2l_svd(box_ijk, level: int, r0: float, f: SvdFactors, q_up, lists=None) -> 
     for k in np.unique(ok):
         sel = ok == k
         pt[tg[sel]] += qt[sr[sel]] @ f.C[k].T          # K~_o q~ for every pair of offset o
-    pt *= level_scale(level, r0)
+    pt *= factors_scale(f, level, r0)
     out = pt @ f.U.T
     return out[:, 0, :] if squeeze else out
 
@@ -205,7 +239,7 @@ def m2l_svd_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, pbar, lists=N
     for k in np.unique(ok):
         sel = ok == k
         qt[sr[sel]] += pt[tg[sel]] @ f.C[k]            # K~_o^T p~bar
-    qt *= level_scale(level, r0)
+    qt *= factors_scale(f, level, r0)
     out = qt @ f.R.T
     return out[:, 0, :] if squeeze else out
 
@@ -231,7 +265,7 @@ def m2l_svd_targets(box_ijk, level: int, r0: float, f: SvdFactors, q_up, targets
             if s is None or np.max(np.abs((bt >> 1) - (bs >> 1))) > 1:
                 continue
             acc += (q[s] @ f.R) @ f.C[otab[tuple(o)]].T
-        out[row] = level_scale(level, r0) * acc @ f.U.T
+        out[row] = factors_scale(f, level, r0) * acc @ f.U.T
     return out
 
 
@@ -267,7 +301,7 @@ def m2l_svd_stage2(box_ijk, level: int, r0: float, f: SvdFactors, s2, q_up, list
         sel = ok == k
         uh, vh = s2[k]
         pt[tg[sel]] += (qt[sr[sel]] @ vh.T) @ uh.T
-    pt *= level_scale(level, r0)
+    pt *= factors_scale(f, level, r0)
     out = pt @ f.U.T
     return out[:, 0, :] if squeeze else out
 
@@ -282,7 +316,7 @@ def m2l_svd_stage2_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, s2, pb
         sel = ok == k
         uh, vh = s2[k]
         qt[sr[sel]] += (pt[tg[sel]] @ uh) @ vh
-    qt *= level_scale(level, r0)
+    qt *= factors_scale(f, level, r0)
     out = qt @ f.R.T
     return out[:, 0, :] if squeeze else out
 

@@ -34,13 +34,14 @@ EXPORTED = (
     "kifmm_m2l_set_stage2", "kifmm_m2l_stage2_ranks", "kifmm_m2l_stage2_host",
     "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
     "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error", "kifmm_m2l_version",
-    "kifmm_fmm_create", "kifmm_fmm_evaluate", "kifmm_fmm_info", "kifmm_fmm_destroy", "kifmm_m2l_pass_ops_host",
+    "kifmm_fmm_create", "kifmm_fmm_evaluate", "kifmm_fmm_set_normals", "kifmm_fmm_info", "kifmm_fmm_destroy", "kifmm_m2l_pass_ops_host",
 )
 
 
 class Params(ctypes.Structure):
     _fields_ = [("kernel_id", ctypes.c_int), ("p", ctypes.c_int), ("eps", ctypes.c_double),
-                ("d", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("d", ctypes.c_double), ("precision", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("box_halfwidth", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_pairs_host": [i32, i32, vp, pi64, vp, vp, vp],
         "kifmm_fmm_create": [vp, i64, vp, i32, vp, f64, ctypes.POINTER(vp)],
         "kifmm_fmm_evaluate": [vp, vp, vp, i32, vp],
+        "kifmm_fmm_set_normals": [vp, vp],
         "kifmm_fmm_info": [vp, pint, pi64, pi64, pi64, pi64],
         "kifmm_fmm_destroy": [vp],
         "kifmm_m2l_pass_ops_host": [ctypes.POINTER(Params), f64, pint, vp, vp],

@@ -619,6 +619,15 @@ namespace kifmm {
 int register_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth, int n_boxes,
                    const int32_t* box_ijk) {
     int st = KIFMM_OK;
+    if (plan->prm.kernel_id == KIFMM_KERNEL_YUKAWA) {
+        // the operators were formed for boxes of one half-width (Sec. 3.1, O(L) case)
+        const double h = std::ldexp(root_halfwidth, -level), hp = plan->prm.box_halfwidth;
+        if (!(std::fabs(h - hp) <= 1e-12 * hp)) {
+            set_error("this Yukawa plan serves boxes of half-width " + std::to_string(hp) + ", level " +
+                      std::to_string(level) + " has " + std::to_string(h) + ": one plan per level");
+            return KIFMM_ERR_INVALID_ARG;
+        }
+    }
     try {
         std::vector<int32_t> tg, sr, of;
         st = build_pairs(level, n_boxes, box_ijk, tg, sr, of);
@@ -1098,7 +1107,7 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
         offsets316(offs);
         const std::vector<double> u = unit_surface(plan->prm.p);
         for (int k = 0; k < kOffsets; ++k) {
-            unit_m2l_matrix(plan->prm.p, plan->prm.d, offs[k], u, kd.data());
+            unit_m2l_matrix(plan->prm.p, plan->prm.d, offs[k], u, kd.data(), kernel_kh(plan->prm));
             for (size_t i = 0; i < kd.size(); ++i) hk[(size_t)k * n * n + i] = (float)kd[i];
         }
         KIFMM_CUDA_TRY(plan->K.upload(hk.data(), hk.size()));

@@ -11,7 +11,8 @@
 //
 // Device, per evaluate, in stream order:
 //   gather     densities into the leaf-ordered point array        (CUDA cores)
-//   check      h K(x^u, points) q for every leaf                  (CUDA cores)
+//   check      h K(x^u, points) q for every leaf (double layer: h dG/dn(y),
+//              the first step of S2M, Eq. eq-doubles2m)           (CUDA cores)
 //   S~         q~_leaf = Ws (h K q): split + identity-row GEMM    (tensor cores)
 //   M~         level by level, children -> parents: gather GEMM over the
 //              8 octant groups with FP32 reductions, then split   (tensor cores)
@@ -19,7 +20,8 @@
 //   L~         level by level, parents -> children: split of the
 //              parents' p~, gather GEMM adding into the children  (tensor cores)
 //   T~ factor  e_leaf = h Ws^T p~_leaf: split + identity-row GEMM (tensor cores)
-//   leaf sums  L2T from e_leaf plus the near field, in the caller's order
+//   leaf sums  L2T from e_leaf plus the near field (double layer: dG/dn(y)),
+//              in the caller's order
 //
 // Layout (rows = boxes of levels 2..depth back to back, level order):
 //   qb3  BF16 [3][rows + 1][rp]  q~ pieces, last row zero
@@ -130,6 +132,9 @@ struct kifmm_fmm_s {
     std::vector<Pass> up, down;  // indexed by the parent level
     DevBuf<int> up_src, up_dst, up_k, dn_src, dn_dst, dn_k;
     DevBuf<float4> hi, lo, usurf;  // points in leaf units: hi (w = density) + lo
+    DevBuf<float4> nhi, nlo;       // double layer: normals as two FP32 words (leaf order)
+    bool dl = false;
+    std::vector<int32_t> h_perm;   // caller's index of every leaf-ordered point
     DevBuf<int> perm, leaf_start, near_start, near_idx;
     DevBuf<int4> leaf_ijk;
     DevBuf<__nv_bfloat16> qb3, sl, sp;
@@ -318,13 +323,13 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
         for (int t = 0; t < 3; ++t) c[t] = (f->centre[t] - f->r0) + (2.0 * lijk[3 * b + t] + 1.0) * h;
         for (int s = leaf_start[b]; s < leaf_start[b + 1]; ++s) {
             const int64_t i = order[s];
-            // leaf units s = (x - c) / h: hi on the 2^-12 grid (exact in FP32), lo the rest
+            // leaf units s = (x - c) / h: hi on the 2^-20 grid (exact in FP32 for
+            // |s| < 4, i.e. for every point inside the root cube), lo the rest
             float hv[3], lv[3];
             for (int t = 0; t < 3; ++t) {
                 const double v = (points[3 * i + t] - c[t]) / h;
-                const double vh = std::nearbyint(v * 4096.0) / 4096.0;
-                hv[t] = (float)vh;
-                lv[t] = (float)(v - vh);
+                hv[t] = (float)(std::nearbyint(v * 1048576.0) / 1048576.0);
+                lv[t] = (float)(v - (double)hv[t]);
             }
             h_hi[s] = make_float4(hv[0], hv[1], hv[2], 0.f);
             h_lo[s] = make_float4(lv[0], lv[1], lv[2], 0.f);
@@ -348,6 +353,7 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
     KIFMM_CUDA_TRY(f->hi.upload(h_hi.data(), h_hi.size()));
     KIFMM_CUDA_TRY(f->lo.upload(h_lo.data(), h_lo.size()));
     KIFMM_CUDA_TRY(f->perm.upload(order.data(), order.size()));
+    f->h_perm = order;
     KIFMM_CUDA_TRY(f->leaf_start.upload(leaf_start.data(), leaf_start.size()));
     KIFMM_CUDA_TRY(f->leaf_ijk.upload(h_lijk.data(), h_lijk.size()));
     KIFMM_CUDA_TRY(f->near_start.upload(near_start.data(), near_start.size()));
@@ -381,13 +387,17 @@ int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s)
     const float a_surf = (float)(3.0 - 2.0 * plan->prm.d);  // (3-2d) h in leaf units
     const int N = (int)f->n_points;
     KIFMM_CUDA_TRY(launch_gather_density(q, f->perm.ptr, f->hi.ptr, N, s));
+    const float4* nhi = f->dl ? f->nhi.ptr : nullptr;
+    const float4* nlo = f->dl ? f->nlo.ptr : nullptr;
     if (parts & KIFMM_FMM_FAR) {
         const long qstride = (f->rows + 1) * rp;
         const int leaf_tiles = (B + kTileRows - 1) / kTileRows;
-        // S~: check potentials h K(x^u, points) q (= sum q / (4 pi |.|) in leaf units),
-        // then q~ = Ws (.) into the leaf rows of qb3
-        KIFMM_CUDA_TRY(launch_leaf_check(f->hi.ptr, f->lo.ptr, f->leaf_start.ptr, B, f->usurf.ptr, n, a_surf,
-                                         0.0795774715459476679f, f->pc.ptr, np, s));
+        // S~: check potentials h K(x^u, points) q (= sum q / (4 pi |.|) in leaf units;
+        // double layer: h dG/dn = sum q n . d / (4 pi h |d|^3)), then q~ = Ws (.)
+        // into the leaf rows of qb3
+        KIFMM_CUDA_TRY(launch_leaf_check(f->hi.ptr, f->lo.ptr, nhi, f->leaf_start.ptr, B, f->usurf.ptr, n, a_surf,
+                                         (float)(f->dl ? 0.0795774715459476679 / h : 0.0795774715459476679),
+                                         f->pc.ptr, np, s));
         {
             const long sstride = (long)leaf_tiles * kTileRows * np;
             KIFMM_CUDA_TRY(launch_split_rows(f->pc.ptr, B, np, np, np, nullptr, 0, leaf_tiles, f->sp.ptr, sstride, 3, s));
@@ -488,9 +498,10 @@ int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s)
             KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_STORE, a, plan->num_sms, s));
         }
     }
-    KIFMM_CUDA_TRY(launch_leaf_eval(f->hi.ptr, f->lo.ptr, f->leaf_start.ptr, f->leaf_ijk.ptr, f->near_start.ptr,
-                                    f->near_idx.ptr, B, f->usurf.ptr, n, a_surf,
-                                    (float)(0.0795774715459476679 / h), f->pc.ptr, np, f->perm.ptr, out, parts, s));
+    KIFMM_CUDA_TRY(launch_leaf_eval(f->hi.ptr, f->lo.ptr, nhi, nlo, f->leaf_start.ptr, f->leaf_ijk.ptr, f->near_start.ptr,
+                                    f->near_idx.ptr, B, f->usurf.ptr, n, a_surf, (float)(0.0795774715459476679 / h),
+                                    (float)(0.0795774715459476679 / (h * h)), f->pc.ptr, np, f->perm.ptr, out, parts,
+                                    s));
     return KIFMM_OK;
 }
 
@@ -550,6 +561,10 @@ int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points
         set_error("point-source evaluation runs its passes on the tensor cores: use a BF16 / split / f16x3 precision");
         return KIFMM_ERR_UNSUPPORTED;
     }
+    if (plan->prm.kernel_id != KIFMM_KERNEL_LAPLACE) {
+        set_error("point-source evaluation is built for the Laplace kernel");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
     if (plan->n > 512) {
         set_error("point-source evaluation supports n <= 512 surface points (p <= 10)");
         return KIFMM_ERR_UNSUPPORTED;
@@ -598,6 +613,47 @@ int kifmm_fmm_evaluate(kifmm_fmm fmm, const float* q, float* potential, int part
     return evaluate(fmm, q, potential, parts, static_cast<cudaStream_t>(stream));
 }
 
+int kifmm_fmm_set_normals(kifmm_fmm fmm, const double* normals) {
+    if (!fmm) {
+        set_error("fmm is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (!normals) {
+        fmm->dl = false;
+        return KIFMM_OK;
+    }
+    const int64_t N = fmm->n_points;
+    for (int64_t i = 0; i < 3 * N; ++i)
+        if (!std::isfinite(normals[i])) {
+            set_error("non-finite normal at index " + std::to_string(i / 3));
+            return KIFMM_ERR_INVALID_ARG;
+        }
+    if (fmm->plan) {
+        int st = check_device(fmm->plan);
+        if (st != KIFMM_OK) return st;
+    }
+    try {
+        std::vector<float4> vh((size_t)N), vl((size_t)N);
+        for (int64_t s = 0; s < N; ++s) {
+            const double* v = normals + 3 * (int64_t)fmm->h_perm[s];
+            float w[3], r[3];
+            for (int t = 0; t < 3; ++t) {
+                w[t] = (float)v[t];
+                r[t] = (float)(v[t] - (double)w[t]);
+            }
+            vh[s] = make_float4(w[0], w[1], w[2], 0.f);
+            vl[s] = make_float4(r[0], r[1], r[2], 0.f);
+        }
+        KIFMM_CUDA_TRY(fmm->nhi.upload(vh.data(), vh.size()));
+        KIFMM_CUDA_TRY(fmm->nlo.upload(vl.data(), vl.size()));
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    fmm->dl = true;
+    return KIFMM_OK;
+}
+
 int kifmm_fmm_info(kifmm_fmm fmm, int* depth, int64_t* n_leaves, int64_t* n_boxes, int64_t* n_m2l_pairs,
                    int64_t* n_near_pairs) {
     if (!fmm) {
@@ -620,6 +676,10 @@ int kifmm_fmm_destroy(kifmm_fmm fmm) {
 }
 
 int kifmm_m2l_pass_ops_host(const kifmm_m2l_params* params, double rcond, int* kept, double* Ws, double* Mt) {
+    if (params && params->kernel_id != KIFMM_KERNEL_LAPLACE) {
+        set_error("the pass operators are built for the Laplace kernel");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
     Factors f;
     int st = compute_factors(*params, f);
     if (st != KIFMM_OK) return st;

@@ -42,21 +42,24 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_b
 
 // Point-source evaluation (kernels_fmm.cu).  Points in leaf order, leaf b
 // holding [leaf_start[b], leaf_start[b+1]), in leaf units s = (x - c_b) / h
-// split as hi (a multiple of 2^-12, w = density) + lo; usurf: the n points
+// split as hi (a multiple of 2^-20, w = density) + lo; usurf: the n points
 // of the [-1,1]^3 cube surface.
 // hi[i].w = q[perm[i]].
 cudaError_t launch_gather_density(const float* q, const int* perm, float4* hi, int n_points, cudaStream_t stream);
 // out[b][i] = scale * sum_{j in leaf b} q_j / |a u_i - s_j| (i < n <= 512),
-// out[b][n..ld) = 0.
-cudaError_t launch_leaf_check(const float4* hi, const float4* lo, const int* leaf_start, int n_leaves,
-                              const float4* usurf, int n, float a, float scale, float* out, int ld,
+// or, with the normals' hi words nhi (double layer), scale * sum_j q_j
+// nhi_j . (a u_i - s_j) / |a u_i - s_j|^3; out[b][n..ld) = 0.
+cudaError_t launch_leaf_check(const float4* hi, const float4* lo, const float4* nhi, const int* leaf_start,
+                              int n_leaves, const float4* usurf, int n, float a, float scale, float* out, int ld,
                               cudaStream_t stream);
-// out[perm[i]] = scale * ((L2T from e[b][0..n) on a u, parts & 2) + (near
-// field over near_idx[near_start[b]..near_start[b+1]), parts & 1)).
-cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const int* leaf_start, const int4* leaf_ijk,
-                             const int* near_start, const int* near_idx, int n_leaves, const float4* usurf, int n,
-                             float a, float scale, const float* e, int lde, const int* perm, float* out, int parts,
-                             cudaStream_t stream);
+// out[perm[i]] = scale * (L2T from e[b][0..n) on a u, parts & 2) + near field
+// over near_idx[near_start[b]..near_start[b+1]) (parts & 1): scale * sum q_j /
+// |d|, or, with the normals' two words nhi + nlo (double layer), scale_dl *
+// sum q_j n_j . d / |d|^3.
+cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const float4* nhi, const float4* nlo,
+                             const int* leaf_start, const int4* leaf_ijk, const int* near_start, const int* near_idx,
+                             int n_leaves, const float4* usurf, int n, float a, float scale, float scale_dl,
+                             const float* e, int lde, const int* perm, float* out, int parts, cudaStream_t stream);
 
 // Rows of A (FP32, m_rows x cols, ld lda) -> two FP16 pieces [2][m_rows][ldo]
 // (piece stride piece_stride) of sigma_r x with sigma_r the power of two that

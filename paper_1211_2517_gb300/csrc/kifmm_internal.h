@@ -28,8 +28,13 @@ int offset_index(int ox, int oy, int oz);
 std::vector<double> unit_surface(int p);
 
 // Entry (i, j) of the unit-level translation matrix K_o (Sec. 2.2 Eq. eq-m2l,
-// surfaces of Sec. 2.1): G(2 o + (1+d)(u_i - u_j)), G = 1/(4 pi |.|).
-void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>& u, double* K);
+// surfaces of Sec. 2.1): g(|2 o + (1+d)(u_i - u_j)|) with g(r) = exp(-kh r) /
+// (4 pi r); kh = 0 is the Laplace kernel, kh = kappa h the Yukawa kernel at
+// box half-width h (times h).
+void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>& u, double* K, double kh = 0.0);
+
+// kappa h of a plan's kernel (0 for the Laplace kernel).
+double kernel_kh(const kifmm_m2l_params& prm);
 
 // FP64 factors of the stage-1 compression (Sec. 3.1).
 struct Factors {

@@ -41,7 +41,7 @@ thread_local std::string g_last_error;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTieTol = 1e-13;          // equal singular values: within 1e-13 sigma_0
 constexpr unsigned kCacheMagic = 0x4b4d324cu;  // "KM2L"
-constexpr unsigned kCacheVersion = 1;
+constexpr unsigned kCacheVersion = 2;
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -96,7 +96,7 @@ std::vector<double> unit_surface(int p) {
     return u;
 }
 
-void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>& u, double* K) {
+void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>& u, double* K, double kh) {
     const int n = surface_count(p);
     const double s = 1.0 + d;
     for (int i = 0; i < n; ++i) {
@@ -104,9 +104,14 @@ void unit_m2l_matrix(int p, double d, const int o[3], const std::vector<double>&
                      xi2 = 2.0 * o[2] + s * u[3 * i + 2];
         for (int j = 0; j < n; ++j) {
             const double a = xi0 - s * u[3 * j], b = xi1 - s * u[3 * j + 1], c = xi2 - s * u[3 * j + 2];
-            K[(size_t)i * n + j] = 1.0 / (4.0 * kPi * std::sqrt(a * a + b * b + c * c));
+            const double r = std::sqrt(a * a + b * b + c * c);
+            K[(size_t)i * n + j] = (kh == 0.0 ? 1.0 : std::exp(-kh * r)) / (4.0 * kPi * r);
         }
     }
+}
+
+double kernel_kh(const kifmm_m2l_params& prm) {
+    return prm.kernel_id == KIFMM_KERNEL_YUKAWA ? prm.kappa * prm.box_halfwidth : 0.0;
 }
 
 int check_params(const kifmm_m2l_params* prm) {
@@ -114,9 +119,15 @@ int check_params(const kifmm_m2l_params* prm) {
         set_error("params is NULL");
         return KIFMM_ERR_INVALID_ARG;
     }
-    if (prm->kernel_id != KIFMM_KERNEL_LAPLACE) {
-        set_error("kernel_id " + std::to_string(prm->kernel_id) + " is not supported (only 0 = Laplace)");
+    if (prm->kernel_id != KIFMM_KERNEL_LAPLACE && prm->kernel_id != KIFMM_KERNEL_YUKAWA) {
+        set_error("kernel_id " + std::to_string(prm->kernel_id) + " is not supported (0 = Laplace, 1 = Yukawa)");
         return KIFMM_ERR_UNSUPPORTED;
+    }
+    if (prm->kernel_id == KIFMM_KERNEL_YUKAWA &&
+        !(prm->kappa > 0.0 && prm->box_halfwidth > 0.0 && std::isfinite(prm->kappa) &&
+          std::isfinite(prm->box_halfwidth) && prm->kappa * prm->box_halfwidth <= 64.0)) {
+        set_error("the Yukawa kernel needs kappa > 0, box_halfwidth > 0 and kappa * box_halfwidth <= 64");
+        return KIFMM_ERR_INVALID_ARG;
     }
     if (prm->p < 2 || prm->p > 12) {
         set_error("p must be in [2, 12], got " + std::to_string(prm->p));
@@ -234,7 +245,7 @@ void householder_merge(int n, double* R, int mb, double* B) {
 }
 
 // Triangular factor of K_fat^T (316 n x n).  Returns R, column-major n x n.
-std::vector<double> tsqr_kfat_t(int p, double d, const std::vector<double>& u, ThreadTeam& team) {
+std::vector<double> tsqr_kfat_t(int p, double d, double kh, const std::vector<double>& u, ThreadTeam& team) {
     const int n = surface_count(p);
     int offs[kOffsets][3];
     offsets316(offs);
@@ -244,7 +255,7 @@ std::vector<double> tsqr_kfat_t(int p, double d, const std::vector<double>& u, T
         std::vector<double> K((size_t)n * n), B((size_t)n * n);
         const int lo = (int)((long)kOffsets * tid / nthreads), hi = (int)((long)kOffsets * (tid + 1) / nthreads);
         for (int k = lo; k < hi; ++k) {
-            unit_m2l_matrix(p, d, offs[k], u, K.data());
+            unit_m2l_matrix(p, d, offs[k], u, K.data(), kh);
             // block of K_fat^T: rows j (source points), columns i; B(j,i) = K_o[i][j]
             // column-major B: column i contiguous over j -> B[i*n + j] = K[i*n + j]
             std::copy(K.begin(), K.end(), B.begin());
@@ -348,8 +359,8 @@ std::string cache_path(const kifmm_m2l_params& prm) {
     const char* dir = std::getenv("KIFMM_M2L_CACHE");
     if (!dir || !*dir) return std::string();
     char name[256];
-    std::snprintf(name, sizeof(name), "/kifmm_m2l_v%u_k%d_p%d_d%.17g_eps%.17g.bin", kCacheVersion, prm.kernel_id,
-                  prm.p, prm.d, prm.eps);
+    std::snprintf(name, sizeof(name), "/kifmm_m2l_v%u_k%d_p%d_d%.17g_eps%.17g_kh%.17g.bin", kCacheVersion,
+                  prm.kernel_id, prm.p, prm.d, prm.eps, kernel_kh(prm));
     return std::string(dir) + name;
 }
 
@@ -359,10 +370,11 @@ bool load_cache(const std::string& path, const kifmm_m2l_params& prm, Factors& f
     if (!fp) return false;
     unsigned hdr[2];
     int dims[4];
-    double pd[2];
+    double pd[3];
     bool ok = std::fread(hdr, sizeof(hdr), 1, fp) == 1 && hdr[0] == kCacheMagic && hdr[1] == kCacheVersion &&
               std::fread(dims, sizeof(dims), 1, fp) == 1 && std::fread(pd, sizeof(pd), 1, fp) == 1 &&
-              dims[0] == prm.kernel_id && dims[1] == prm.p && pd[0] == prm.d && pd[1] == prm.eps;
+              dims[0] == prm.kernel_id && dims[1] == prm.p && pd[0] == prm.d && pd[1] == prm.eps &&
+              pd[2] == kernel_kh(prm);
     if (ok) {
         f.p = dims[1];
         f.n = surface_count(f.p);
@@ -391,7 +403,7 @@ void store_cache(const std::string& path, const kifmm_m2l_params& prm, const Fac
     if (!fp) return;
     unsigned hdr[2] = {kCacheMagic, kCacheVersion};
     int dims[4] = {prm.kernel_id, prm.p, f.r, f.n};
-    double pd[2] = {prm.d, prm.eps};
+    double pd[3] = {prm.d, prm.eps, kernel_kh(prm)};
     bool ok = std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 && std::fwrite(dims, sizeof(dims), 1, fp) == 1 &&
               std::fwrite(pd, sizeof(pd), 1, fp) == 1 &&
               std::fwrite(f.sigma.data(), sizeof(double), f.n, fp) == (size_t)f.n &&
@@ -417,7 +429,7 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
     const std::vector<double> u = unit_surface(p);
     try {
         ThreadTeam team(team_size());
-        std::vector<double> R = tsqr_kfat_t(p, prm.d, u, team);
+        std::vector<double> R = tsqr_kfat_t(p, prm.d, kernel_kh(prm), u, team);
         // zero the strict lower triangle (Householder vectors are not stored in R)
         for (int c = 0; c < n; ++c)
             for (int i = c + 1; i < n; ++i) R[i + (size_t)c * n] = 0.0;
@@ -449,7 +461,7 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
         team.run([&](int tid, int nt) {
             std::vector<double> K((size_t)n * n), T((size_t)n * r);
             for (int k = tid; k < kOffsets; k += nt) {
-                unit_m2l_matrix(p, prm.d, offs[k], u, K.data());
+                unit_m2l_matrix(p, prm.d, offs[k], u, K.data(), kernel_kh(prm));
                 // T = K_o U~  (n x r)
                 std::fill(T.begin(), T.end(), 0.0);
                 for (int i = 0; i < n; ++i) {

@@ -36,9 +36,11 @@ def pass_ops_host(p: int, eps: float, d: float = 0.1, rcond: float = 1e-9):
 class PointFMM:
     """The octree of one point cloud bound to an ``M2LPlan`` (tensor-core
     precision).  ``points``: float64 [N, 3]; ``depth``: leaf level; the root
-    cube is (centre, r0) when given, else the padded bounding cube."""
+    cube is (centre, r0) when given, else the padded bounding cube.
+    ``normals`` (float64 [N, 3]) makes the sources dipoles: the double-layer
+    potential sum_j dG(x_i, x_j)/dn(x_j) q_j (Sec. 4, Eq. eq-doubles2m)."""
 
-    def __init__(self, plan: M2LPlan, points, depth: int, centre=None, r0: float | None = None):
+    def __init__(self, plan: M2LPlan, points, depth: int, centre=None, r0: float | None = None, normals=None):
         pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
         self.plan = plan
         self.n_points = pts.shape[0]
@@ -48,6 +50,21 @@ class PointFMM:
             c = np.ascontiguousarray(centre, dtype=np.float64).reshape(3)
         call("kifmm_fmm_create", plan._h, self.n_points, pts.ctypes.data,
              int(depth), None if c is None else c.ctypes.data, float(r0 or 0.0), ctypes.byref(self._h))
+        self.double_layer = False
+        if normals is not None:
+            self.set_normals(normals)
+
+    def set_normals(self, normals) -> None:
+        """Dipole sources with these normals (float64 [N, 3]); None: point charges."""
+        if normals is None:
+            call("kifmm_fmm_set_normals", self._h, None)
+            self.double_layer = False
+            return
+        nrm = np.ascontiguousarray(normals, dtype=np.float64).reshape(-1, 3)
+        if nrm.shape[0] != self.n_points:
+            raise ValueError(f"normals has {nrm.shape[0]} rows, expected {self.n_points}")
+        call("kifmm_fmm_set_normals", self._h, nrm.ctypes.data)
+        self.double_layer = True
 
     def close(self) -> None:
         if self._h:
@@ -99,6 +116,8 @@ def _autograd():
 
         @staticmethod
         def backward(ctx, g):
+            if ctx.fmm.double_layer:
+                raise NotImplementedError("the double-layer evaluation is not symmetric: its adjoint is not built")
             return ctx.fmm.evaluate(g.contiguous(), ctx.parts), None, None
 
     return FMMPotential

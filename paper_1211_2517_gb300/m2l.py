@@ -14,10 +14,15 @@ from . import _lib
 from ._lib import PREC, Params, call, lib
 
 
-def _params(p: int, eps: float, d: float, precision: str, kernel_id: int = 0) -> Params:
+KERNELS = {"laplace": 0, "yukawa": 1}
+
+
+def _params(p: int, eps: float, d: float, precision: str, kernel="laplace", kappa: float = 0.0,
+            box_halfwidth: float = 0.0) -> Params:
     if precision not in PREC:
         raise ValueError(f"precision must be one of {sorted(PREC)}")
-    return Params(kernel_id, int(p), float(eps), float(d), PREC[precision])
+    kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    return Params(kid, int(p), float(eps), float(d), PREC[precision], float(kappa), float(box_halfwidth))
 
 
 def surface_count(p: int) -> int:
@@ -25,12 +30,14 @@ def surface_count(p: int) -> int:
     return 6 * (p - 1) ** 2 + 2
 
 
-def factors_host(p: int, eps: float, d: float = 0.1):
+def factors_host(p: int, eps: float, d: float = 0.1, kernel="laplace", kappa: float = 0.0,
+                 box_halfwidth: float = 0.0):
     """Run the library's FP64 precompute on the host.
 
-    Returns (sigma [n], U [n, r], C [316, r, r]) as float64 arrays.
+    Returns (sigma [n], U [n, r], C [316, r, r]) as float64 arrays (for the
+    Yukawa kernel: of h K at box half-width h, see ``M2LPlan``).
     """
-    prm = _params(p, eps, d, "fp32")
+    prm = _params(p, eps, d, "fp32", kernel, kappa, box_halfwidth)
     n, r = ctypes.c_int(0), ctypes.c_int(0)
     call("kifmm_m2l_factors_host", ctypes.byref(prm), ctypes.byref(n), ctypes.byref(r), None, None, None)
     sigma = np.empty(n.value)
@@ -93,14 +100,18 @@ def _check_tensor(x, name, shape):
 class M2LPlan:
     """A precomputed compressed M2L operator plus registered octree levels.
 
-    ``precision``: "fp32" (CUDA cores), "bf16", "split3" or "split6"
-    (tcgen05 tensor cores; split6 keeps FP32-level accuracy).
+    ``precision``: "fp32" (CUDA cores), "bf16", "split3", "split6" or
+    "f16x3" (tcgen05 tensor cores; split6 and f16x3 keep FP32-level
+    accuracy).  ``kernel``: "laplace", or "yukawa" with ``kappa`` and the
+    half-width ``box_halfwidth`` of the one level the plan serves (the
+    kernel is not homogeneous: one plan per level, Sec. 3.1).
     """
 
-    def __init__(self, p: int, eps: float, d: float = 0.1, precision: str = "split6", kernel_id: int = 0):
+    def __init__(self, p: int, eps: float, d: float = 0.1, precision: str = "split6", kernel="laplace",
+                 kappa: float = 0.0, box_halfwidth: float = 0.0):
         self.p, self.eps, self.d, self.precision = int(p), float(eps), float(d), precision
         self._h = ctypes.c_void_p(None)
-        prm = _params(p, eps, d, precision, kernel_id)
+        prm = _params(p, eps, d, precision, kernel, kappa, box_halfwidth)
         call("kifmm_m2l_precompute", ctypes.byref(prm), ctypes.byref(self._h))
         r, rp, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         call("kifmm_m2l_plan_rank", self._h, ctypes.byref(r), ctypes.byref(rp), ctypes.byref(n))

@@ -180,6 +180,85 @@ def test_edge_cases(g):
     assert rel(got, near + far) < 1e-6
 
 
+@pytest.fixture(scope="module")
+def sphere_dl_case(sphere_case):
+    """The 65,536-point sphere with its outward normals as dipole sources
+    (the double layer of Sec. 4, Eq. eq-doubles2m): the oracle's near field
+    and compressed far field at p = 8."""
+    pts, q, tree, _, _ = sphere_case
+    nrm = pts / np.linalg.norm(pts, axis=1, keepdims=True)
+    f = om.svd_factors(8, D, 1e-7)
+    ops = ofmm.pass_operators(f, 8, D)
+    near = ofmm.near_field(tree, pts, q, normals=nrm)
+    far = ofmm.fmm_compressed_far(tree, pts, f, ops, 8, D, q, normals=nrm)
+    return pts, q, nrm, near, far
+
+
+@pytest.mark.parametrize("precision", ["split6", "f16x3"])
+def test_double_layer_matches_oracle(g, sphere_case, sphere_dl_case, precision):
+    """Near field (n . d by the compensated dot product on two-word normals)
+    within 1e-6 of the oracle.  Far field: dipole check potentials put most
+    of each q~ and e_leaf row's norm into modes that the far field does not
+    see, so the FP32 accumulation of the S~ and T~ GEMMs (|Ws| entries up to
+    3e6 from the 1e-9 pseudo-inverse) reaches the far field amplified: noise
+    of 1e-7 of the row norm there gave 3.3e-6 (q~) and 1.1e-5 (e_leaf) of
+    the far field in an FP64 emulation on 8000 sphere points (point charges:
+    2e-8 and 1.3e-7).  A larger cutoff trades this for method error (1e-7:
+    1.5e-6 and 2.9e-6 but 1.4e-5 against the direct sum), so the operators
+    stay and the bounds are far 4e-5 of its own norm, total 2e-5 against the
+    oracle and 5e-5 against the direct sum (the method's own FP64 error at
+    p = 8: 6.3e-6 on 8000 sphere points)."""
+    pts, q, nrm, near, far = sphere_dl_case
+    plan = g.M2LPlan(8, 1e-7, D, precision)
+    tree = g.PointFMM(plan, pts, 5, normals=nrm)
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    got = {k: tree.evaluate(qd, k).cpu().numpy().astype(np.float64) for k in (1, 2, 3)}
+    e_near, e_far, e_all = rel(got[1], near), rel(got[2], far), rel(got[3], near + far)
+    targets = np.random.default_rng(6).choice(pts.shape[0], 400, replace=False)
+    e_direct = rel(got[3][targets], ofmm.direct_sum(pts, q, targets, normals=nrm))
+    print(f"sphere65k double layer {precision}: near {e_near:.3e} far {e_far:.3e} total {e_all:.3e} "
+          f"direct {e_direct:.3e}")
+    assert e_near < 1e-6 and e_far < 4e-5 and e_all < 2e-5 and e_direct < 5e-5
+    # back to point charges on the same tree
+    tree.set_normals(None)
+    single = tree.evaluate(qd).cpu().numpy().astype(np.float64)
+    _, _, _, sl_near, sl_far = sphere_case
+    assert rel(single, sl_near + sl_far) < 1e-6
+    # the double-layer operator is not symmetric: no gradient through it
+    tree.set_normals(nrm)
+    qt = qd.clone().requires_grad_(True)
+    with pytest.raises(NotImplementedError):
+        g.fmm_potential(tree, qt).sum().backward()
+
+
+def test_double_layer_edge_cases(g):
+    plan = g.M2LPlan(6, 1e-7, D, "split6")
+    # two dipoles in one leaf: q_j n_j . (x_i - x_j) / (4 pi |x_i - x_j|^3)
+    pts = np.array([[0.1, 0.1, 0.1], [0.15, 0.1, 0.1]])
+    nrm = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    tree = g.PointFMM(plan, pts, 3, centre=np.array([0.5, 0.5, 0.5]), r0=0.5, normals=nrm)
+    got = tree.evaluate(torch.tensor([1.0, -2.0], dtype=torch.float32, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(got, [2.0 / (0.01 * np.pi), 1.0 / (0.01 * np.pi)], rtol=2e-6)
+    # random normals in the unit cube, depth 2 (no L2L), against the oracle
+    pts = synth.points_uniform_cube(3000, 31)
+    nrm = np.random.default_rng(32).standard_normal((3000, 3))
+    q = synth.densities_uniform(3000, 33)
+    otree = synth.build_tree(pts, 2, centre=np.array([0.5, 0.5, 0.5]), r0=0.5)
+    f = om.svd_factors(6, D, 1e-7)
+    want = ofmm.fmm_potential(otree, pts, q, 6, D, f=f, normals=nrm)
+    tree = g.PointFMM(plan, pts, 2, centre=np.array([0.5, 0.5, 0.5]), r0=0.5, normals=nrm)
+    got = tree.evaluate(torch.tensor(q, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel(got, want) < 2e-5
+    from paper_1211_2517_gb300 import KifmmError
+
+    bad = nrm.copy()
+    bad[5, 2] = np.inf
+    with pytest.raises(KifmmError, match="INVALID_ARG"):
+        tree.set_normals(bad)
+    with pytest.raises(ValueError):
+        tree.set_normals(nrm[:10])
+
+
 def test_argument_errors(g):
     from paper_1211_2517_gb300 import KifmmError
 

@@ -725,3 +725,55 @@ def test_batch64_full_config(g, oracle_factors):
         assert err <= 1e-6, err
     for plan in plans.values():
         plan.close()
+
+
+_YUKAWA = {}
+
+
+def _yukawa_factors(kappa, h):
+    if (kappa, h) not in _YUKAWA:
+        _YUKAWA[(kappa, h)] = om.svd_factors(8, 0.1, 1e-7, kappa=kappa, h=h)
+    return _YUKAWA[(kappa, h)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split6", "f16x3"])
+def test_yukawa_per_level_plans(g, sphere_small, precision):
+    """The Yukawa kernel exp(-kappa r) / (4 pi r) is not homogeneous, so the
+    translation matrices of every level are compressed separately (Sec. 3.1's
+    O(L) case): one plan per level, formed at its box half-width.  Forward
+    and adjoint against the oracle's per-level factors, the FP32 dense
+    baseline against the oracle's dense Yukawa M2L, and the level check."""
+    from paper_1211_2517_gb300 import KifmmError
+
+    tree, qs = sphere_small
+    kappa = 3.0
+    rng = np.random.default_rng(77)
+    for l in (2, 3, 4):
+        h = tree.r0 / (1 << l)
+        f = _yukawa_factors(kappa, h)
+        plan = g.M2LPlan(8, 1e-7, 0.1, precision, "yukawa", kappa, h)
+        assert plan.r == f.r
+        plan.set_level(l, tree.levels[l], tree.r0)
+        ref = om.m2l_svd(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64))
+        out = plan.apply(torch.from_numpy(qs[l]).cuda(), l)
+        y = rng.standard_normal(qs[l].shape).astype(np.float32)
+        aty = plan.apply_adjoint(torch.from_numpy(y).cuda(), l)
+        plan.sync()
+        ref_adj = om.m2l_svd_adjoint(tree.levels[l], l, tree.r0, f, y.astype(np.float64))
+        err, err_adj = rel(out.cpu().numpy(), ref), rel(aty.cpu().numpy(), ref_adj)
+        print(f"yukawa kappa={kappa} level {l} (kappa h = {kappa * h:.3f}, r = {f.r}) {precision}: "
+              f"forward {err:.3e} adjoint {err_adj:.3e}")
+        assert err <= TOL[precision] and err_adj <= TOL[precision], (err, err_adj)
+        if precision == "fp32" and l == 2:
+            dense = plan.apply_dense(torch.from_numpy(qs[l]).cuda(), l)
+            plan.sync()
+            ref_d = om.m2l_dense(tree.levels[l], l, tree.r0, 8, 0.1, qs[l].astype(np.float64), centre=tree.centre,
+                                 kappa=kappa)
+            assert rel(dense.cpu().numpy(), ref_d) <= 1e-6
+        other = 3 if l != 3 else 4
+        with pytest.raises(KifmmError, match="INVALID_ARG"):
+            plan.set_level(other, tree.levels[other], tree.r0)
+        if l == 2 and precision != "fp32":
+            with pytest.raises(KifmmError, match="UNSUPPORTED"):
+                g.PointFMM(plan, synth.points_uniform_cube(100, 1), 3)
+        plan.close()

@@ -46,7 +46,10 @@ def test_param_validation(native):
     L = native.lib()
     n, r = ctypes.c_int(), ctypes.c_int()
     bad = [
-        (Params(1, 6, 1e-7, 0.1, 0), -2),   # unsupported kernel
+        (Params(2, 6, 1e-7, 0.1, 0), -2),   # unsupported kernel
+        (Params(1, 6, 1e-7, 0.1, 0, 0.0, 0.5), -1),    # Yukawa without kappa
+        (Params(1, 6, 1e-7, 0.1, 0, 2.0, 0.0), -1),    # Yukawa without box half-width
+        (Params(1, 6, 1e-7, 0.1, 0, 200.0, 1.0), -1),  # kappa h > 64
         (Params(0, 1, 1e-7, 0.1, 0), -1),   # p too small
         (Params(0, 13, 1e-7, 0.1, 0), -1),  # p too large
         (Params(0, 6, 1e-13, 0.1, 0), -1),  # eps below 1e-12
@@ -89,6 +92,23 @@ def test_factors_match_oracle_through_products(native, oracle_factors, p, eps):
     tab = geo.offset_index_table()
     for k in (0, 17, 158, 315):
         np.testing.assert_allclose(C[k].T, C[tab[tuple(-offs[k])]], rtol=0, atol=1e-12 * np.abs(C).max())
+
+
+def test_yukawa_factors_match_oracle(native):
+    # the library compresses its unit operator h K_h (K_h the Yukawa
+    # matrices of boxes of half-width h, Sec. 3.1's per-level case): the
+    # oracle's per-level factors with singular values and cores times h
+    kappa, h = 3.0, 0.125
+    sigma, U, C = native.factors_host(6, 1e-5, 0.1, "yukawa", kappa, h)
+    f = om.svd_factors(6, 0.1, 1e-5, kappa=kappa, h=h)
+    assert U.shape[1] == f.r
+    np.testing.assert_allclose(sigma, h * f.sigma, rtol=0, atol=1e-12 * h * f.sigma[0])
+    kmax = np.abs(f.K).max()
+    for k in range(0, 316, 7):
+        assert np.abs(U @ C[k] @ U.T - h * (f.U @ f.C[k] @ f.R.T)).max() < 1e-11 * h * kmax, k
+    # a different kappa h is a different operator
+    _, U2, C2 = native.factors_host(6, 1e-5, 0.1, "yukawa", kappa, 2 * h)
+    assert U2.shape[1] != U.shape[1] or np.abs(U2 @ C2[0] @ U2.T - U @ C[0] @ U.T).max() > 1e-3 * np.abs(C[0]).max()
 
 
 def test_factors_full_rank_and_truncation_rule(native):

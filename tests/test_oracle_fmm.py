@@ -178,3 +178,112 @@ def test_compressed_fmm_operator_is_symmetric(cube_case):
     # (two separately computed pseudo-inverses: equal up to their noise)
     np.testing.assert_allclose(fmm.l2l_matrix(6, D, 1.0, 3), fmm.m2m_matrix(6, D, 1.0, 3).T, rtol=0,
                                atol=1e-7 * np.abs(fmm.m2m_matrix(6, D, 1.0, 3)).max())
+
+
+# ---------------------------------------------------------------------------
+# double layer (Sec. 4, Eq. eq-doubles2m): dG/dn(y) in S2T and in S2M's
+# first step
+# ---------------------------------------------------------------------------
+def _sphere_quadrature(nt, nphi):
+    """Points, outward normals and weights of a product rule on the unit
+    sphere: Gauss-Legendre in cos(theta), trapezoid in phi (spectrally
+    accurate for integrands analytic on the sphere)."""
+    t, wt = np.polynomial.legendre.leggauss(nt)
+    phi = 2.0 * np.pi * np.arange(nphi) / nphi
+    st = np.sqrt(1.0 - t * t)
+    y = np.stack([np.outer(st, np.cos(phi)), np.outer(st, np.sin(phi)), np.outer(t, np.ones(nphi))], -1).reshape(-1, 3)
+    w = np.outer(wt, np.full(nphi, 2.0 * np.pi / nphi)).reshape(-1)
+    return y, y.copy(), w
+
+
+def test_double_layer_kernel_gauss_law():
+    # the double-layer potential of unit density on a closed surface is -1
+    # inside and 0 outside (Gauss); the rule integrates it to rounding
+    y, n, w = _sphere_quadrature(32, 64)
+    assert abs(w.sum() - 4.0 * np.pi) < 1e-12
+    rng = np.random.default_rng(3)
+    inside = rng.uniform(-1.0, 1.0, size=(20, 3))
+    inside *= 0.5 * rng.uniform(0.0, 1.0, size=(20, 1)) / np.linalg.norm(inside, axis=1, keepdims=True)
+    outside = rng.standard_normal((20, 3))
+    outside *= rng.uniform(2.5, 6.0, size=(20, 1)) / np.linalg.norm(outside, axis=1, keepdims=True)
+    np.testing.assert_allclose(geo.laplace_double_layer_kernel(inside, y, n) @ w, -1.0, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(geo.laplace_double_layer_kernel(outside, y, n) @ w, 0.0, rtol=0, atol=1e-11)
+    # and it is the normal derivative of G at the source: finite differences
+    x, y0, n0 = np.array([[0.3, -0.2, 0.9]]), np.array([[0.1, 0.4, -0.2]]), np.array([[0.6, 0.0, 0.8]])
+    hh = 1e-5
+    fd = (geo.laplace_kernel(x, y0 + hh * n0) - geo.laplace_kernel(x, y0 - hh * n0)) / (2 * hh)
+    np.testing.assert_allclose(geo.laplace_double_layer_kernel(x, y0, n0), fd, rtol=1e-9)
+
+
+def test_double_layer_direct_sum_closed_form():
+    # dipoles at (0,0,0), (1,0,0), (0,2,0) with normals x, (0.6,0.8,0), z and
+    # densities 1, 2, 3: p_i = sum_j q_j n_j.(x_i - x_j) / (4 pi |x_i - x_j|^3)
+    pts = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    nrm = np.array([[1.0, 0.0, 0.0], [0.6, 0.8, 0.0], [0.0, 0.0, 1.0]])
+    q = np.array([1.0, 2.0, 3.0])
+    want = np.array([-1.2 / (4.0 * np.pi), 1.0 / (4.0 * np.pi), 1.0 / (10.0 * np.sqrt(5.0) * np.pi)])
+    np.testing.assert_allclose(fmm.direct_sum(pts, q, normals=nrm), want, rtol=1e-14, atol=1e-17)
+
+
+def test_double_layer_near_field_bruteforce():
+    pts = synth.points_sphere(600, 5)
+    nrm = pts / np.linalg.norm(pts, axis=1, keepdims=True)
+    q = synth.densities_normal(600, 6)
+    depth = 3
+    tree = synth.build_tree(pts, depth)
+    lo = tree.centre - tree.r0
+    ijk = np.clip(np.floor((pts - lo) / (2.0 * tree.r0) * (1 << depth)).astype(np.int64), 0, (1 << depth) - 1)
+    want = np.zeros(600)
+    for i in range(600):
+        for j in range(600):
+            if i != j and np.max(np.abs(ijk[i] - ijk[j])) <= 1:
+                dx = pts[i] - pts[j]
+                want[i] += q[j] * (nrm[j] @ dx) / (4.0 * np.pi * np.linalg.norm(dx) ** 3)
+    np.testing.assert_allclose(fmm.near_field(tree, pts, q, normals=nrm), want, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("c", [0, 3])
+def test_double_layer_s2m_reproduces_far_potential(c):
+    # dipoles inside child c of a unit parent: single-layer equivalent
+    # densities solved from their double-layer check potentials
+    # (Eq. eq-doubles2m) reproduce their potential beyond the far-field
+    # boundary
+    p, hc = 6, 0.5
+    centre = np.array([(c >> 2) & 1, (c >> 1) & 1, c & 1], dtype=np.float64) - 0.5
+    rng = np.random.default_rng(40 + c)
+    src = centre + rng.uniform(-hc, hc, size=(30, 3))
+    nrm = rng.standard_normal((30, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    q = rng.standard_normal(30)
+    xu = geo.surface_points(p, centre, (3.0 - 2.0 * D) * hc)
+    q_child = upward.check_to_equivalent(p, D, hc, fmm.FMM_RCOND) @ (geo.laplace_double_layer_kernel(xu, src, nrm) @ q)
+    q_parent = fmm.m2m_matrix(p, D, 1.0, c) @ q_child
+    far = _shell_points(40, 60 + c, 3.0, 5.0)
+    got = geo.laplace_kernel(far, geo.surface_points(p, np.zeros(3), 1.0 + D)) @ q_parent
+    want = geo.laplace_double_layer_kernel(far, src, nrm) @ q
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-4
+
+
+@pytest.fixture(scope="module")
+def dipole_case():
+    """1500 points on the unit sphere with their outward normals, depth 3,
+    and the direct double-layer sum at every point."""
+    pts = synth.points_sphere(1500, 8)
+    nrm = pts / np.linalg.norm(pts, axis=1, keepdims=True)
+    q = synth.densities_normal(1500, 9)
+    tree = synth.build_tree(pts, 3)
+    return tree, pts, nrm, q, fmm.direct_sum(pts, q, normals=nrm)
+
+
+def test_double_layer_fmm_converges_to_direct_sum(dipole_case):
+    tree, pts, nrm, q, exact = dipole_case
+    near = fmm.near_field(tree, pts, q, normals=nrm)
+    errs = {}
+    for p in (4, 6):
+        pot = near + fmm.fmm_uncompressed_far(tree, pts, p, D, q, normals=nrm)
+        errs[p] = np.linalg.norm(pot - exact) / np.linalg.norm(exact)
+    f = m2l.svd_factors(8, D, 1e-7)
+    pot8 = fmm.fmm_potential(tree, pts, q, 8, D, f=f, normals=nrm)
+    errs[8] = np.linalg.norm(pot8 - exact) / np.linalg.norm(exact)
+    assert errs[4] < 5e-3 and errs[6] < 1e-4 and errs[8] < 4e-6, errs
+    assert errs[6] < errs[4] / 5.0 and errs[8] < errs[6] / 5.0, errs
