@@ -347,7 +347,9 @@ def run_ours(args, rank, world, local_rank):
                    6: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks drained)",
                    9: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 2 K-chunks, 2 per MMA step)",
                    10: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 2 per MMA step)",
-                   11: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 3 per MMA step)"}.get(
+                   11: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 3 per MMA step)",
+                   12: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 3 per MMA step, "
+                       "rows reduced without a transpose)"}.get(
                        (tune or {}).get("variant"), "umma_kernel<A_GATHER,E_RED> (offset-grouped core)"),
         "core_dtype": {"f16x3": "fp16 pieces x fp16 pieces, fp32 accumulate (3 products)",
                        "split6": "bf16 pieces, fp32 accumulate (6 products)"}.get(args.precision, args.precision),

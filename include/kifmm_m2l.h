@@ -320,6 +320,9 @@ int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
  * partial sums of two / one K-chunks drained into registers while the next
  * partial's MMAs run; 4 / 5: as 2 / 3 with the output rows reduced into p~
  * by TMA bulk reductions; 6 (f16x3 only): partials of three K-chunks;
+ * 9 / 10 / 11 (f16x3; 9 also split6): as 2 / 6 / 6 with two / two / three
+ * K-chunks of a partial issued per MMA step; 12 (f16x3 only): as 11 with
+ * every epilogue lane reducing its own row into p~ without a transpose;
  * other precisions: 0), core_ms = the core launch's
  * mean time (ms) under that choice, from_cache = 1 if read back from the
  * cache file. */

@@ -388,6 +388,7 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     a.core_drain = plan->variant_drain();
     a.red_bulk = plan->variant_bulk();
     a.mma_pair = plan->variant_pair();
+    a.direct_rows = plan->variant_direct();
     a.s2_on = plan->s2_on;
     a.s2_V = plan->s2V.ptr;
     a.s2_U = plan->s2U.ptr;

@@ -194,6 +194,7 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.core_drain = plan->variant_drain();
         a.red_bulk = plan->variant_bulk();
         a.mma_pair = plan->variant_pair();
+        a.direct_rows = plan->variant_direct();
         a.s2_on = plan->s2_on;
         a.s2_V = plan->s2V.ptr;
         a.s2_U = plan->s2U.ptr;

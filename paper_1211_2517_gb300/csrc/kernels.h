@@ -162,6 +162,7 @@ struct UmmaArgs {
     const float* row_scale;   // E_RED: when set, output row r is scaled by row_scale[row_src[r]]
     int red_bulk;             // E_RED, drained partials: reduce rows into D with TMA bulk reductions
     int mma_pair;             // drained partials: K-chunks of a partial the MMA thread takes per step (<= 1: one)
+    int direct_rows;          // E_RED, drained partials: every lane reduces its own row into D (no transpose)
     int* error_flag;          // device int, set when a bounded wait times out
 };
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& args, int num_sms, cudaStream_t stream);

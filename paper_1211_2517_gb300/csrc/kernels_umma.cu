@@ -760,6 +760,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ++pcount;
             }
             if (!ok) break;
+            if (EMODE == E_RED && args.direct_rows) {
+                // every lane reduces its own row segment: 16-byte vector
+                // atomics at D[orow][n0 + c ..], no shared-memory transpose
+                if (orow >= 0) {
+                    const float f = oscale * rsc;
+                    float* drow = args.D + orow * args.ldd + n0;
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const int c = (c_beg + jj) * 32;
+                        if (c_beg + jj < c_end) {
+                            const int ncols = c + 32 <= nthis ? 32 : 16;
+#pragma unroll
+                            for (int qq = 0; qq < 8; ++qq)
+                                if (4 * qq < ncols)
+                                    red_add_v4(drow + c + 4 * qq, __float_as_uint(f * sums[jj * 32 + 4 * qq]),
+                                               __float_as_uint(f * sums[jj * 32 + 4 * qq + 1]),
+                                               __float_as_uint(f * sums[jj * 32 + 4 * qq + 2]),
+                                               __float_as_uint(f * sums[jj * 32 + 4 * qq + 3]));
+                        }
+                    }
+                }
+                continue;
+            }
             if (EMODE == E_RED && args.red_bulk) {
                 // every lane hands its own row segment to the TMA unit: one bulk
                 // reduction of 32 (or 16) FP32 values per chunk, staged in the

@@ -130,12 +130,15 @@ struct kifmm_m2l_plan_s {
         switch (tune_variant) {
             case 2: case 4: return 2;
             case 3: case 5: return 1;
-            case 6: case 10: case 11: return 3;
+            case 6: case 10: case 11: case 12: return 3;
             case 9: return 2;
             default: return 0;
         }
     }
-    int variant_pair() const { return tune_variant == 11 ? 3 : (tune_variant == 9 || tune_variant == 10) ? 2 : 1; }
+    int variant_pair() const {
+        return (tune_variant == 11 || tune_variant == 12) ? 3 : (tune_variant == 9 || tune_variant == 10) ? 2 : 1;
+    }
+    int variant_direct() const { return tune_variant == 12 ? 1 : 0; }
     int variant_bulk() const { return (tune_variant == 4 || tune_variant == 5) ? 1 : 0; }
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each (Cb: 2 FP16 pieces of tau K~ for F16X3)

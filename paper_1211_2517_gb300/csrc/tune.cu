@@ -21,7 +21,9 @@
 //                with the rows reduced into p~ by TMA bulk reductions instead
 //                of vector atomics; 6 (f16x3 only) partials of three K-chunks;
 //                9 and 10 (f16x3 only) as 2 and 6 with two K-chunks of a
-//                partial issued per MMA step, 11 (f16x3 only) with all three.
+//                partial issued per MMA step, 11 (f16x3 only) with all three,
+//                12 (f16x3 only) as 11 with every epilogue lane reducing its
+//                own row segment into p~ (no shared-memory transpose).
 //                The FP16 split (f16x3) has no variant 1.
 // Each candidate is timed with CUDA events around the core launch of
 // kifmm_m2l_apply_levels.  With $KIFMM_M2L_AUTOTUNE_CACHE naming a file,
@@ -143,7 +145,7 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
         int c = 0, g = 0, rs = 0;
         double t = 0;
         if (it != entries.end() && parse_entry(it->second, &c, &g, &rs, &t) && c >= 16 && c % 16 == 0 &&
-            c <= 512 && (g == 0 || g == 1) && rs >= 0 && rs <= 11) {
+            c <= 512 && (g == 0 || g == 1) && rs >= 0 && rs <= 12) {
             plan->tune_chunk = c == core_chunk_default(plan) ? 0 : c;
             plan->tune_contig = g;
             plan->tune_variant = rs;
@@ -172,6 +174,7 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
                 cands.push_back({c0, g, 6});  // three-K-chunk partials: short enough chains for 3 products
                 cands.push_back({c0, g, 10});
                 cands.push_back({c0, g, 11});
+                cands.push_back({c0, g, 12});
             }
         }
         cands.push_back({c0, g, 0});
