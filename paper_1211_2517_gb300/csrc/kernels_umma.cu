@@ -2020,7 +2020,10 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     L.drain = gather && a.core_drain > 0 && (a.n_products == 6 || a.n_products == 3) && a.n_chunk <= 192
                   ? std::min(a.core_drain, 3)
                   : 0;
-    uint32_t trans_bytes = (L.drain ? 2 : 1) * kEpiWarps * 32 * kTransStride * 4;
+    // the drained core that reduces rows straight from registers (direct_rows)
+    // needs no transpose buffers: their room goes to the ring
+    const bool no_trans = L.drain && gather && emode == E_RED && a.direct_rows;
+    uint32_t trans_bytes = no_trans ? 0u : (L.drain ? 2u : 1u) * kEpiWarps * 32 * kTransStride * 4;
     int avail = max_smem - 2048 - (int)trans_bytes;
     L.stages = avail / (int)L.stage_bytes;
     if (L.drain && L.stages < 2) {
