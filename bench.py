@@ -464,12 +464,23 @@ def run_ours(args, rank, world, local_rank):
         far_ms = timed(lambda: ftree.evaluate(qd, 2, out=pot), k_f)
         info = ftree.info()
         npts = wl.points.shape[0]
+        # the same points as dipoles with their outward normals (double layer, Sec. 4)
+        ftree.set_normals(wl.points / np.linalg.norm(wl.points, axis=1, keepdims=True))
+        for _ in range(3):
+            ftree.evaluate(qd, 3, out=pot)
+        dl_ms = timed(lambda: ftree.evaluate(qd, 3, out=pot), k_f)
+        dl_near_ms = timed(lambda: ftree.evaluate(qd, 1, out=pot), k_f)
+        ftree.set_normals(None)
         fmm = {"value": npts * k_f / (f_ms / 1e3), "unit": "points/s (potential at every point from all others)",
                "ms_per_evaluate": f_ms / k_f, "near_ms": near_ms / k_f, "far_ms": far_ms / k_f,
                "m2l_precision": args.precision,
                "points": npts, "depth": info["depth"], "leaves": info["leaves"], "m2l_pairs": info["m2l_pairs"],
                "near_pairs": info["near_pairs"],
                "near_pairs_per_s": info["near_pairs"] * k_f / (near_ms / 1e3),
+               "double_layer": {"value": npts * k_f / (dl_ms / 1e3), "unit": "points/s",
+                                "ms_per_evaluate": dl_ms / k_f, "near_ms": dl_near_ms / k_f,
+                                "sources": "the same points as dipoles, outward unit normals",
+                                "parity": "tests/test_gpu_fmm.py::test_double_layer_matches_oracle"},
                "parity": "tests/test_gpu_fmm.py: within 1e-6 relative L2 of the FP64 oracle's compressed FMM and "
                          "of the direct sum"}
         ftree.close()

@@ -418,7 +418,8 @@ int kifmm_fmm_evaluate(kifmm_fmm fmm, const float* q, float* potential, int part
  * (the evaluation is not symmetric in this mode).
  *   normals  HOST float64 [n_points][3] in the caller's point order (n_j as
  *            given: unit normals for a double-layer integral); copied to the
- *            device in leaf order.  NULL returns the tree to single layer.
+ *            device in leaf order (synchronous: no evaluate of this tree may
+ *            be in flight).  NULL returns the tree to single layer.
  * Errors: KIFMM_ERR_INVALID_ARG (NULL fmm, non-finite entries),
  * KIFMM_ERR_OOM, KIFMM_ERR_CUDA. */
 int kifmm_fmm_set_normals(kifmm_fmm fmm, const double* normals);
