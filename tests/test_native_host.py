@@ -63,6 +63,9 @@ def test_param_validation(native):
         assert L.kifmm_m2l_last_error()
     assert L.kifmm_m2l_factors_host(None, None, None, None, None, None) == -1
     assert L.kifmm_m2l_destroy(None) == 0
+    assert L.kifmm_fmm_set_normals(None, None) == -1  # no tree
+    yuk = Params(1, 6, 1e-7, 0.1, 0, 2.0, 0.25)
+    assert L.kifmm_m2l_pass_ops_host(ctypes.byref(yuk), 1e-9, None, None, None) == -2  # Laplace passes only
     cnt = ctypes.c_int64()
     assert L.kifmm_m2l_pairs_host(2, 1, np.array([[4, 0, 0]], np.int32).ctypes.data, ctypes.byref(cnt),
                                   None, None, None) == -1  # coordinate out of range
