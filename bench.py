@@ -485,6 +485,42 @@ def run_ours(args, rank, world, local_rank):
                          "of the direct sum"}
         ftree.close()
 
+    # ---- a non-homogeneous kernel (Sec. 3.1's O(L) precompute): the Yukawa
+    # kernel exp(-kappa r) / (4 pi r), one plan per level, the same levels and
+    # densities as the headline --------------------------------------------
+    yukawa = None
+    if args.precision != "fp32" and not args.no_yukawa:
+        try:
+            kappa = 3.0
+            t0 = time.time()
+            yplans = {}
+            for l in LEVELS:
+                yp = M2LPlan(wl.p, wl.eps, wl.d, args.precision, "yukawa", kappa, tree.r0 / (1 << l))
+                yp.set_level(l, tree.levels[l], tree.r0)
+                yplans[l] = yp
+            setup_s = time.time() - t0
+            if not args.no_autotune:
+                for l, yp in yplans.items():
+                    yp.autotune(q[l], l, l, reps=2, out=out[l])
+
+            def ystep():
+                for l, yp in yplans.items():
+                    yp.apply(q[l], l, out=out[l])
+
+            for _ in range(3):
+                ystep()
+            torch.cuda.synchronize()
+            k_y = min(args.steps, 20)
+            y_ms = timed(ystep, k_y)
+            yukawa = {"value": total_pairs * k_y / (y_ms / 1e3), "unit": UNIT, "ms_per_step": y_ms / k_y,
+                      "kappa": kappa, "ranks_by_level": {str(l): yp.r for l, yp in yplans.items()},
+                      "precompute_s_all_levels": setup_s, "precision": args.precision,
+                      "parity": "tests/test_gpu_m2l.py::test_yukawa_per_level_plans"}
+            for yp in yplans.values():
+                yp.close()
+        except Exception as exc:  # a secondary leg: reported, the headline line still prints
+            yukawa = {"error": f"{type(exc).__name__}: {exc}"}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -501,6 +537,7 @@ def run_ours(args, rank, world, local_rank):
         "split6": split6,
         "stage2": stage2,
         "fmm": fmm,
+        "yukawa_per_level": yukawa,
         "parity": "tests/test_gpu_m2l.py: f16x3, split6 and fp32 within 1e-6 relative L2 of the FP64 oracle",
     }
 
@@ -610,6 +647,7 @@ def main():
     ap.add_argument("--precision", choices=("f16x3", "split6", "split3", "bf16", "fp32"), default="f16x3")
     ap.add_argument("--no-autotune", action="store_true", help="use the plan's default core variant")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle leg")
+    ap.add_argument("--no-yukawa", action="store_true", help="skip the per-level Yukawa leg")
     ap.add_argument("--workload", choices=("sphere2m_p8", "batch64"), default="sphere2m_p8",
                     help="sphere2m_p8: the headline configuration; batch64: the 64-instance mixed batch")
     args = ap.parse_args()
