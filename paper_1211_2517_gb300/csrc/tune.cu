@@ -61,7 +61,13 @@ std::string tune_key(kifmm_m2l_plan plan, const MultiState* ms, int nrhs, int lo
     std::snprintf(buf, sizeof(buf), "p=%d eps=%.6e d=%.6g prec=%d sm=%d%d sms=%d levels=%d-%d nrhs=%d boxes=%lld pairs=%lld",
                   plan->prm.p, plan->prm.eps, plan->prm.d, plan->prm.precision, prop.major, prop.minor, plan->num_sms,
                   lo, hi, nrhs, (long long)ms->total_boxes, (long long)pairs);
-    return buf;
+    std::string key = buf;
+    if (plan->prm.kernel_id != KIFMM_KERNEL_LAPLACE) {
+        // another operator (and rank) on the same boxes: its own entry
+        std::snprintf(buf, sizeof(buf), " kernel=%d kh=%.17g", plan->prm.kernel_id, kernel_kh(plan->prm));
+        key += buf;
+    }
+    return key;
 }
 
 // The cache file holds one entry per line:
