@@ -454,13 +454,21 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
             for (int i = 0; i < n; ++i) f.U[(size_t)i * r + j] = sgn * vj[i];
         }
 
-        // cores K~_o = U~^T K_o U~
+        // cores K~_o = U~^T K_o U~.  K_o^T = K_{-o} (G radial, one point
+        // pattern for both surfaces), so K~_{-o} = K~_o^T: one core of every
+        // (o, -o) pair is formed, plus every 40th partner as a check of the
+        // identity the transposes rely on
         int offs[kOffsets][3];
         offsets316(offs);
+        std::vector<int> partner(kOffsets), formed;
+        for (int k = 0; k < kOffsets; ++k) partner[k] = offset_index(-offs[k][0], -offs[k][1], -offs[k][2]);
+        for (int k = 0; k < kOffsets; ++k)
+            if (k < partner[k] || k % 40 == 0) formed.push_back(k);
         f.C.assign((size_t)kOffsets * r * r, 0.0);
         team.run([&](int tid, int nt) {
             std::vector<double> K((size_t)n * n), T((size_t)n * r);
-            for (int k = tid; k < kOffsets; k += nt) {
+            for (size_t fi = tid; fi < formed.size(); fi += nt) {
+                const int k = formed[fi];
                 unit_m2l_matrix(p, prm.d, offs[k], u, K.data(), kernel_kh(prm));
                 // T = K_o U~  (n x r)
                 std::fill(T.begin(), T.end(), 0.0);
@@ -486,10 +494,12 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
                 }
             }
         });
-        // symmetry K~_o^T = K~_{-o}
+        // symmetry K~_o^T = K~_{-o} on the pairs formed both ways, then the
+        // transposes for the rest
         double cmax = 0, dmax = 0;
-        for (int k = 0; k < kOffsets; ++k) {
-            const int km = offset_index(-offs[k][0], -offs[k][1], -offs[k][2]);
+        for (int k : formed) {
+            const int km = partner[k];
+            if (k < km && km % 40 != 0) continue;
             const double* ck = f.C.data() + (size_t)k * r * r;
             const double* cm = f.C.data() + (size_t)km * r * r;
             for (int a = 0; a < r; ++a)
@@ -499,6 +509,13 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
                 }
         }
         f.sym_err = cmax > 0 ? dmax / cmax : 0.0;
+        for (int k = 0; k < kOffsets; ++k) {
+            if (k < partner[k] || k % 40 == 0) continue;
+            const double* cp = f.C.data() + (size_t)partner[k] * r * r;
+            double* ck = f.C.data() + (size_t)k * r * r;
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b) ck[(size_t)a * r + b] = cp[(size_t)b * r + a];
+        }
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed in the FP64 precompute");
         return KIFMM_ERR_OOM;
