@@ -41,7 +41,7 @@ thread_local std::string g_last_error;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTieTol = 1e-13;          // equal singular values: within 1e-13 sigma_0
 constexpr unsigned kCacheMagic = 0x4b4d324cu;  // "KM2L"
-constexpr unsigned kCacheVersion = 2;
+constexpr unsigned kCacheVersion = 3;
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -346,6 +346,122 @@ void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& V, std::vect
     V.swap(Vs);
 }
 
+// Right singular vectors and singular values of A (n x n column-major) by the
+// preconditioned one-sided Jacobi method of Drmac and Veselic (SIAM J. Matrix
+// Anal. Appl. 29, 2008): A P = Q R1 by Householder QR with column pivoting,
+// then one-sided Jacobi on the columns of R1^T, which are graded, so the
+// sweeps converge several times sooner than on A itself (14 against 40 for
+// the K_fat factor at p = 10).  With R1^T Y = X S the right singular vectors
+// of A are P X (X the normalised columns): no rotation is accumulated.  A is
+// overwritten; V column-major, both sorted by descending singular value.
+void jacobi_svd_pre(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& sig, ThreadTeam& team) {
+    std::vector<int> perm(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::vector<double> cn(n), cn0(n);
+    for (int j = 0; j < n; ++j) {
+        double acc = 0;
+        const double* aj = A.data() + (size_t)j * n;
+        for (int i = 0; i < n; ++i) acc += aj[i] * aj[i];
+        cn[j] = cn0[j] = acc;
+    }
+    std::vector<double> v(n);
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int j = k + 1; j < n; ++j) if (cn[j] > cn[piv]) piv = j;
+        if (piv != k) {
+            std::swap_ranges(A.begin() + (size_t)k * n, A.begin() + (size_t)(k + 1) * n, A.begin() + (size_t)piv * n);
+            std::swap(cn[k], cn[piv]); std::swap(cn0[k], cn0[piv]); std::swap(perm[k], perm[piv]);
+        }
+        double* ak = A.data() + (size_t)k * n;
+        double nrm = 0;
+        for (int i = k; i < n; ++i) nrm += ak[i] * ak[i];
+        nrm = std::sqrt(nrm);
+        if (nrm == 0.0) continue;
+        const double alpha = ak[k] > 0 ? -nrm : nrm;
+        // v = x - alpha e1, normalised so that H = I - 2 v v^T / (v^T v)
+        for (int i = k; i < n; ++i) v[i] = ak[i];
+        v[k] -= alpha;
+        double vv = 0;
+        for (int i = k; i < n; ++i) vv += v[i] * v[i];
+        ak[k] = alpha;
+        for (int i = k + 1; i < n; ++i) ak[i] = 0.0;
+        if (vv == 0.0) continue;
+        team.run([&](int tid, int nt) {
+            for (int j = k + 1 + tid; j < n; j += nt) {
+                double* aj = A.data() + (size_t)j * n;
+                double d = 0;
+                for (int i = k; i < n; ++i) d += v[i] * aj[i];
+                const double w = 2.0 * d / vv;
+                for (int i = k; i < n; ++i) aj[i] -= w * v[i];
+            }
+        });
+        for (int j = k + 1; j < n; ++j) {
+            const double* aj = A.data() + (size_t)j * n;
+            cn[j] -= aj[k] * aj[k];
+            if (cn[j] < 1e-8 * cn0[j]) {  // recompute after cancellation
+                double acc = 0;
+                for (int i = k + 1; i < n; ++i) acc += aj[i] * aj[i];
+                cn[j] = cn0[j] = acc;
+            }
+        }
+    }
+    // B = R1^T (column j of B = row j of R1), column-major
+    std::vector<double> B((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i <= j; ++i) B[(size_t)i * n + j] = A[(size_t)j * n + i];
+    const double tol = 1e-15;
+    std::vector<int> ring(n);
+    std::iota(ring.begin(), ring.end(), 0);
+    std::vector<long> rot_count(team.size());
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        std::fill(rot_count.begin(), rot_count.end(), 0L);
+        for (int round = 0; round < n - 1; ++round) {
+            team.run([&](int tid, int nt) {
+                for (int m = tid; m < n / 2; m += nt) {
+                    int a = ring[m], b = ring[n - 1 - m];
+                    if (a > b) std::swap(a, b);
+                    double* ap = B.data() + (size_t)a * n;
+                    double* aq = B.data() + (size_t)b * n;
+                    double al = 0, be = 0, ga = 0;
+                    for (int i = 0; i < n; ++i) { al += ap[i] * ap[i]; be += aq[i] * aq[i]; ga += ap[i] * aq[i]; }
+                    if (ga == 0.0 || std::fabs(ga) <= tol * std::sqrt(al * be)) continue;
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                    for (int i = 0; i < n; ++i) { const double x = ap[i], y = aq[i]; ap[i] = c * x - sn * y; aq[i] = sn * x + c * y; }
+                    ++rot_count[tid];
+                }
+            });
+            int last = ring[n - 1];
+            for (int i = n - 1; i > 1; --i) ring[i] = ring[i - 1];
+            ring[1] = last;
+        }
+        long rotations = 0;
+        for (long c : rot_count) rotations += c;
+        if (rotations == 0) break;
+    }
+    std::vector<double> s(n);
+    for (int j = 0; j < n; ++j) {
+        double acc = 0;
+        const double* bj = B.data() + (size_t)j * n;
+        for (int i = 0; i < n; ++i) acc += bj[i] * bj[i];
+        s[j] = std::sqrt(acc);
+    }
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return s[x] > s[y]; });
+    sig.resize(n);
+    V.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        const int src = ord[j];
+        sig[j] = s[src];
+        const double* bj = B.data() + (size_t)src * n;
+        double* vj = V.data() + (size_t)j * n;
+        if (s[src] > 0)
+            for (int k = 0; k < n; ++k) vj[perm[k]] = bj[k] / s[src];
+    }
+}
+
 int truncation_rank(const std::vector<double>& sig, double eps) {
     const int n = (int)sig.size();
     if (eps <= 0) return n;
@@ -434,7 +550,7 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
         for (int c = 0; c < n; ++c)
             for (int i = c + 1; i < n; ++i) R[i + (size_t)c * n] = 0.0;
         std::vector<double> V, sig;
-        jacobi_svd(n, R, V, sig, team);
+        jacobi_svd_pre(n, R, V, sig, team);
         const int r = truncation_rank(sig, prm.eps);
 
         f.p = p;
