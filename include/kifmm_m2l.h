@@ -112,12 +112,15 @@ typedef struct kifmm_m2l_plan_s* kifmm_m2l_plan;   /* opaque; owned by the libra
 
 /* Build the translation operators for `params` (Sec. 3.1, Step 1.4 of the
  * paper's algorithm): forms the 316 unit-level K_o, takes the SVD of K_fat
- * in FP64 on the host (TSQR + one-sided Jacobi), truncates at eps (a cut
- * through a cluster of equal singular values moves past the cluster: values
- * within 1e-13 sigma_0 count as equal), sets R~ = U~ (K_o^T = K_{-o} for this
- * radial kernel, so the thin SVD's right basis spans U~'s space), forms
- * K~_o = U~^T K_o U~ in FP64 and uploads FP32 / BF16-split copies to the
- * current CUDA device.  The FP64 factors are cached on disk under
+ * in FP64 on the host (TSQR, then the preconditioned one-sided Jacobi
+ * method: column-pivoted QR, Jacobi on the transposed factor), truncates at
+ * eps (a cut through a cluster of equal singular values moves past the
+ * cluster: values within 1e-13 sigma_0 count as equal), sets R~ = U~
+ * (K_o^T = K_{-o} for both radial kernels, so the thin SVD's right basis
+ * spans U~'s space), forms K~_o = U~^T K_o U~ in FP64 for one offset of
+ * every (o, -o) pair (the other is its transpose; the identity is checked
+ * on sampled pairs and the plan refused above 1e-10 relative) and uploads
+ * FP32 / BF16 / FP16-split copies to the current CUDA device.  The FP64 factors are cached on disk under
  * $KIFMM_M2L_CACHE (default: no cache) keyed by (kernel, p, d, eps, kappa h).
  * On success *out owns device memory until kifmm_m2l_destroy(). */
 int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out);
