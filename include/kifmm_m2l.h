@@ -126,12 +126,14 @@ typedef struct kifmm_m2l_plan_s* kifmm_m2l_plan;   /* opaque; owned by the libra
 int kifmm_m2l_precompute(const kifmm_m2l_params* params, kifmm_m2l_plan* out);
 
 /* Release every host and device resource of the plan (NULL is a no-op).
- * The caller must have synchronised streams that used it. */
+ * The caller must have synchronised streams that used it.
+ * Library lifetime; no passage of the paper. */
 int kifmm_m2l_destroy(kifmm_m2l_plan plan);
 
 /* Rank introspection: *r = retained rank, *r_pad = r rounded up to a
  * multiple of 16 (device layout; the extra columns are zero), *n = surface
- * points.  Any output pointer may be NULL. */
+ * points.  Any output pointer may be NULL.
+ * r is the rank kept by the truncation of Sec. 3.1 (Eqs. eq-kfat, fat). */
 int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n);
 
 /* ---- per-level state --------------------------------------------------- */
@@ -148,7 +150,8 @@ int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n);
 int kifmm_m2l_set_level(kifmm_m2l_plan plan, int instance, int level, double root_halfwidth,
                         int n_boxes, const int32_t* box_ijk);
 
-/* Number of M2L pairs (target, source) of a registered level. */
+/* Number of M2L pairs (target, source) of a registered level.
+ * The pairs are those of the interaction fields I^t (Sec. 2.1, Step 1.2). */
 int kifmm_m2l_level_pairs(kifmm_m2l_plan plan, int instance, int level, int64_t* n_pairs);
 
 /* ---- the translation --------------------------------------------------- */
@@ -168,7 +171,8 @@ int kifmm_m2l_apply(kifmm_m2l_plan plan, int instance, int level, int nrhs,
  *   qbar_up = beta * qbar_up + R~ q~bar
  * applied as the core of the reversed offset, K~_o^T = K~_{-o} (which holds
  * to FP64 rounding because K_o^T = K_{-o} and R~ = U~; checked at
- * precompute).  Same layouts and rules as kifmm_m2l_apply. */
+ * precompute).  Same layouts and rules as kifmm_m2l_apply.
+ * The transpose of Eq. evalcmp1 (Sec. 3.1), formed with K~_o^T = K~_{-o}. */
 int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                             const float* pbar_down, float* qbar_up, float beta, void* stream);
 
@@ -186,7 +190,8 @@ int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nr
 int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                            const float* q_up, float* p_down, float beta, void* stream);
 
-/* Adjoint of kifmm_m2l_apply_levels (see kifmm_m2l_apply_adjoint). */
+/* Adjoint of kifmm_m2l_apply_levels (see kifmm_m2l_apply_adjoint).
+ * The transpose of Eq. evalcmp1 (Sec. 3.1) over several levels. */
 int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                                    const float* pbar_down, float* qbar_up, float beta, void* stream);
 
@@ -231,7 +236,8 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
 /* Synchronise `stream` and report device-side failures of earlier applies
  * on this plan: KIFMM_ERR_TIMEOUT when a bounded wait inside the
  * tensor-core kernel ran out (results of that apply are invalid; the flag
- * is cleared), KIFMM_ERR_CUDA on an asynchronous CUDA error. */
+ * is cleared), KIFMM_ERR_CUDA on an asynchronous CUDA error.
+ * Library utility; no passage of the paper. */
 int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
 
 /* ---- allocation-free apply ------------------------------------------------ */
@@ -262,7 +268,8 @@ int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
  *    (the call clears what must start at zero).  Calls whose device work
  *    overlaps, e.g. on two streams at once, race and give wrong results:
  *    serialise them.
- * Same argument rules as kifmm_m2l_apply. */
+ * Same argument rules as kifmm_m2l_apply.
+ * Computes Eq. evalcmp1 (Sec. 3.1) like kifmm_m2l_apply. */
 #define KIFMM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                             const float* q_up, float* p_down, float beta, void* stream);
@@ -288,13 +295,15 @@ int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nr
 int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2);
 
 /* The per-offset ranks k_o of stage 2 (k[316], HOST memory, offsets in the
- * lexicographic order above).  KIFMM_ERR_STATE when stage 2 is off. */
+ * lexicographic order above).  KIFMM_ERR_STATE when stage 2 is off.
+ * Stage 2 is Sec. 3.2 (Eqs. eq-lra, eq-vareps2). */
 int kifmm_m2l_stage2_ranks(kifmm_m2l_plan plan, int* k);
 
 /* Host-only stage 2 (no GPU needed): the FP64 precompute of
  * kifmm_m2l_precompute followed by the factoring of kifmm_m2l_set_stage2;
  * writes the 316 ranks to k and, if core is not NULL, the truncated cores
- * Uhat_o Vhat_o to core[316][r][r] (row-major, r from kifmm_m2l_factors_host). */
+ * Uhat_o Vhat_o to core[316][r][r] (row-major, r from kifmm_m2l_factors_host).
+ * Stage 2 is Sec. 3.2 (Eqs. eq-lra, eq-vareps2). */
 int kifmm_m2l_stage2_host(const kifmm_m2l_params* params, double c2, int* k, double* core);
 
 /* ---- tracing ------------------------------------------------------------ */
@@ -302,14 +311,16 @@ int kifmm_m2l_stage2_host(const kifmm_m2l_params* params, double c2, int* k, dou
 /* Per-stage timing (enable != 0 turns it on, 0 off; off by default).  While
  * on, every apply / apply_adjoint records CUDA events on the caller's
  * stream around its compression, core and expansion kernels.  Recording
- * costs a few microseconds per stage; leave it off for throughput runs. */
+ * costs a few microseconds per stage; leave it off for throughput runs.
+ * Library utility; no passage of the paper. */
 int kifmm_m2l_profile_enable(kifmm_m2l_plan plan, int enable);
 
 /* Read and clear the stage times recorded since the last read: waits for
  * the recorded events, writes ms[0..2] = summed milliseconds of the
  * compression, core and expansion kernels, and *launches = the number of
  * this library's kernel launches inside those intervals.  Either output
- * may be NULL. */
+ * may be NULL.
+ * Library utility; no passage of the paper. */
 int kifmm_m2l_profile_read(kifmm_m2l_plan plan, double* ms, int64_t* launches);
 
 /* ---- autotuning ---------------------------------------------------------- */
@@ -399,7 +410,8 @@ typedef struct kifmm_fmm_s* kifmm_fmm;
  * tree registers its levels on the plan under instances >= 2^30; destroy
  * every tree of a plan before the plan.  Errors: KIFMM_ERR_INVALID_ARG
  * (NULL pointer, sizes, non-finite coordinates), KIFMM_ERR_OOM,
- * KIFMM_ERR_CUDA. */
+ * KIFMM_ERR_CUDA.
+ * The octree and lists of Sec. 2.1 and the setup of Sec. 4. */
 int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points, int depth,
                      const double* centre, double r0, kifmm_fmm* out);
 
@@ -408,7 +420,8 @@ int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points
  * float32 [n_points] in the caller's point order; potential is overwritten.
  * Asynchronous on `stream`; calls on one tree (and on trees of one plan)
  * must be serialised.  Errors: KIFMM_ERR_INVALID_ARG (NULL, parts out of
- * 1..3), KIFMM_ERR_CUDA. */
+ * 1..3), KIFMM_ERR_CUDA.
+ * Eq. eq_eval by the complete algorithm of Sec. 4 with the compressed passes of Sec. 3.3. */
 int kifmm_fmm_evaluate(kifmm_fmm fmm, const float* q, float* potential, int parts, void* stream);
 
 /* Double layer (Sec. 4, Eq. eq-doubles2m): with normals set, the sources are
@@ -429,11 +442,13 @@ int kifmm_fmm_set_normals(kifmm_fmm fmm, const double* normals);
 
 /* Sizes of a tree: depth, leaves, boxes on levels 2..depth, M2L pairs over
  * those levels, and (target point, source point) pairs of the near field
- * (the point itself excluded).  Any output may be NULL. */
+ * (the point itself excluded).  Any output may be NULL.
+ * Sizes of the Sec. 2.1 tree and lists. */
 int kifmm_fmm_info(kifmm_fmm fmm, int* depth, int64_t* n_leaves, int64_t* n_boxes, int64_t* n_m2l_pairs,
                    int64_t* n_near_pairs);
 
-/* Release a tree and its levels on the plan.  NULL is a no-op. */
+/* Release a tree and its levels on the plan.  NULL is a no-op.
+ * Library lifetime; no passage of the paper. */
 int kifmm_fmm_destroy(kifmm_fmm fmm);
 
 /* ---- host-side introspection (no GPU needed) ----------------------------- */
@@ -443,7 +458,8 @@ int kifmm_fmm_destroy(kifmm_fmm fmm);
  * sigma: [n] singular values of K_fat, descending (or NULL);
  * U: [n][r] row-major retained left basis U~ (or NULL);
  * C: [316][r][r] row-major unit-level cores K~_o (or NULL).
- * Call once with the arrays NULL to learn n and r. */
+ * Call once with the arrays NULL to learn n and r.
+ * The factors of Sec. 3.1 (Eqs. eq-kfat, fat, eq-cmpM2Ls). */
 int kifmm_m2l_factors_host(const kifmm_m2l_params* params, int* n, int* r,
                            double* sigma, double* U, double* C);
 
@@ -467,10 +483,12 @@ int kifmm_m2l_pass_ops_host(const kifmm_m2l_params* params, double rcond, int* k
 int kifmm_m2l_pairs_host(int level, int n_boxes, const int32_t* box_ijk, int64_t* n_pairs,
                          int32_t* targets, int32_t* sources, int32_t* offsets);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).
+ * Library utility; no passage of the paper. */
 const char* kifmm_m2l_last_error(void);
 
-/* Library version string. */
+/* Library version string.
+ * Library utility; no passage of the paper. */
 const char* kifmm_m2l_version(void);
 
 #ifdef __cplusplus

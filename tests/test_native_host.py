@@ -210,3 +210,18 @@ def test_pass_ops_host_matches_oracle(native, p):
         a = U @ Mt[c].T @ U.T
         b = f.U @ ops.Lt[c] @ f.U.T
         assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(b), c
+
+
+def test_every_entry_point_cites_its_passage():
+    # each declaration of the C ABI is preceded by a comment that cites the
+    # passage of the paper it computes, or says that it has none
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "kifmm_m2l.h")).read()
+    names = re.findall(r"^(?:int|const char\*)\s+(kifmm_\w+)\(", hdr, flags=re.M)
+    assert len(names) >= 25
+    for name in names:
+        start = re.search(r"^(?:int|const char\*)\s+" + name + r"\(", hdr, flags=re.M).start()
+        end = hdr.rfind("*/", 0, start)
+        comment = hdr[hdr.rfind("/*", 0, end):end]
+        between = [ln for ln in hdr[end + 2:start].splitlines() if ln.strip()]
+        assert all(ln.startswith("#define") for ln in between), name
+        assert re.search(r"Sec\.|Eq\.|Step |no passage of the paper", comment), name
