@@ -57,20 +57,21 @@ FMM_RCOND = 1e-9
 # translating matrices (Sec. 2.2)
 # ---------------------------------------------------------------------------
 def downward_check_to_equivalent(p: int, d: float, h: float, rcond: float = FMM_RCOND) -> np.ndarray:
-    """Truncated-SVD pseudo-inverse of K(x^d, y^d) for a box of half-width h."""
+    """Truncated-SVD pseudo-inverse of K(x^d, y^d) for a box of half-width h.
+    Sec. 2.2 (L and T of the downward pass) on the surfaces of Sec. 2.1."""
     x = geo.surface_points(p, np.zeros(3), (1.0 + d) * h)
     y = geo.surface_points(p, np.zeros(3), (3.0 - 2.0 * d) * h)
     return np.linalg.pinv(geo.laplace_kernel(x, y), rcond=rcond)
 
 
 def child_signs() -> np.ndarray:
-    """[8, 3] signs (2 b - 1) of the octant c = 4 b_x + 2 b_y + b_z."""
+    """[8, 3] signs (2 b - 1) of the octant c = 4 b_x + 2 b_y + b_z. Sec. 2.1 (children of an octree box)."""
     return np.array([[2 * ((c >> 2) & 1) - 1, 2 * ((c >> 1) & 1) - 1, 2 * (c & 1) - 1]
                      for c in range(8)], dtype=np.float64)
 
 
 def octant(ijk: np.ndarray) -> np.ndarray:
-    """Octant index of boxes within their parents, from integer coordinates."""
+    """Octant index of boxes within their parents, from integer coordinates. Sec. 2.1 (children of an octree box)."""
     ijk = np.asarray(ijk, dtype=np.int64)
     return 4 * (ijk[:, 0] & 1) + 2 * (ijk[:, 1] & 1) + (ijk[:, 2] & 1)
 
@@ -127,7 +128,7 @@ def pass_operators(f: m2l_mod.SvdFactors, p: int, d: float, rcond: float = FMM_R
 # tree helpers
 # ---------------------------------------------------------------------------
 def leaf_points(tree):
-    """(order, bounds): points of leaf b are order[bounds[b]:bounds[b+1]]."""
+    """(order, bounds): points of leaf b are order[bounds[b]:bounds[b+1]]. Sec. 2.1 (leaves of the octree)."""
     nb = tree.levels[tree.depth].shape[0]
     order = np.argsort(tree.leaf_of_point, kind="stable")
     bounds = np.searchsorted(tree.leaf_of_point[order], np.arange(nb + 1))
@@ -135,7 +136,7 @@ def leaf_points(tree):
 
 
 def parent_rows(tree, level: int) -> np.ndarray:
-    """Row of each level-``level`` box's parent in ``tree.levels[level - 1]``."""
+    """Row of each level-``level`` box's parent in ``tree.levels[level - 1]``. Sec. 2.1 (parent of an octree box)."""
     par = {tuple(b): i for i, b in enumerate(tree.levels[level - 1].astype(np.int64))}
     return np.array([par[tuple(b)] for b in (tree.levels[level].astype(np.int64) >> 1)], dtype=np.int64)
 
@@ -151,7 +152,7 @@ def near_leaves(tree, b: int) -> np.ndarray:
 # ---------------------------------------------------------------------------
 def source_kernel(x, pts, src, normals=None) -> np.ndarray:
     """Kernel from the sources pts[src] to the points x: G, or dG/dn(y) with
-    the sources' normals for a double layer."""
+    the sources' normals for a double layer. Eq. eq_eval's kernel; the double layer of Sec. 4, Eq. eq-doubles2m."""
     if normals is None:
         return geo.laplace_kernel(x, pts[src])
     return geo.laplace_double_layer_kernel(x, pts[src], np.asarray(normals, dtype=np.float64)[src])
@@ -159,7 +160,7 @@ def source_kernel(x, pts, src, normals=None) -> np.ndarray:
 
 def direct_sum(points, q, targets=None, normals=None) -> np.ndarray:
     """p_i = sum_{j != i} G(x_i, x_j) q_j for the listed targets (all by
-    default); with ``normals``, dG(x_i, x_j)/dn(x_j) in place of G."""
+    default); with ``normals``, dG(x_i, x_j)/dn(x_j) in place of G. Eq. eq_eval."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     idx = np.arange(pts.shape[0]) if targets is None else np.asarray(targets)
@@ -174,7 +175,8 @@ def direct_sum(points, q, targets=None, normals=None) -> np.ndarray:
 
 
 def near_field(tree, points, q, normals=None) -> np.ndarray:
-    """S2T: potential at every point from the points of its leaf's near field."""
+    """S2T: potential at every point from the points of its leaf's near field.
+    Sec. 2.2 (S2T) over the near field of Sec. 2.1."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     order, bounds = leaf_points(tree)
@@ -195,7 +197,7 @@ def near_field(tree, points, q, normals=None) -> np.ndarray:
 # ---------------------------------------------------------------------------
 def _upward(tree, points, p, d, q, rcond, normals=None):
     """Upward equivalent densities of levels 2..depth (S2M, M2M), every
-    operator formed at the box's own half-width."""
+    operator formed at the box's own half-width. Eqs. eq-s2m, eq-m2m."""
     pts = np.asarray(points, dtype=np.float64)
     L = tree.depth
     order, bounds = leaf_points(tree)
@@ -253,7 +255,8 @@ def fmm_uncompressed_far(tree, points, p: int, d: float, q, rcond: float = FMM_R
 # ---------------------------------------------------------------------------
 def leaf_check_potentials(tree, points, p: int, d: float, q, normals=None) -> np.ndarray:
     """K(x^u, points in the leaf) q for every leaf, [B_depth, n]: the part of
-    S that depends on the points (double-layer kernel with ``normals``)."""
+    S that depends on the points (double-layer kernel with ``normals``).
+    Eq. eq-s2m (its first step); the double layer of Eq. eq-doubles2m."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     L = tree.depth
@@ -269,7 +272,7 @@ def leaf_check_potentials(tree, points, p: int, d: float, q, normals=None) -> np
 
 
 def compressed_upward(tree, points, f, ops: PassOperators, p: int, d: float, q, normals=None) -> dict:
-    """q~ of levels 2..depth: q~ = S~ q at the leaves, q~_C = sum_c M~_c q~_c."""
+    """q~ of levels 2..depth: q~ = S~ q at the leaves, q~_C = sum_c M~_c q~_c. Sec. 3.3 (S~ and M~)."""
     L = tree.depth
     qt = {L: tree.halfwidth(L) * leaf_check_potentials(tree, points, p, d, q, normals) @ ops.Ws.T}
     for level in range(L - 1, 1, -1):
@@ -293,7 +296,7 @@ def compressed_m2l(box_ijk, level: int, r0: float, f, qt) -> np.ndarray:
 
 
 def compressed_downward(tree, f, ops: PassOperators, qt: dict) -> dict:
-    """p~ of levels 2..depth: M2L of each level plus p~_E += L~_c p~_parent."""
+    """p~ of levels 2..depth: M2L of each level plus p~_E += L~_c p~_parent. Sec. 3.3 (the compressed M2L and L~)."""
     L = tree.depth
     pt = {}
     for level in range(2, L + 1):
@@ -308,7 +311,7 @@ def compressed_downward(tree, f, ops: PassOperators, qt: dict) -> dict:
 
 def leaf_l2t(tree, points, p: int, d: float, e_leaf) -> np.ndarray:
     """Potential at every point from its leaf's downward equivalent densities
-    e_leaf [B_depth, n] placed on y^d."""
+    e_leaf [B_depth, n] placed on y^d. Eq. eq-l2t (Sec. 2.2)."""
     pts = np.asarray(points, dtype=np.float64)
     L = tree.depth
     h = tree.halfwidth(L)

@@ -62,12 +62,14 @@ def surface_grid(p: int) -> np.ndarray:
 
 
 def unit_surface(p: int) -> np.ndarray:
-    """Surface points of the cube [-1,1]^3: 2*ijk/(p-1) - 1, float64 [n,3]."""
+    """Surface points of the cube [-1,1]^3: 2*ijk/(p-1) - 1, float64 [n,3].
+    Sec. 2.1 (equivalent and check surfaces)."""
     return 2.0 * surface_grid(p) / (p - 1) - 1.0
 
 
 def surface_points(p: int, centre, halfwidth: float) -> np.ndarray:
-    """Points on the boundary of the cube with the given centre and half-width."""
+    """Points on the boundary of the cube with the given centre and half-width.
+    Sec. 2.1 (equivalent and check surfaces)."""
     return np.asarray(centre, dtype=np.float64)[None, :] + halfwidth * unit_surface(p)
 
 
@@ -83,12 +85,12 @@ def m2l_offsets() -> np.ndarray:
 
 
 def offset_index_table() -> dict:
-    """Map tuple(o) -> index into ``m2l_offsets()``."""
+    """Map tuple(o) -> index into ``m2l_offsets()``. Sec. 3.1 (the 316 offsets)."""
     return {tuple(o): k for k, o in enumerate(m2l_offsets())}
 
 
 def _linear_keys(ijk: np.ndarray) -> np.ndarray:
-    """Injective integer key of box coordinates in [-8, 2**20)^3."""
+    """Injective integer key of box coordinates in [-8, 2**20)^3. Sec. 2.1 (integer box coordinates)."""
     ijk = ijk.astype(np.int64) + 8
     return (ijk[..., 0] << 42) | (ijk[..., 1] << 21) | ijk[..., 2]
 
@@ -134,7 +136,7 @@ def interaction_lists(box_ijk: np.ndarray):
 
 def interaction_lists_bruteforce(box_ijk: np.ndarray):
     """O(B^2) statement of the same set: all pairs with |o|_inf >= 2 and
-    |parent(t) - parent(s)|_inf <= 1.  For tiny inputs only."""
+    |parent(t) - parent(s)|_inf <= 1.  For tiny inputs only. Sec. 2.1 (interaction field)."""
     box_ijk = np.asarray(box_ijk, dtype=np.int64)
     otab = offset_index_table()
     tg, sr, ok = [], [], []

@@ -33,7 +33,8 @@ from . import geometry as geo
 # translation matrices
 # ---------------------------------------------------------------------------
 def kernel_matrix(x, y, kappa: float = 0.0) -> np.ndarray:
-    """G(x_i, y_j): Laplace, or Yukawa with screening ``kappa`` > 0."""
+    """G(x_i, y_j): Laplace, or Yukawa with screening ``kappa`` > 0.
+    Sec. 4 (Laplace kernel); Sec. 3.1 (non-homogeneous case)."""
     return geo.laplace_kernel(x, y) if kappa == 0.0 else geo.yukawa_kernel(x, y, kappa)
 
 
@@ -48,7 +49,7 @@ def m2l_matrix_geometric(p: int, d: float, centre_t, centre_s, h: float, kappa: 
 
 def unit_m2l_matrices(p: int, d: float, kappa: float = 0.0, h: float = 1.0) -> np.ndarray:
     """The 316 translation matrices K_o of boxes of half-width h (unit by
-    default) with centres 2 o h apart, [316, n, n]."""
+    default) with centres 2 o h apart, [316, n, n]. Eq. eq-m2l; Sec. 3.1 (the 316 matrices)."""
     offs = geo.m2l_offsets()
     zero = np.zeros(3)
     return np.stack([m2l_matrix_geometric(p, d, 2.0 * h * o.astype(np.float64), zero, h, kappa)
@@ -101,7 +102,8 @@ def truncation_rank(sigma: np.ndarray, eps: float, tie_tol: float = 1e-13) -> in
 
 def _fix_signs(m: np.ndarray) -> np.ndarray:
     """Make the largest-magnitude entry of each column positive (an arbitrary
-    but deterministic choice; singular vectors are defined up to sign)."""
+    but deterministic choice; singular vectors are defined up to sign).
+    Sec. 3.1 (singular vectors; the sign is a reading)."""
     idx = np.argmax(np.abs(m), axis=0)
     s = np.sign(m[idx, np.arange(m.shape[1])])
     s[s == 0] = 1.0
@@ -157,6 +159,7 @@ def factors_scale(f: SvdFactors, level: int, r0: float) -> float:
 # M2L on a level of boxes
 # ---------------------------------------------------------------------------
 def _as3(q):
+    """Layout helper; no passage of the paper."""
     q = np.asarray(q, dtype=np.float64)
     return (q[:, None, :], True) if q.ndim == 2 else (q, False)
 
@@ -231,7 +234,8 @@ def m2l_svd(box_ijk, level: int, r0: float, f: SvdFactors, q_up, lists=None) -> 
 
 
 def m2l_svd_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, pbar, lists=None) -> np.ndarray:
-    """Transpose of ``m2l_svd``: q-bar^s = s_l R~ sum_{t: s in I^t} K~_{t-s}^T U~^T p-bar^t."""
+    """Transpose of ``m2l_svd``: q-bar^s = s_l R~ sum_{t: s in I^t} K~_{t-s}^T U~^T p-bar^t.
+    The transpose of Eq. evalcmp1 (Sec. 3.1)."""
     pb, squeeze = _as3(pbar)
     tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
     pt = pb @ f.U                                    # [B, nrhs, r]
@@ -249,7 +253,7 @@ def m2l_svd_targets(box_ijk, level: int, r0: float, f: SvdFactors, q_up, targets
 
     For sampled checks at sizes where the full oracle is too slow.
     Returns [len(targets), nrhs, n].
-    """
+    Eq. evalcmp1 (Sec. 3.1)."""
     q, _ = _as3(q_up)
     box_ijk = np.asarray(box_ijk, dtype=np.int64)
     index = {tuple(b): i for i, b in enumerate(box_ijk)}
@@ -307,7 +311,8 @@ def m2l_svd_stage2(box_ijk, level: int, r0: float, f: SvdFactors, s2, q_up, list
 
 
 def m2l_svd_stage2_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, s2, pbar, lists=None) -> np.ndarray:
-    """Transpose of ``m2l_svd_stage2``: q-bar~^s = s_l sum_t Vhat_o^T (Uhat_o^T p-bar~^t)."""
+    """Transpose of ``m2l_svd_stage2``: q-bar~^s = s_l sum_t Vhat_o^T (Uhat_o^T p-bar~^t).
+    The transpose of Eq. eq-lra's products (Sec. 3.2)."""
     pb, squeeze = _as3(pbar)
     tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
     pt = pb @ f.U

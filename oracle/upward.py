@@ -23,7 +23,7 @@ PINV_RCOND = 1e-12
 
 def check_to_equivalent(p: int, d: float, h: float, rcond: float = PINV_RCOND) -> np.ndarray:
     """Truncated-SVD pseudo-inverse of K(x^u, y^u) for a box of half-width h
-    (singular values below rcond * sigma_max dropped)."""
+    (singular values below rcond * sigma_max dropped). Sec. 2.2 (S and M) on the surfaces of Sec. 2.1."""
     x = geo.surface_points(p, np.zeros(3), (3.0 - 2.0 * d) * h)
     y = geo.surface_points(p, np.zeros(3), (1.0 + d) * h)
     return np.linalg.pinv(geo.laplace_kernel(x, y), rcond=rcond)
@@ -80,7 +80,7 @@ def m2m(tree, p: int, d: float, q_child: np.ndarray, level: int) -> np.ndarray:
 
 
 def upward_pass(tree, points: np.ndarray, p: int, d: float, q_points: np.ndarray) -> dict:
-    """Upward equivalent densities for every level 2..depth, {level: [B_l, n]}."""
+    """Upward equivalent densities for every level 2..depth, {level: [B_l, n]}. Eqs. eq-s2m, eq-m2m (Sec. 2.2)."""
     out = {tree.depth: s2m(tree, points, p, d, q_points)}
     for level in range(tree.depth - 1, 1, -1):
         out[level] = m2m(tree, p, d, out[level + 1], level)
