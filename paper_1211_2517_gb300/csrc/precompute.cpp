@@ -41,7 +41,7 @@ thread_local std::string g_last_error;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTieTol = 1e-13;          // equal singular values: within 1e-13 sigma_0
 constexpr unsigned kCacheMagic = 0x4b4d324cu;  // "KM2L"
-constexpr unsigned kCacheVersion = 3;
+constexpr unsigned kCacheVersion = 4;
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -218,14 +218,33 @@ int team_size() {
     return n;
 }
 
+// Dot product with eight independent partial sums: without reassociation a
+// single accumulator makes every FMA wait for the previous one; eight
+// chains let the loads and FMAs overlap (TSQR 1.7x faster at p = 10).
+inline double dot8(const double* a, const double* b, int n) {
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0;
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+        s0 += a[i] * b[i];
+        s1 += a[i + 1] * b[i + 1];
+        s2 += a[i + 2] * b[i + 2];
+        s3 += a[i + 3] * b[i + 3];
+        s4 += a[i + 4] * b[i + 4];
+        s5 += a[i + 5] * b[i + 5];
+        s6 += a[i + 6] * b[i + 6];
+        s7 += a[i + 7] * b[i + 7];
+    }
+    for (; i < n; ++i) s0 += a[i] * b[i];
+    return ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7));
+}
+
 // Merge a dense block B (mb x n, column-major) into the upper-triangular R
 // (n x n, column-major): on return R is the triangular factor of [R; B].
 // B is overwritten with Householder vectors.
 void householder_merge(int n, double* R, int mb, double* B) {
     for (int k = 0; k < n; ++k) {
         double* bk = B + (size_t)k * mb;
-        double xn2 = 0.0;
-        for (int i = 0; i < mb; ++i) xn2 += bk[i] * bk[i];
+        const double xn2 = dot8(bk, bk, mb);
         if (xn2 == 0.0) continue;
         const double alpha = R[k + (size_t)k * n];
         const double beta = (alpha >= 0.0 ? -1.0 : 1.0) * std::sqrt(alpha * alpha + xn2);
@@ -235,8 +254,7 @@ void householder_merge(int n, double* R, int mb, double* B) {
         R[k + (size_t)k * n] = beta;
         for (int c = k + 1; c < n; ++c) {
             double* bc = B + (size_t)c * mb;
-            double w = R[k + (size_t)c * n];
-            for (int i = 0; i < mb; ++i) w += bk[i] * bc[i];
+            double w = R[k + (size_t)c * n] + dot8(bk, bc, mb);
             w *= tau;
             R[k + (size_t)c * n] -= w;
             for (int i = 0; i < mb; ++i) bc[i] -= w * bk[i];
@@ -290,12 +308,7 @@ void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& V, std::vect
                 if (a > b) std::swap(a, b);
                 double* ap = A.data() + (size_t)a * n;
                 double* aq = A.data() + (size_t)b * n;
-                double alpha = 0, beta = 0, gamma = 0;
-                for (int i = 0; i < n; ++i) {
-                    alpha += ap[i] * ap[i];
-                    beta += aq[i] * aq[i];
-                    gamma += ap[i] * aq[i];
-                }
+                const double alpha = dot8(ap, ap, n), beta = dot8(aq, aq, n), gamma = dot8(ap, aq, n);
                 if (gamma == 0.0 || std::fabs(gamma) <= tol * std::sqrt(alpha * beta)) continue;
                 const double zeta = (beta - alpha) / (2.0 * gamma);
                 const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
@@ -373,24 +386,20 @@ void jacobi_svd_pre(int n, std::vector<double>& A, std::vector<double>& V, std::
             std::swap(cn[k], cn[piv]); std::swap(cn0[k], cn0[piv]); std::swap(perm[k], perm[piv]);
         }
         double* ak = A.data() + (size_t)k * n;
-        double nrm = 0;
-        for (int i = k; i < n; ++i) nrm += ak[i] * ak[i];
-        nrm = std::sqrt(nrm);
+        const double nrm = std::sqrt(dot8(ak + k, ak + k, n - k));
         if (nrm == 0.0) continue;
         const double alpha = ak[k] > 0 ? -nrm : nrm;
         // v = x - alpha e1, normalised so that H = I - 2 v v^T / (v^T v)
         for (int i = k; i < n; ++i) v[i] = ak[i];
         v[k] -= alpha;
-        double vv = 0;
-        for (int i = k; i < n; ++i) vv += v[i] * v[i];
+        const double vv = dot8(v.data() + k, v.data() + k, n - k);
         ak[k] = alpha;
         for (int i = k + 1; i < n; ++i) ak[i] = 0.0;
         if (vv == 0.0) continue;
         team.run([&](int tid, int nt) {
             for (int j = k + 1 + tid; j < n; j += nt) {
                 double* aj = A.data() + (size_t)j * n;
-                double d = 0;
-                for (int i = k; i < n; ++i) d += v[i] * aj[i];
+                const double d = dot8(v.data() + k, aj + k, n - k);
                 const double w = 2.0 * d / vv;
                 for (int i = k; i < n; ++i) aj[i] -= w * v[i];
             }
@@ -422,8 +431,7 @@ void jacobi_svd_pre(int n, std::vector<double>& A, std::vector<double>& V, std::
                     if (a > b) std::swap(a, b);
                     double* ap = B.data() + (size_t)a * n;
                     double* aq = B.data() + (size_t)b * n;
-                    double al = 0, be = 0, ga = 0;
-                    for (int i = 0; i < n; ++i) { al += ap[i] * ap[i]; be += aq[i] * aq[i]; ga += ap[i] * aq[i]; }
+                    const double al = dot8(ap, ap, n), be = dot8(aq, aq, n), ga = dot8(ap, aq, n);
                     if (ga == 0.0 || std::fabs(ga) <= tol * std::sqrt(al * be)) continue;
                     const double zeta = (be - al) / (2.0 * ga);
                     const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
