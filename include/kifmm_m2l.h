@@ -15,7 +15,15 @@
  * surface y^{s,u} both at half-width (1+d) h (Sec. 2.1), I^t the
  * interaction field (Sec. 2.1), the 316 unit-level cores
  * K~_o = U~^T K_o R~ from the SVDs of K_fat and K_thin (Sec. 3.1), and the
- * level scale s_l = (r0 / 2^l)^(-1) from homogeneity (Sec. 3.1).
+ * level scale s_l = (r0 / 2^l)^(-1) from homogeneity (Sec. 3.1).  A
+ * non-homogeneous kernel (the Yukawa kernel exp(-kappa r) / (4 pi r)) takes
+ * one plan per level instead (Sec. 3.1's O(L) case, KIFMM_KERNEL_YUKAWA).
+ *
+ * Around the M2L: the second compression stage (Sec. 3.2), batched
+ * multi-instance launches, a tile autotuner, and the complete potential
+ * evaluation of a point cloud (kifmm_fmm_*: near field plus the compressed
+ * passes S~, M~, L~, T~ of Sec. 3.3; point charges or dipoles, the double
+ * layer of Sec. 4).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
