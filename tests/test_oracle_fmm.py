@@ -287,3 +287,13 @@ def test_double_layer_fmm_converges_to_direct_sum(dipole_case):
     errs[8] = np.linalg.norm(pot8 - exact) / np.linalg.norm(exact)
     assert errs[4] < 5e-3 and errs[6] < 1e-4 and errs[8] < 4e-6, errs
     assert errs[6] < errs[4] / 5.0 and errs[8] < errs[6] / 5.0, errs
+
+
+def test_double_layer_compressed_at_full_rank_equals_uncompressed(dipole_case):
+    # every singular value kept: Sec. 3.3's compressed passes applied to the
+    # dipoles' check potentials reproduce the uncompressed far field
+    tree, pts, nrm, q, _ = dipole_case
+    f = m2l.svd_factors(4, D, 0.0)
+    far_c = fmm.fmm_compressed_far(tree, pts, f, fmm.pass_operators(f, 4, D), 4, D, q, normals=nrm)
+    far_u = fmm.fmm_uncompressed_far(tree, pts, 4, D, q, normals=nrm)
+    assert np.linalg.norm(far_c - far_u) / np.linalg.norm(far_u) < 1e-10
