@@ -46,8 +46,11 @@ struct Factors {
     double sym_err = 0;         // max |K~_o^T - K~_{-o}| / max |K~|
 };
 
-// Full host precompute, with the optional on-disk cache.  Returns a status.
+// Full host precompute, with the optional on-disk cache and a one-entry
+// in-process memo of the last result.  Returns a status.
 int compute_factors(const kifmm_m2l_params& prm, Factors& f);
+// The same without the in-process memo.
+int compute_factors_uncached(const kifmm_m2l_params& prm, Factors& f);
 
 // Stage-2 per-offset factors (Sec. 3.2, Eq. eq-lra): K~_o = U_o S_o Q_o^T,
 // keep the k_o singular values >= eps2 * sigma_0(K_fat) with

@@ -543,7 +543,59 @@ void store_cache(const std::string& path, const kifmm_m2l_params& prm, const Fac
 
 }  // namespace
 
+namespace {
+
+// The factors of the last precompute in this process (one entry, held until
+// exit): a size query followed by the data query, or several plans of one
+// operator, cost one precompute.
+struct Memo {
+    bool valid = false;
+    int kernel_id = 0, p = 0;
+    double d = 0, eps = 0, kh = 0;
+    Factors f;
+};
+std::mutex g_memo_mutex;
+Memo g_memo;
+
+bool memo_matches(const kifmm_m2l_params& prm) {
+    return g_memo.valid && g_memo.kernel_id == prm.kernel_id && g_memo.p == prm.p && g_memo.d == prm.d &&
+           g_memo.eps == prm.eps && g_memo.kh == kernel_kh(prm);
+}
+
+}  // namespace
+
 int compute_factors(const kifmm_m2l_params& prm, Factors& f) {
+    int st = check_params(&prm);
+    if (st != KIFMM_OK) return st;
+    try {
+        std::lock_guard<std::mutex> lock(g_memo_mutex);
+        if (memo_matches(prm)) {
+            f = g_memo.f;
+            return KIFMM_OK;
+        }
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed copying the factors");
+        return KIFMM_ERR_OOM;
+    }
+    st = compute_factors_uncached(prm, f);
+    if (st != KIFMM_OK) return st;
+    try {
+        std::lock_guard<std::mutex> lock(g_memo_mutex);
+        g_memo.valid = false;
+        g_memo.f = f;
+        g_memo.kernel_id = prm.kernel_id;
+        g_memo.p = prm.p;
+        g_memo.d = prm.d;
+        g_memo.eps = prm.eps;
+        g_memo.kh = kernel_kh(prm);
+        g_memo.valid = true;
+    } catch (const std::bad_alloc&) {
+        g_memo.valid = false;  // the factors are returned all the same
+    }
+    return KIFMM_OK;
+}
+
+int compute_factors_uncached(const kifmm_m2l_params& prm, Factors& f) {
     int st = check_params(&prm);
     if (st != KIFMM_OK) return st;
     const std::string cpath = cache_path(prm);
