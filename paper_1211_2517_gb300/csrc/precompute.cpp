@@ -726,7 +726,7 @@ int compute_stage2(const Factors& f, double c2, Stage2& s2) {
                 A.assign((size_t)re * re, 0.0);
                 for (int c = 0; c < r; ++c)
                     for (int i = 0; i < r; ++i) A[(size_t)c * re + i] = C[(size_t)i * r + c];
-                jacobi_svd(re, A, V, sig, solo);  // V: right singular vectors q_j (columns), sig descending
+                jacobi_svd_pre(re, A, V, sig, solo);  // V: right singular vectors q_j (columns), sig descending
                 int k = 0;
                 while (k < r && sig[k] >= thr && sig[k] > 0) ++k;
                 s2.k[o] = k;
@@ -735,12 +735,7 @@ int compute_stage2(const Factors& f, double c2, Stage2& s2) {
                 for (int j = 0; j < k; ++j) {
                     const double* q = V.data() + (size_t)j * re;
                     // u_j = K~_o q_j / sigma_j
-                    for (int a = 0; a < r; ++a) {
-                        double acc = 0;
-                        const double* ca = C + (size_t)a * r;
-                        for (int b = 0; b < r; ++b) acc += ca[b] * q[b];
-                        u[a] = acc / sig[j];
-                    }
+                    for (int a = 0; a < r; ++a) u[a] = dot8(C + (size_t)a * r, q, r) / sig[j];
                     for (int a = 0; a < r; ++a) s2.Uh[o][(size_t)a * k + j] = u[a];
                     for (int b = 0; b < r; ++b) s2.Vh[o][(size_t)j * r + b] = sig[j] * q[b];
                 }
