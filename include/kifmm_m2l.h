@@ -248,6 +248,17 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
  * Library utility; no passage of the paper. */
 int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream);
 
+/* Bound, in nanoseconds, of every mbarrier wait inside this plan's core
+ * kernels from the next apply on (0 restores the default of 2 s).  A wait
+ * that runs out sets the plan's device error flag, the kernel stops all its
+ * roles, waits for its copies and MMAs in flight and frees its tensor
+ * memory, and the next kifmm_m2l_sync returns KIFMM_ERR_TIMEOUT; the plan
+ * stays usable.  A very short bound (a few ns) makes the first wait that is
+ * not already complete give up, which is how the failure path is tested
+ * without faulting the GPU.  Library utility (failure detection):
+ * no passage of the paper.  Errors: KIFMM_ERR_INVALID_ARG for a NULL plan. */
+int kifmm_m2l_set_wait_limit(kifmm_m2l_plan plan, unsigned long long ns);
+
 /* ---- allocation-free apply ------------------------------------------------ */
 
 /* kifmm_m2l_apply without any device allocation.  The paper has no

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkifmm_m2l.so")
 
 KIFMM_OK = 0
+KIFMM_ERR_TIMEOUT = -5
 ERR_NAMES = {
     -1: "KIFMM_ERR_INVALID_ARG",
     -2: "KIFMM_ERR_UNSUPPORTED",
@@ -32,7 +33,7 @@ EXPORTED = (
     "kifmm_m2l_apply_noalloc", "kifmm_m2l_apply_levels", "kifmm_m2l_apply_levels_adjoint",
     "kifmm_m2l_apply_batch",
     "kifmm_m2l_set_stage2", "kifmm_m2l_stage2_ranks", "kifmm_m2l_stage2_host",
-    "kifmm_m2l_sync", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
+    "kifmm_m2l_sync", "kifmm_m2l_set_wait_limit", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
     "kifmm_m2l_factors_host", "kifmm_m2l_pairs_host", "kifmm_m2l_last_error", "kifmm_m2l_version",
     "kifmm_fmm_create", "kifmm_fmm_evaluate", "kifmm_fmm_set_normals", "kifmm_fmm_info", "kifmm_fmm_destroy", "kifmm_m2l_pass_ops_host",
 )
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_apply_levels_adjoint": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_batch": [i32, ctypes.POINTER(BatchItem), i32, vp],
         "kifmm_m2l_sync": [vp, vp],
+        "kifmm_m2l_set_wait_limit": [vp, ctypes.c_ulonglong],
         "kifmm_m2l_profile_enable": [vp, i32],
         "kifmm_m2l_profile_read": [vp, ctypes.POINTER(ctypes.c_double), pi64],
         "kifmm_m2l_autotune": [vp, i32, i32, i32, i32, vp, vp, i32, ctypes.POINTER(TuneResult), vp],

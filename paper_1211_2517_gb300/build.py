@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkifmm_m2l.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["api.cu", "batch.cu", "fmm.cu", "kernels_fmm.cu", "kernels_simt.cu", "kernels_umma.cu", "noalloc.cu",
+CUDA_SOURCES = ["api.cu", "batch.cu", "fmm.cu", "kernels_core.cu", "kernels_fmm.cu", "kernels_simt.cu", "kernels_umma.cu", "noalloc.cu",
                 "tune.cu"]
 CXX_SOURCES = ["precompute.cpp"]
 # Per-file flags: the point-source leaf kernels never see subnormal values

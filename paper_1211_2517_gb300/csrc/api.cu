@@ -389,6 +389,7 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     a.red_bulk = plan->variant_bulk();
     a.mma_pair = plan->variant_pair();
     a.direct_rows = plan->variant_direct();
+    a.core_bres = plan->variant_bres();
     a.s2_on = plan->s2_on;
     a.s2_V = plan->s2V.ptr;
     a.s2_U = plan->s2U.ptr;
@@ -405,6 +406,7 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     a.n_products = plan->products;
     a.hilo = plan->core_hilo;
     a.error_flag = plan->err_flag.ptr;
+    a.wait_ns = plan->core_wait_ns;
     KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     return KIFMM_OK;
 }
@@ -1006,6 +1008,15 @@ int kifmm_m2l_sync(kifmm_m2l_plan plan, void* stream) {
         set_error("a bounded wait inside the tensor-core kernel timed out; results are invalid");
         return KIFMM_ERR_TIMEOUT;
     }
+    return KIFMM_OK;
+}
+
+int kifmm_m2l_set_wait_limit(kifmm_m2l_plan plan, unsigned long long ns) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    plan->core_wait_ns = ns;
     return KIFMM_OK;
 }
 

@@ -195,6 +195,7 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.red_bulk = plan->variant_bulk();
         a.mma_pair = plan->variant_pair();
         a.direct_rows = plan->variant_direct();
+        a.core_bres = plan->variant_bres();
         a.s2_on = plan->s2_on;
         a.s2_V = plan->s2V.ptr;
         a.s2_U = plan->s2U.ptr;
@@ -213,6 +214,7 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.f16 = f16 ? 1 : 0;
         a.row_scale = f16 ? g.qs.ptr : nullptr;
         a.error_flag = plan->err_flag.ptr;
+        a.wait_ns = plan->core_wait_ns;
         KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     }
     {

@@ -1,9 +1,12 @@
-// Kernel launch wrappers (device code in kernels_simt.cu, kernels_umma.cu).
+// Kernel launch wrappers (device code in kernels_simt.cu, kernels_umma.cu,
+// kernels_core.cu, kernels_fmm.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cstddef>
 #include <cstdint>
 
 namespace kifmm {
@@ -140,6 +143,7 @@ struct UmmaArgs {
                               // outputs follow the rows-mode conventions (m_rows or segments)
     int core_resident;        // core, split6 with hilo: 1 = A tile resident in shared memory, K~_o in N blocks
     int core_drain;           // core, split6: K-chunks per partial drained into registers by 8 epilogue warps (0: off)
+    int core_bres;            // core, 1 or 2 pieces: the staged-epilogue kernel of kernels_core.cu
     // core, stage 2 (Sec. 3.2): K~_o = Uhat_o Vhat_o with per-offset rank k_o
     int s2_on;
     const __nv_bfloat16* s2_V;  // pieces [pieces][316][96][kdim]: rows of Vhat_o, zero past k_o
@@ -164,7 +168,19 @@ struct UmmaArgs {
     int mma_pair;             // drained partials: K-chunks of a partial the MMA thread takes per step (<= 1: one)
     int direct_rows;          // E_RED, drained partials: every lane reduces its own row into D (no transpose)
     int* error_flag;          // device int, set when a bounded wait times out
+    unsigned long long wait_ns;  // bound of every mbarrier wait in ns (0: the default, 2 s)
 };
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& args, int num_sms, cudaStream_t stream);
+
+// The core whose epilogue stages rows in shared memory and reduces them into
+// p~ by TMA bulk reductions (kernels_core.cu): 1 or 2 pieces (n_products 1
+// or 3); cudaErrorNotSupported when the operands do not fit.
+cudaError_t launch_core_stage(const UmmaArgs& args, int num_sms, int max_smem, int dev, cudaStream_t stream);
+// Its shared-memory need (0: does not fit max_smem), ring stages in *stages.
+size_t core_stage_smem(int pieces, int kdim, int ndim, int max_smem, int* stages);
+
+// A 2-byte-element matrix [rows][cols] as a 2D TMA tensor map with boxes of
+// ch (32: 64-byte swizzle, 16: 32-byte swizzle) x box_rows; maps are cached.
+cudaError_t tma_map_2d(const void* ptr, uint64_t rows, int cols, int ch, int box_rows, CUtensorMap* out);
 
 }  // namespace kifmm

@@ -46,21 +46,22 @@
 
 #include "kernels.h"
 #include "kifmm_m2l.h"
+#include "umma_ptx.h"
 
 namespace kifmm {
 
 namespace {
 
+using namespace ptx;
+
 constexpr int kEpiWarps = 4, kProdWarps = 7;
 constexpr int kRowsProdWarps = 4;  // producer warps of the rows modes (128 threads, one per tile row)
 constexpr int kThreads = (kEpiWarps + kProdWarps + 1) * 32;  // 384
-constexpr int kTileM = 128;
 // K elements per pipeline stage (64-byte rows, 64-byte swizzle).  The
 // templates also support 16 (32-byte rows, 32-byte swizzle); measured on the
 // core, twice the stages of half the size cost more than they hide.
 __host__ __device__ constexpr int chunk_of(int) { return 32; }
 constexpr int kCBoxRows = 64;           // rows per TMA box of K~_o
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct Smem {
     // barriers live at the start of dynamic shared memory
@@ -73,182 +74,8 @@ struct Smem {
     uint64_t drain;
     uint32_t tmem_base;
     volatile int abort_flag;
+    unsigned long long wait_ns;  // bound of every mbarrier wait of this launch
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: true when the phase completed, false on timeout / abort
-// (SM: the kernel's barrier block, which holds the CTA's abort flag).
-template <class SM>
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, SM* sm, int* err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (sm->abort_flag) return false;
-        if (global_ns() - t0 > kWaitNs) {
-            sm->abort_flag = 1;
-            atomicExch(err, 1);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Bulk reduction of `bytes` (a multiple of 16) FP32 values from shared
-// memory into global memory by the TMA unit: dst[i] += src[i].
-__device__ __forceinline__ void bulk_reduce_add_f32(float* dst, uint32_t src, uint32_t bytes) {
-    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst), "r"(src),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// The sources of this thread's committed bulk operations have been read.
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// This thread's committed bulk operations are complete.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-// Arrive on `bar` once every cp.async this thread issued so far has landed
-// (the arrival counts against the barrier's expected count).
-__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-// wait until at most n (1..7) groups are pending
-__device__ __forceinline__ void cp_async_wait_pending(int n) {
-    switch (n) {
-        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
-        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
-        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
-    }
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// UMMA shared-memory descriptor, K-major, rows of CH BF16 elements swizzled
-// over their width: CH = 32 -> 64-byte swizzle (layout type 4), 8-row groups
-// 512 bytes apart; CH = 16 -> 32-byte swizzle (layout type 6), 8-row groups
-// 256 bytes apart.  Version 1 (bits 46-47), layout type in bits 61-63.
-template <int CH>
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;                        // LBO (unused for swizzled K-major)
-    d |= (uint64_t)((8 * CH * 2) >> 4) << 32;      // SBO: one 8-row group
-    d |= (uint64_t)1 << 46;                        // descriptor version
-    d |= (uint64_t)(CH == 32 ? 4 : 6) << 61;       // SWIZZLE_64B / SWIZZLE_32B
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128.
-__device__ __forceinline__ uint32_t umma_idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-}
-// The same with A=B=F16 (format code 0 in both operand fields) when f16 != 0.
-__device__ __forceinline__ uint32_t umma_idesc(int n, int f16) {
-    return f16 ? (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24) : umma_idesc_bf16(n);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void red_add_v4(float* addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-
-// Byte offset of 16-byte chunk c of row m in a swizzled tile whose base is
-// aligned to the swizzle atom: 64-byte rows (CH = 32): bits [4,6) ^= bits
-// [7,9); 32-byte rows (CH = 16): bit 4 ^= bit 7.
-template <int CH>
-__device__ __forceinline__ uint32_t swz(int m, int c) {
-    const uint32_t o = (uint32_t)m * (CH * 2) + (uint32_t)c * 16;
-    return CH == 32 ? (o ^ (((o >> 7) & 3u) << 4)) : (o ^ (((o >> 7) & 1u) << 4));
-}
 
 struct Layout {
     int stages, na, nc, c_rows_alloc, n_acc, acc_cols, n_items, n_chunks, kc_count;
@@ -330,6 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
+        sm->wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kEpiWarps + kProdWarps) {
@@ -1104,6 +932,7 @@ struct RSmem {
     uint64_t drain;
     uint32_t tmem_base;
     volatile int abort_flag;
+    unsigned long long wait_ns;  // bound of every mbarrier wait of this launch
 };
 
 struct RLayout {
@@ -1146,6 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
+        sm->wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kResMmaWarp) {
@@ -1420,6 +1250,7 @@ struct S2Smem {
     uint64_t t_full, t_empty, tsplit, tbuf_free, p_full, p_empty, drain;
     uint32_t tmem_base;
     volatile int abort_flag;
+    unsigned long long wait_ns;  // bound of every mbarrier wait of this launch
 };
 
 struct S2Layout {
@@ -1466,6 +1297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&sm->p_empty, kEpiWarps * 32);
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
+        sm->wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kEpiWarps + kProdWarps) {
@@ -1956,6 +1788,12 @@ cudaError_t launch_core_stage2(const UmmaArgs& a, int num_sms, cudaStream_t stre
 
 }  // namespace
 
+cudaError_t tma_map_2d(const void* ptr, uint64_t rows, int cols, int ch, int box_rows, CUtensorMap* out) {
+    EncodeTiledFn encode = get_encode_fn();
+    if (!encode) return cudaErrorNotSupported;
+    return get_map2d(static_cast<const __nv_bfloat16*>(ptr), (cuuint64_t)rows, cols, ch, box_rows, encode, out);
+}
+
 cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cudaStream_t stream) {
     if (a.kdim % 16 != 0 || a.kdim <= 0 || a.ndim % 16 != 0 || a.ndim < 16 || a.n_chunk % 16 != 0 ||
         a.n_chunk < 16 || a.n_chunk > 512)
@@ -2014,6 +1852,10 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
             if (ce != cudaSuccess) return ce;
         }
         max_smem = g_max_smem[dev];
+    }
+    if (gather && emode == E_RED && a.core_bres && !a.row_identity) {
+        const cudaError_t e = launch_core_stage(a, num_sms, max_smem, dev, stream);
+        if (e != cudaErrorNotSupported) return e;
     }
     // drain mode (split6 core): 8 epilogue warps, which needs at most 3
     // producer warps (= stages) and N <= 192 per item (96 sums per thread)

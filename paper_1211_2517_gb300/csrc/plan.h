@@ -125,12 +125,12 @@ struct kifmm_m2l_plan_s {
     // two K-chunks drained into registers, 3 / 5 of one, 6 / 10 of three
     // (f16x3); 4 / 5 reduce the rows into p~ with TMA bulk reductions
     // instead of vector atomics; 9 / 10 issue two K-chunks per MMA step,
-    // 11 (f16x3) a whole partial of three
+    // 11 (f16x3) a whole partial of three; 13 keeps K~_o in shared memory
     int variant_drain() const {
         switch (tune_variant) {
             case 2: case 4: return 2;
             case 3: case 5: return 1;
-            case 6: case 10: case 11: case 12: return 3;
+            case 6: case 10: case 11: case 12: case 13: return 3;
             case 9: return 2;
             default: return 0;
         }
@@ -139,6 +139,8 @@ struct kifmm_m2l_plan_s {
         return (tune_variant == 11 || tune_variant == 12) ? 3 : (tune_variant == 9 || tune_variant == 10) ? 2 : 1;
     }
     int variant_direct() const { return tune_variant == 12 ? 1 : 0; }
+    // 13 (1 or 2 pieces): K~_o resident in shared memory, only the A rows streamed
+    int variant_bres() const { return tune_variant == 13 ? 1 : 0; }
     int variant_bulk() const { return (tune_variant == 4 || tune_variant == 5) ? 1 : 0; }
     kifmm::DevBuf<float> C, K;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each (Cb: 2 FP16 pieces of tau K~ for F16X3)
@@ -158,6 +160,7 @@ struct kifmm_m2l_plan_s {
     kifmm::DevBuf<__nv_bfloat16> s2V, s2U;     // 3 BF16 pieces each
     kifmm::DevBuf<int> s2_k16;                 // [316] k_o rounded up to 16
     kifmm::DevBuf<int> err_flag;
+    unsigned long long core_wait_ns = 0;  // bound of the core kernels' waits (0: 2 s)
     std::map<std::pair<int, int>, std::unique_ptr<kifmm::LevelState>> levels;
     // multi-level batches keyed by (instance, level_lo, level_hi, adjoint)
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<kifmm::MultiState>> multi;

@@ -23,7 +23,10 @@
 //                9 and 10 (f16x3 only) as 2 and 6 with two K-chunks of a
 //                partial issued per MMA step, 11 (f16x3 only) with all three,
 //                12 (f16x3 only) as 11 with every epilogue lane reducing its
-//                own row segment into p~ (no shared-memory transpose).
+//                own row segment into p~ (no shared-memory transpose);
+//                13 (1 or 2 pieces) the core that keeps K~_o in shared memory
+//                while a CTA's contiguous run of tiles shares it, and streams
+//                only the gathered A rows.
 //                The FP16 split (f16x3) has no variant 1.
 // Each candidate is timed with CUDA events around the core launch of
 // kifmm_m2l_apply_levels.  With $KIFMM_M2L_AUTOTUNE_CACHE naming a file,
@@ -151,7 +154,7 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
         int c = 0, g = 0, rs = 0;
         double t = 0;
         if (it != entries.end() && parse_entry(it->second, &c, &g, &rs, &t) && c >= 16 && c % 16 == 0 &&
-            c <= 512 && (g == 0 || g == 1) && rs >= 0 && rs <= 12) {
+            c <= 512 && (g == 0 || g == 1) && rs >= 0 && rs <= 13) {
             plan->tune_chunk = c == core_chunk_default(plan) ? 0 : c;
             plan->tune_contig = g;
             plan->tune_variant = rs;
@@ -183,6 +186,7 @@ extern "C" int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_l
                 cands.push_back({c0, g, 12});
             }
         }
+        if (plan->products <= 3 && g == 1) cands.push_back({c0, g, 13});  // K~_o resident (contiguous runs only)
         cands.push_back({c0, g, 0});
         if (c1 >= 16 && c1 < c0) cands.push_back({c1, g, 0});
     }

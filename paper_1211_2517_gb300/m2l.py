@@ -253,6 +253,10 @@ class M2LPlan:
         """Synchronise the stream and raise on device-side failures."""
         call("kifmm_m2l_sync", self._h, _stream_handle(stream))
 
+    def set_wait_limit(self, ns: int = 0) -> None:
+        """Bound of the core kernels' device waits in ns from the next apply on (0: the default 2 s)."""
+        call("kifmm_m2l_set_wait_limit", self._h, int(ns))
+
 
 def apply_batch(items, use_graph: bool = False, stream=None):
     """Compressed M2L of many instances in one batch.

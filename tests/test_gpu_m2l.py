@@ -471,7 +471,7 @@ def test_f16x3_core_variants_match_oracle(g, oracle_factors, sphere_small, monke
     x_all = torch.from_numpy(np.concatenate([qs[l] for l in (2, 3, 4)])).cuda()
     res = plan.autotune(x_all, 2, 4, reps=2)
     print("autotune f16x3", res)
-    assert res["variant"] in (0, 2, 3, 4, 5, 6, 9, 10, 11, 12)
+    assert res["variant"] in (0, 2, 3, 4, 5, 6, 9, 10, 11, 12, 13)
     import json
 
     key = list(json.loads(cache.read_text()))[0]
@@ -480,7 +480,7 @@ def test_f16x3_core_variants_match_oracle(g, oracle_factors, sphere_small, monke
             for l in (2, 3, 4) for adj in (False, True)}
     for chunk, contig, variant in [(192, 0, 2), (192, 1, 2), (192, 0, 3), (192, 0, 4), (192, 1, 5), (192, 0, 6),
                                    (192, 1, 6), (192, 0, 9), (192, 0, 10), (192, 1, 10), (192, 0, 11), (192, 1, 11),
-                                   (192, 0, 12), (192, 1, 12), (192, 0, 0), (96, 1, 0)]:
+                                   (192, 0, 12), (192, 1, 12), (192, 1, 13), (192, 0, 0), (96, 1, 0)]:
         cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "variant": %d, "core_ms": 1.0}\n}\n'
                          % (key, chunk, contig, variant))
         got = plan.autotune(x_all, 2, 4, reps=1)
@@ -496,6 +496,66 @@ def test_f16x3_core_variants_match_oracle(g, oracle_factors, sphere_small, monke
                       f"rel L2 {err:.3e}")
                 assert err <= TOL["f16x3"], (chunk, contig, variant, adj, l, err)
                 row += nb
+    plan.close()
+
+
+def _force_variant(plan, x_all, lo, hi, cache, key, chunk, contig, variant):
+    cache.write_text('{\n"%s": {"n_chunk": %d, "contiguous": %d, "variant": %d, "core_ms": 1.0}\n}\n'
+                     % (key, chunk, contig, variant))
+    got = plan.autotune(x_all, lo, hi, reps=1)
+    assert got["from_cache"] and got["variant"] == variant, got
+
+
+@pytest.mark.parametrize("precision", ["f16x3", "split3", "bf16"])
+def test_resident_core_matches_oracle(g, oracle_factors, sphere_small, torus_mid, monkeypatch, tmp_path, precision):
+    """Core variant 13 (K~_o resident in shared memory, only the gathered A
+    rows streamed) against the oracle, forward and adjoint: p = 8 (r_pad 192,
+    one N part; levels 2-4 with 3 rhs, so tiles end raggedly inside every
+    offset group) and p = 10 at eps = 1e-8 (r_pad 272: two N parts of 144
+    and 128 columns, a 16-wide last K-chunk)."""
+    import json
+
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("KIFMM_M2L_AUTOTUNE_CACHE", str(cache))
+    tree, qs = sphere_small
+    f = oracle_factors(8, 0.1, 1e-7)
+    plan = make_plan(g, 8, 1e-7, precision, tree, (2, 3, 4))
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in (2, 3, 4)])).cuda()
+    c0 = plan.autotune(x_all, 2, 4, reps=1)["n_chunk"]
+    key = list(json.loads(cache.read_text()))[0]
+    _force_variant(plan, x_all, 2, 4, cache, key, c0, 1, 13)
+    for adj in (False, True):
+        out = plan.apply_levels(x_all, 2, 4, adjoint=adj).cpu().numpy()
+        plan.sync()
+        row = 0
+        for l in (2, 3, 4):
+            nb = tree.levels[l].shape[0]
+            ref = (om.m2l_svd_adjoint if adj else om.m2l_svd)(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64))
+            err = rel(out[row:row + nb], ref)
+            print(f"resident core p=8 {precision} adjoint {adj} level {l}: rel L2 {err:.3e}")
+            assert err <= TOL[precision], (adj, l, err)
+            row += nb
+    plan.close()
+    cache.unlink()
+    tree, qs = torus_mid
+    f = oracle_factors(10, 0.1, 1e-8)
+    plan = make_plan(g, 10, 1e-8, precision, tree, range(2, 6))
+    assert plan.r_pad == 272
+    x_all = torch.from_numpy(np.concatenate([qs[l] for l in range(2, 6)])).cuda()
+    c0 = plan.autotune(x_all, 2, 5, reps=1)["n_chunk"]
+    key = list(json.loads(cache.read_text()))[0]
+    _force_variant(plan, x_all, 2, 5, cache, key, c0, 1, 13)
+    for adj in (False, True):
+        out = plan.apply_levels(x_all, 2, 5, adjoint=adj).cpu().numpy()
+        plan.sync()
+        row = 0
+        for l in range(2, 6):
+            nb = tree.levels[l].shape[0]
+            ref = (om.m2l_svd_adjoint if adj else om.m2l_svd)(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64))
+            err = rel(out[row:row + nb], ref)
+            print(f"resident core p=10 {precision} adjoint {adj} level {l}: rel L2 {err:.3e}")
+            assert err <= TOL[precision], (adj, l, err)
+            row += nb
     plan.close()
 
 
