@@ -168,6 +168,57 @@ def oracle_sample(wl, seconds_budget):
     return done_pairs, spent, "oracle.m2l.m2l_svd (NumPy FP64, BLAS) on " + "; ".join(parts)
 
 
+_ORACLE_DENSE = {}
+
+
+def oracle_dense_sample(wl, seconds_budget):
+    """Time the FP64 oracle's uncompressed M2L (Eq. (4) through the 316
+    unit matrices, grouped by offset) on the first targets of the finest
+    level that fit the budget; returns (pairs, seconds, description)."""
+    import numpy as np
+
+    import synth
+    from oracle import geometry as geo
+    from oracle import m2l as om
+
+    key = (wl.p, wl.d)
+    if key not in _ORACLE_DENSE:
+        _ORACLE_DENSE[key] = om.unit_m2l_matrices(wl.p, wl.d)
+    K = _ORACLE_DENSE[key]
+    level = max(LEVELS)
+    box = wl.tree.levels[level]
+    tg, sr, ok = geo.interaction_lists(box)
+    q = synth.random_box_densities(box.shape[0], 1, K.shape[1], 2000 + level)[:, 0].astype(np.float64)
+    nt = max(1, box.shape[0] // 64)
+    done, spent, used = 0, 0.0, nt
+    while nt <= box.shape[0]:
+        sel = tg < nt
+        t0 = time.perf_counter()
+        om.m2l_dense_unit(box, level, wl.tree.r0, K, q, (tg[sel], sr[sel], ok[sel]))
+        done, spent, used = int(sel.sum()), time.perf_counter() - t0, nt
+        if spent > seconds_budget / 4:
+            break
+        nt *= 2
+    return done, spent, (f"oracle.m2l.m2l_dense_unit (NumPy FP64, BLAS) on level {level}, targets 0..{used - 1} "
+                         f"({done} pairs)")
+
+
+def oracle_single_thread(seconds_budget):
+    """The compressed oracle sample again in a child process whose BLAS runs
+    one thread (the thread count is fixed when NumPy loads); returns the
+    child's (pairs, seconds, description) or None."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, synth; "
+            "wl = synth.workload(bench.WORKLOAD); print(json.dumps(bench.oracle_sample(wl, %r)))"
+            % (ROOT, float(seconds_budget)))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=600).stdout.strip().splitlines()
+        return tuple(json.loads(out[-1])) if out else None
+    except (subprocess.TimeoutExpired, OSError, ValueError):
+        return None
+
+
 def job_throughput(local_ms: float, local_units: float, steps: int, device, world: int):
     """Whole-job throughput of weak-scaled replicas: the units every rank
     processed, summed, over the slowest rank's time (max over ranks).
@@ -216,7 +267,7 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels_umma.cu",):
+    for f in ("kernels_umma.cu", "kernels_core.cu", "umma_ptx.h"):
         h.update(open(os.path.join(ROOT, "paper_1211_2517_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -349,7 +400,9 @@ def run_ours(args, rank, world, local_rank):
                    10: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 2 per MMA step)",
                    11: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 3 per MMA step)",
                    12: "umma_kernel<A_GATHER,E_RED> (offset-grouped core, partials of 3 K-chunks, 3 per MMA step, "
-                       "rows reduced without a transpose)"}.get(
+                       "rows reduced without a transpose)",
+                   13: "core_stage_kernel (offset-grouped core, partials of 3 K-chunks drained into registers, rows "
+                       "staged in shared memory and reduced into p~ by TMA bulk reductions)"}.get(
                        (tune or {}).get("variant"), "umma_kernel<A_GATHER,E_RED> (offset-grouped core)"),
         "core_dtype": {"f16x3": "fp16 pieces x fp16 pieces, fp32 accumulate (3 products)",
                        "split6": "bf16 pieces, fp32 accumulate (6 products)"}.get(args.precision, args.precision),
@@ -521,6 +574,25 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:  # a secondary leg: reported, the headline line still prints
             yukawa = {"error": f"{type(exc).__name__}: {exc}"}
 
+    # ---- config 3 (p = 10 torus) and config 4 (64-instance batch) ----------
+    torus = batch64 = None
+    if args.precision != "fp32" and not args.no_extra:
+        try:
+            torus = torus_measure(args, dev, min(args.steps, 50), bf16_peak)
+        except Exception as exc:  # a secondary leg: reported, the headline line still prints
+            torus = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            kb = min(args.steps, 10)
+            bv, bms, bpairs, bach, _ = batch64_measure(args, rank, world, dev, kb, 3, False)
+            batch64 = {"value": bv, "unit": UNIT, "ms_per_step": bms / kb, "pairs_per_step": bpairs,
+                       "steps": kb, "precision": args.precision, "workload": BATCH64_DESC,
+                       "roofline": {"bound": "tensor", "achieved": bach, "peak": bf16_peak, "unit": "TFLOP/s",
+                                    "frac": bach / bf16_peak, "flops_per_unit": "2 r^2 per box pair and rhs",
+                                    "time": "whole batch (compression, core and expansion of three operators)"},
+                       "parity": "tests/test_gpu_m2l.py::test_batch64_full_config"}
+        except Exception as exc:
+            batch64 = {"error": f"{type(exc).__name__}: {exc}"}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -538,6 +610,8 @@ def run_ours(args, rank, world, local_rank):
         "stage2": stage2,
         "fmm": fmm,
         "yukawa_per_level": yukawa,
+        "torus4m_p10": torus,
+        "batch64": batch64,
         "parity": "tests/test_gpu_m2l.py: f16x3, split6 and fp32 within 1e-6 relative L2 of the FP64 oracle",
     }
 
@@ -545,6 +619,13 @@ def run_ours(args, rank, world, local_rank):
         cp, cs, cdesc = oracle_sample(wl, 20.0)
         line["cpu_baseline"] = {"value": cp / cs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": cdesc}
+        one = oracle_single_thread(10.0)
+        if one:
+            line["cpu_baseline"]["single_thread"] = {"value": one[0] / one[1], "unit": UNIT, "cores": 1,
+                                                     "sample": one[2]}
+        dp, ds, ddesc = oracle_dense_sample(wl, 10.0)
+        line["cpu_baseline"]["dense"] = {"value": dp / ds, "unit": UNIT, "cores": os.cpu_count(),
+                                         "kind": "oracle, uncompressed M2L", "sample": ddesc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if plan6 is not plan:
@@ -552,23 +633,74 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
 
 
-def run_batch64(args, rank, world, local_rank):
-    """Config 4: 64 ellipsoid instances (N log-uniform 5e4-1e6, depth 3-6,
-    p in {6, 8, 10}, 16 rhs), all M2L levels, one grouped batch replayed from a
-    CUDA graph per step (rank k takes instances 64 k .. 64 k + 63)."""
+def torus_measure(args, dev, steps, peak):
+    """Config 3: the 4,194,304-point torus (R = 1, r = 0.3), depth 6, p = 10,
+    eps = 1e-8 (r = 271, r_pad = 272: the core splits N in two parts), levels
+    2-6 in one apply per step; the core's roofline with 2 r^2 FLOPs per pair."""
+    import numpy as np
     import torch
 
-    import __graft_entry__
+    import synth
+    from paper_1211_2517_gb300 import M2LPlan
 
-    if rank == 0:
-        __graft_entry__.build()
-    if world > 1:
-        torch.distributed.barrier()
+    wl = synth.workload("torus4m_p10", seed=0)
+    tree = wl.tree
+    plan = M2LPlan(wl.p, wl.eps, wl.d, args.precision)
+    pairs = sum(plan.set_level(l, tree.levels[l], tree.r0) for l in LEVELS)
+    q_all = torch.from_numpy(np.concatenate(
+        [synth.random_box_densities(tree.levels[l].shape[0], 1, plan.n, 700 + l)[:, 0] for l in LEVELS])).to(dev)
+    out = torch.empty_like(q_all)
+    lo, hi = min(LEVELS), max(LEVELS)
+    tune = plan.autotune(q_all, lo, hi, reps=3, out=out) if not args.no_autotune else None
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(k):
+        evs = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.apply_levels(q_all, lo, hi, out=out)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    timed(3)
+    ms = timed(steps)
+    plan.profile(True)
+    kp = min(steps, 20)
+    timed(kp)
+    st, _ = plan.profile_read()
+    plan.profile(False)
+    plan.sync()
+    core_ms = st["core"] / kp
+    achieved = 2.0 * plan.r * plan.r * pairs / (core_ms / 1e3) / 1e12
+    res = {"value": pairs * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "pairs_per_step": pairs,
+           "rank_r": plan.r, "r_pad": plan.r_pad, "precision": args.precision,
+           "core_ms_per_step": core_ms, "stage_ms_per_step": {k: v / kp for k, v in st.items()},
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "flops_per_unit": f"2 r^2 = {2 * plan.r * plan.r} per box pair"},
+           "core_variant": {k: tune[k] for k in ("n_chunk", "contiguous", "variant")} if tune else "default",
+           "workload": "torus4m_p10: 4,194,304 points area-uniform on a torus R=1 r=0.3 (seed 0), depth 6, levels "
+                       "2-6, p=10 (n=488), eps=1e-8, d=0.1, 1 rhs, N(0,1) upward-equivalent densities",
+           "parity": "tests/test_gpu_m2l.py::test_full_size_torus_p10_sampled and the p = 10 parity tests"}
+    plan.close()
+    return res
+
+
+def batch64_measure(args, rank, world, dev, steps, warmup, sample_clocks):
+    """Config 4: 64 ellipsoid instances (N log-uniform 5e4-1e6, depth 3-6,
+    p in {6, 8, 10}, 16 rhs), all M2L levels, one grouped batch replayed from a
+    CUDA graph per step (rank k takes instances 64 k .. 64 k + 63).  Returns
+    (units per second over all ranks, slowest rank's ms, units, achieved
+    TFLOP/s, clocks)."""
+    import torch
+
     import synth
     from paper_1211_2517_gb300 import M2LPlan, apply_batch
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
     plans = {p: M2LPlan(p, 1e-7, 0.1, args.precision) for p in (6, 8, 10)}
     items, pairs, flops = [], 0, 0.0
     for j in range(64):
@@ -585,17 +717,18 @@ def run_batch64(args, rank, world, local_rank):
                       "out": torch.empty_like(x)})
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         apply_batch(items, use_graph=True)
     torch.cuda.synchronize()
-    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", ""))
-    sampler = ClockSampler(uuid)
-    sampler.start()
+    sampler = None
+    if sample_clocks:
+        sampler = ClockSampler(str(getattr(torch.cuda.get_device_properties(dev), "uuid", "")))
+        sampler.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     evs = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -605,25 +738,44 @@ def run_batch64(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    value, max_ms, _ = job_throughput(total_ms, pairs, args.steps, dev, world)
+    value, max_ms, units = job_throughput(total_ms, pairs, steps, dev, world)
+    achieved = flops / (total_ms / steps / 1e3) / 1e12
+    for plan in plans.values():
+        plan.close()
+    return value, max_ms, pairs, achieved, clocks
+
+
+BATCH64_DESC = ("batch64: 64 ellipsoid instances (axes U[0.5,2], N log-uniform 5e4-1e6, depth U{3..6}, "
+                "p U{6,8,10}, eps 1e-7, d 0.1), 16 rhs each, N(0,1) upward-equivalent densities, all M2L levels "
+                "in one grouped batch replayed from a CUDA graph")
+
+
+def run_batch64(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    value, max_ms, pairs, achieved, clocks = batch64_measure(args, rank, world, dev, args.steps, args.warmup, True)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    achieved = flops / (total_ms / args.steps / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f16x3": "f16", "fp32": "f32"}.get(args.precision, "bf16"), "data": "synthetic",
-        "config": {"workload": "batch64: 64 ellipsoid instances (axes U[0.5,2], N log-uniform 5e4-1e6, depth "
-                               "U{3..6}, p U{6,8,10}, eps 1e-7, d 0.1), 16 rhs each, N(0,1) upward-equivalent "
-                               "densities, all M2L levels in one grouped batch replayed from a CUDA graph",
-                   "pairs_per_step": pairs, "precision": args.precision,
+        "config": {"workload": BATCH64_DESC, "pairs_per_step": pairs, "precision": args.precision,
                    "l2": "flushed before every timed step (256 MB write)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
                      "frac": achieved / bf16_peak, "traffic": None,
@@ -634,8 +786,6 @@ def run_batch64(args, rank, world, local_rank):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for plan in plans.values():
-        plan.close()
 
 
 def main():
@@ -648,6 +798,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="use the plan's default core variant")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle leg")
     ap.add_argument("--no-yukawa", action="store_true", help="skip the per-level Yukawa leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the torus4m_p10 and batch64 legs")
     ap.add_argument("--workload", choices=("sphere2m_p8", "batch64"), default="sphere2m_p8",
                     help="sphere2m_p8: the headline configuration; batch64: the 64-instance mixed batch")
     args = ap.parse_args()

@@ -6,9 +6,9 @@
  * "A SVD accelerated kernel-independent fast multipole method and its
  * application to BEM" (arXiv 1211.2517):
  *
- *   dense M2L            p^{t,d} = sum_{s in I^t} K(t,s) q^{s,u}        (Eq. eq-m2l)
+ *   dense M2L            p^{t,d} = sum_{s in I^t} K(t,s) q^{s,u}        (Eq. (4))
  *   compressed M2L       p^{t,d} = U~ [ s_l sum_{s in I^t} K~_{t-s} (R~^T q^{s,u}) ]
- *                                                     (Eqs. eq-cmpM2Ls, evalcmp1)
+ *                                                     (Eqs. (13), (14))
  *
  * with K(t,s)_ij = G(x_i^{t,d}, y_j^{s,u}), G = 1/(4 pi |x-y|) (Sec. 4), the
  * target's downward check surface x^{t,d} and the source's upward equivalent
@@ -141,7 +141,7 @@ int kifmm_m2l_destroy(kifmm_m2l_plan plan);
 /* Rank introspection: *r = retained rank, *r_pad = r rounded up to a
  * multiple of 16 (device layout; the extra columns are zero), *n = surface
  * points.  Any output pointer may be NULL.
- * r is the rank kept by the truncation of Sec. 3.1 (Eqs. eq-kfat, fat). */
+ * r is the rank kept by the truncation of Sec. 3.1 (Eqs. (8), (10)). */
 int kifmm_m2l_plan_rank(kifmm_m2l_plan plan, int* r, int* r_pad, int* n);
 
 /* ---- per-level state --------------------------------------------------- */
@@ -164,7 +164,7 @@ int kifmm_m2l_level_pairs(kifmm_m2l_plan plan, int instance, int level, int64_t*
 
 /* ---- the translation --------------------------------------------------- */
 
-/* Compressed M2L of one registered level (Eq. evalcmp1 restricted to M2L):
+/* Compressed M2L of one registered level (Eq. (14) restricted to M2L):
  *   q~ = R~^T q_up ;  p~^t = s_l sum_{s in I^t} K~_{t-s} q~^s ;
  *   p_down = beta * p_down + U~ p~
  * q_up, p_down: DEVICE float32 [n_boxes][nrhs][n]; they must not overlap.
@@ -180,7 +180,7 @@ int kifmm_m2l_apply(kifmm_m2l_plan plan, int instance, int level, int nrhs,
  * applied as the core of the reversed offset, K~_o^T = K~_{-o} (which holds
  * to FP64 rounding because K_o^T = K_{-o} and R~ = U~; checked at
  * precompute).  Same layouts and rules as kifmm_m2l_apply.
- * The transpose of Eq. evalcmp1 (Sec. 3.1), formed with K~_o^T = K~_{-o}. */
+ * The transpose of Eq. (14) (Sec. 3.1), formed with K~_o^T = K~_{-o}. */
 int kifmm_m2l_apply_adjoint(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                             const float* pbar_down, float* qbar_up, float beta, void* stream);
 
@@ -199,7 +199,7 @@ int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int 
                            const float* q_up, float* p_down, float beta, void* stream);
 
 /* Adjoint of kifmm_m2l_apply_levels (see kifmm_m2l_apply_adjoint).
- * The transpose of Eq. evalcmp1 (Sec. 3.1) over several levels. */
+ * The transpose of Eq. (14) (Sec. 3.1) over several levels. */
 int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                                    const float* pbar_down, float* qbar_up, float beta, void* stream);
 
@@ -233,7 +233,7 @@ typedef struct kifmm_m2l_batch_item {
  * plan must not write overlapping p_down buffers. */
 int kifmm_m2l_apply_batch(int n_items, const kifmm_m2l_batch_item* items, int use_graph, void* stream);
 
-/* Uncompressed M2L (Eq. eq-m2l), the baseline the compression is compared
+/* Uncompressed M2L (Eq. (4)), the baseline the compression is compared
  * with:  p_down = beta * p_down + s_l sum_{s in I^t} K_{t-s} q^s  with the
  * FP32 unit-level K_o (formed on first use; 316 n^2 floats of device
  * memory).  Always FP32 CUDA-core arithmetic, accumulated with atomic adds
@@ -270,14 +270,20 @@ int kifmm_m2l_set_wait_limit(kifmm_m2l_plan plan, unsigned long long ns);
  * instead: applications whose memory manager reserved the device up front,
  * solvers held to a fixed memory budget, and latency-critical loops that
  * cannot take the device-wide synchronisation of cudaMalloc / cudaFree.
- * It computes what kifmm_m2l_apply computes (same layouts, beta rule,
- * precision mode and kernels) and calls no allocating routine.  Its
+ * It computes what kifmm_m2l_apply computes (same layouts, beta rule and
+ * precision modes, except KIFMM_PREC_F16X3, which it rejects with
+ * KIFMM_ERR_UNSUPPORTED) and calls no allocating routine.  The core runs
+ * the plan's core variant (the one kifmm_m2l_autotune chose, if any); the
+ * compression and expansion split the FP32 rows into BF16 pieces inside
+ * their GEMMs instead of through the separate split kernel, which saves the
+ * split buffer.  Its
  * scratch is one static device array of KIFMM_NOALLOC_SCRATCH_BYTES
  * (64 MiB) that every GPU which loads this part of the library keeps until
  * the process exits.
- *  - The first call on a device looks up the array's device address
- *    (once per device, with that device current); make that first call
- *    before any stream capture.
+ *  - The first call on a device (and the first after that device's
+ *    context was destroyed and created again) looks up the array's device
+ *    address, with that device current; make that first call before any
+ *    stream capture.
  *  - A level and nrhs whose scratch would not fit is rejected with
  *    KIFMM_ERR_INVALID_ARG before anything is launched; the message gives
  *    the bytes needed.  The need is about n_boxes * nrhs * r_pad bytes
@@ -288,7 +294,7 @@ int kifmm_m2l_set_wait_limit(kifmm_m2l_plan plan, unsigned long long ns);
  *    overlaps, e.g. on two streams at once, race and give wrong results:
  *    serialise them.
  * Same argument rules as kifmm_m2l_apply.
- * Computes Eq. evalcmp1 (Sec. 3.1) like kifmm_m2l_apply. */
+ * no passage of the paper (an allocation-free variant of kifmm_m2l_apply). */
 #define KIFMM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                             const float* q_up, float* p_down, float beta, void* stream);
@@ -296,9 +302,9 @@ int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nr
 /* ---- stage 2: per-offset low-rank cores (Sec. 3.2) ----------------------- */
 
 /* Switch the plan's core to the second compression stage of Sec. 3.2
- * (Eq. eq-lra): each unit-level core is factored in FP64 on the host,
+ * (Eq. (17)): each unit-level core is factored in FP64 on the host,
  * K~_o = U_o S_o Q_o^T, and truncated to the k_o singular values with
- * sigma >= eps2 * sigma_0(K_fat), eps2 = c2 * eps / r (Eq. eq-vareps2, with
+ * sigma >= eps2 * sigma_0(K_fat), eps2 = c2 * eps / r (Eq. (18), with
  * eps = the plan's eps_1 and r its rank); then
  *   p~^t += s_l Uhat_o (Vhat_o q~^s),  Uhat_o = U_o[:, :k_o] (r x k_o),
  *                                      Vhat_o = S_o Q_o^T restricted (k_o x r),
@@ -315,14 +321,14 @@ int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2);
 
 /* The per-offset ranks k_o of stage 2 (k[316], HOST memory, offsets in the
  * lexicographic order above).  KIFMM_ERR_STATE when stage 2 is off.
- * Stage 2 is Sec. 3.2 (Eqs. eq-lra, eq-vareps2). */
+ * Stage 2 is Sec. 3.2 (Eqs. (17), (18)). */
 int kifmm_m2l_stage2_ranks(kifmm_m2l_plan plan, int* k);
 
 /* Host-only stage 2 (no GPU needed): the FP64 precompute of
  * kifmm_m2l_precompute followed by the factoring of kifmm_m2l_set_stage2;
  * writes the 316 ranks to k and, if core is not NULL, the truncated cores
  * Uhat_o Vhat_o to core[316][r][r] (row-major, r from kifmm_m2l_factors_host).
- * Stage 2 is Sec. 3.2 (Eqs. eq-lra, eq-vareps2). */
+ * Stage 2 is Sec. 3.2 (Eqs. (17), (18)). */
 int kifmm_m2l_stage2_host(const kifmm_m2l_params* params, double c2, int* k, double* core);
 
 /* ---- tracing ------------------------------------------------------------ */
@@ -393,14 +399,14 @@ int kifmm_m2l_autotune(kifmm_m2l_plan plan, int instance, int level_lo, int leve
 /* ---- complete potential evaluation for point sources ------------------- */
 
 /* The potential of a point cloud on itself, p_i = sum_{j != i} G(x_i, x_j) q_j
- * (Eq. eq_eval), evaluated as in the complete algorithm of Sec. 4 with the
+ * (Eq. (1)), evaluated as in the complete algorithm of Sec. 4 with the
  * compressed upward and downward passes of Sec. 3.3:
  *   near field  direct sums over the leaves sharing at least one vertex
  *               with the point's leaf, that leaf included (Sec. 2.1);
  *   far field   S~ = R~^T S at the leaves, M~ = R~^T M R~ up the tree, the
  *               plan's compressed M2L cores on levels 2..depth, L~ = U~^T L U~
- *               down the tree, T~ = T U~ at the leaves (Eqs. eq-s2m ..
- *               eq-l2t with Sec. 3.3's operators).
+ *               down the tree, T~ = T U~ at the leaves (Eqs. (2) ..
+ *               (6) with Sec. 3.3's operators).
  * S, M, L, T are the KIFMM check / equivalent surface translations of
  * Sec. 2.1: upward equivalent and downward check surfaces at half-width
  * (1+d) h, upward check and downward equivalent surfaces at (3-2d) h; the
@@ -440,10 +446,10 @@ int kifmm_fmm_create(kifmm_m2l_plan plan, int64_t n_points, const double* points
  * Asynchronous on `stream`; calls on one tree (and on trees of one plan)
  * must be serialised.  Errors: KIFMM_ERR_INVALID_ARG (NULL, parts out of
  * 1..3), KIFMM_ERR_CUDA.
- * Eq. eq_eval by the complete algorithm of Sec. 4 with the compressed passes of Sec. 3.3. */
+ * Eq. (1) by the complete algorithm of Sec. 4 with the compressed passes of Sec. 3.3. */
 int kifmm_fmm_evaluate(kifmm_fmm fmm, const float* q, float* potential, int parts, void* stream);
 
-/* Double layer (Sec. 4, Eq. eq-doubles2m): with normals set, the sources are
+/* Double layer (Sec. 4, Eq. (26)): with normals set, the sources are
  * dipoles and evaluate computes
  *   p_i = sum_{j != i} dG(x_i, x_j)/dn(x_j) q_j,
  *   dG(x, y)/dn(y) = n(y) . (x - y) / (4 pi |x - y|^3),
@@ -478,7 +484,7 @@ int kifmm_fmm_destroy(kifmm_fmm fmm);
  * U: [n][r] row-major retained left basis U~ (or NULL);
  * C: [316][r][r] row-major unit-level cores K~_o (or NULL).
  * Call once with the arrays NULL to learn n and r.
- * The factors of Sec. 3.1 (Eqs. eq-kfat, fat, eq-cmpM2Ls). */
+ * The factors of Sec. 3.1 (Eqs. (8), (10), (13)). */
 int kifmm_m2l_factors_host(const kifmm_m2l_params* params, int* n, int* r,
                            double* sigma, double* U, double* C);
 

@@ -13,16 +13,16 @@ Modules:
   geometry  -- surfaces (Sec. 2.1), the 316 offsets (Sec. 3.1), interaction
                lists (Sec. 2.1), the Laplace kernel and its double-layer
                normal derivative (Sec. 4), the Yukawa kernel.
-  m2l       -- dense M2L (Eq. eq-m2l), the fat/thin SVDs and the truncated
-               compressed M2L (Eqs. eq-kfat, fat, thin, eq-cmpM2Ls, evalcmp1),
+  m2l       -- dense M2L (Eq. (4)), the fat/thin SVDs and the truncated
+               compressed M2L (Eqs. (8), (10), (11), (13), (14)),
                level scaling by homogeneity (Sec. 3.1) or per-level factors
                for a non-homogeneous kernel, the adjoint, the stage-2
-               per-offset low-rank factors (Eq. eq-lra).
-  upward    -- S2M / M2M (Eqs. eq-s2m, eq-m2m) to make realistic M2L inputs,
-               and direct summation (Eq. eq_eval) for brute-force checks.
+               per-offset low-rank factors (Eq. (17)).
+  upward    -- S2M / M2M (Eqs. (2), (3)) to make realistic M2L inputs,
+               and direct summation (Eq. (1)) for brute-force checks.
   fmm       -- the complete evaluation for point sources: near field (S2T),
-               far field through S2M, M2M, M2L, L2L, L2T (Eqs. eq-s2m ..
-               eq-tran0), uncompressed and with Sec. 3.3's compressed
+               far field through S2M, M2M, M2L, L2L, L2T (Eqs. (2) ..
+               (7)), uncompressed and with Sec. 3.3's compressed
                operators S~, M~, L~, T~; direct summation; dipole sources
                (the double layer of Sec. 4).
 

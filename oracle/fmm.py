@@ -2,10 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The potential at every point of a cloud from every other point (Eq. eq_eval)
+The potential at every point of a cloud from every other point (Eq. (1))
 is split as in Sec. 2.2 and the complete algorithm of Sec. 4: the near field
 by direct summation (S2T) and the far field by S2M, M2M, M2L, L2L, L2T
-(Eqs. eq-s2m .. eq-l2t, composed as Eq. eq-tran0).  Sec. 3.3 compresses the
+(Eqs. (2) .. (6), composed as Eq. (7)).  Sec. 3.3 compresses the
 upward and downward passes with the M2L bases: S~ = R~^T S, M~ = R~^T M R~,
 L~ = U~^T L U~, T~ = T U~, and the M2L then maps q~ to p~ with the cores
 K~_o alone.  Both forms are here: ``fmm_uncompressed`` forms every operator
@@ -30,7 +30,7 @@ these are the KIFMM ones it cites):
   potentials at the leaf's points.
 * The near field of a leaf is every leaf sharing at least one vertex with it,
   itself included (Sec. 2.1); a point does not act on itself.
-* Double layer (Sec. 4, Eq. eq-doubles2m): with normals n(y_j) given, the
+* Double layer (Sec. 4, Eq. (26)): with normals n(y_j) given, the
   sources are dipoles of density q_j, and G is replaced by dG/dn(y) in S2T
   and in the leaf check potentials (the first step of S2M); the equivalent
   densities and every later step stay single layer.
@@ -77,7 +77,7 @@ def octant(ijk: np.ndarray) -> np.ndarray:
 
 
 def m2m_matrix(p: int, d: float, hp: float, c: int, rcond: float = FMM_RCOND) -> np.ndarray:
-    """M for the child in octant c of a parent of half-width hp (Eq. eq-m2m):
+    """M for the child in octant c of a parent of half-width hp (Eq. (3)):
     child upward equivalent densities -> parent upward equivalent densities."""
     hc = 0.5 * hp
     x = geo.surface_points(p, np.zeros(3), (3.0 - 2.0 * d) * hp)
@@ -86,7 +86,7 @@ def m2m_matrix(p: int, d: float, hp: float, c: int, rcond: float = FMM_RCOND) ->
 
 
 def l2l_matrix(p: int, d: float, hp: float, c: int, rcond: float = FMM_RCOND) -> np.ndarray:
-    """L for the child in octant c of a parent of half-width hp (Eq. eq-l2l):
+    """L for the child in octant c of a parent of half-width hp (Eq. (5)):
     parent downward check potentials -> child downward check potentials."""
     hc = 0.5 * hp
     x = geo.surface_points(p, child_signs()[c] * hc, (1.0 + d) * hc)
@@ -148,11 +148,11 @@ def near_leaves(tree, b: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# direct summation and near field (Eq. eq_eval)
+# direct summation and near field (Eq. (1))
 # ---------------------------------------------------------------------------
 def source_kernel(x, pts, src, normals=None) -> np.ndarray:
     """Kernel from the sources pts[src] to the points x: G, or dG/dn(y) with
-    the sources' normals for a double layer. Eq. eq_eval's kernel; the double layer of Sec. 4, Eq. eq-doubles2m."""
+    the sources' normals for a double layer. Eq. (1)'s kernel; the double layer of Sec. 4, Eq. (26)."""
     if normals is None:
         return geo.laplace_kernel(x, pts[src])
     return geo.laplace_double_layer_kernel(x, pts[src], np.asarray(normals, dtype=np.float64)[src])
@@ -160,7 +160,7 @@ def source_kernel(x, pts, src, normals=None) -> np.ndarray:
 
 def direct_sum(points, q, targets=None, normals=None) -> np.ndarray:
     """p_i = sum_{j != i} G(x_i, x_j) q_j for the listed targets (all by
-    default); with ``normals``, dG(x_i, x_j)/dn(x_j) in place of G. Eq. eq_eval."""
+    default); with ``normals``, dG(x_i, x_j)/dn(x_j) in place of G. Eq. (1)."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     idx = np.arange(pts.shape[0]) if targets is None else np.asarray(targets)
@@ -193,11 +193,11 @@ def near_field(tree, points, q, normals=None) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# uncompressed far field (Eqs. eq-s2m .. eq-l2t)
+# uncompressed far field (Eqs. (2) .. (6))
 # ---------------------------------------------------------------------------
 def _upward(tree, points, p, d, q, rcond, normals=None):
     """Upward equivalent densities of levels 2..depth (S2M, M2M), every
-    operator formed at the box's own half-width. Eqs. eq-s2m, eq-m2m."""
+    operator formed at the box's own half-width. Eqs. (2), (3)."""
     pts = np.asarray(points, dtype=np.float64)
     L = tree.depth
     order, bounds = leaf_points(tree)
@@ -221,7 +221,7 @@ def _upward(tree, points, p, d, q, rcond, normals=None):
 
 
 def fmm_uncompressed_far(tree, points, p: int, d: float, q, rcond: float = FMM_RCOND, normals=None) -> np.ndarray:
-    """Far-field potential at every point: T L K M S q (Eq. eq-tran0) summed
+    """Far-field potential at every point: T L K M S q (Eq. (7)) summed
     over the levels, each translating matrix formed at its box size."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
@@ -256,7 +256,7 @@ def fmm_uncompressed_far(tree, points, p: int, d: float, q, rcond: float = FMM_R
 def leaf_check_potentials(tree, points, p: int, d: float, q, normals=None) -> np.ndarray:
     """K(x^u, points in the leaf) q for every leaf, [B_depth, n]: the part of
     S that depends on the points (double-layer kernel with ``normals``).
-    Eq. eq-s2m (its first step); the double layer of Eq. eq-doubles2m."""
+    Eq. (2) (its first step); the double layer of Eq. (26)."""
     pts = np.asarray(points, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     L = tree.depth
@@ -285,7 +285,7 @@ def compressed_upward(tree, points, f, ops: PassOperators, p: int, d: float, q, 
 
 
 def compressed_m2l(box_ijk, level: int, r0: float, f, qt) -> np.ndarray:
-    """p~^t = (r0/2**l)^(-1) sum_{s in I^t} K~_{t-s} q~^s (Eq. evalcmp1 between
+    """p~^t = (r0/2**l)^(-1) sum_{s in I^t} K~_{t-s} q~^s (Eq. (14) between
     the compressed vectors)."""
     tg, sr, ok = geo.interaction_lists(box_ijk)
     pt = np.zeros((np.asarray(box_ijk).shape[0], f.r))
@@ -311,7 +311,7 @@ def compressed_downward(tree, f, ops: PassOperators, qt: dict) -> dict:
 
 def leaf_l2t(tree, points, p: int, d: float, e_leaf) -> np.ndarray:
     """Potential at every point from its leaf's downward equivalent densities
-    e_leaf [B_depth, n] placed on y^d. Eq. eq-l2t (Sec. 2.2)."""
+    e_leaf [B_depth, n] placed on y^d. Eq. (6) (Sec. 2.2)."""
     pts = np.asarray(points, dtype=np.float64)
     L = tree.depth
     h = tree.halfwidth(L)

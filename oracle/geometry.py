@@ -38,7 +38,7 @@ def yukawa_kernel(x: np.ndarray, y: np.ndarray, kappa: float) -> np.ndarray:
 def laplace_double_layer_kernel(x: np.ndarray, y: np.ndarray, n: np.ndarray) -> np.ndarray:
     """dG(x, y)/dn(y) = n(y) . (x - y) / (4 pi |x - y|^3): the double-layer
     kernel that replaces G in S2T and in the first step of S2M for a double
-    layer integral (Sec. 4, Eq. eq-doubles2m).  Gradient of G = 1/(4 pi |x - y|)
+    layer integral (Sec. 4, Eq. (26)).  Gradient of G = 1/(4 pi |x - y|)
     with respect to y, projected on the normal n(y) at the source.
 
     ``x`` [m,3], ``y`` [k,3], ``n`` [k,3] -> [m,k] float64.

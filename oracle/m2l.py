@@ -41,7 +41,7 @@ def kernel_matrix(x, y, kappa: float = 0.0) -> np.ndarray:
 def m2l_matrix_geometric(p: int, d: float, centre_t, centre_s, h: float, kappa: float = 0.0) -> np.ndarray:
     """K_ij = G(x_i, y_j), x on the target's downward check surface and y on
     the source's upward equivalent surface, both at half-width (1+d) h
-    (Eq. eq-m2l with the surfaces of Sec. 2.1).  Formed from coordinates."""
+    (Eq. (4) with the surfaces of Sec. 2.1).  Formed from coordinates."""
     x = geo.surface_points(p, centre_t, (1.0 + d) * h)
     y = geo.surface_points(p, centre_s, (1.0 + d) * h)
     return kernel_matrix(x, y, kappa)
@@ -49,7 +49,7 @@ def m2l_matrix_geometric(p: int, d: float, centre_t, centre_s, h: float, kappa: 
 
 def unit_m2l_matrices(p: int, d: float, kappa: float = 0.0, h: float = 1.0) -> np.ndarray:
     """The 316 translation matrices K_o of boxes of half-width h (unit by
-    default) with centres 2 o h apart, [316, n, n]. Eq. eq-m2l; Sec. 3.1 (the 316 matrices)."""
+    default) with centres 2 o h apart, [316, n, n]. Eq. (4); Sec. 3.1 (the 316 matrices)."""
     offs = geo.m2l_offsets()
     zero = np.zeros(3)
     return np.stack([m2l_matrix_geometric(p, d, 2.0 * h * o.astype(np.float64), zero, h, kappa)
@@ -61,10 +61,10 @@ def unit_m2l_matrices(p: int, d: float, kappa: float = 0.0, h: float = 1.0) -> n
 # ---------------------------------------------------------------------------
 @dataclass
 class SvdFactors:
-    """Truncated factors of Eq. eq-cmpM2Ls at unit half-width.
+    """Truncated factors of Eq. (13) at unit half-width.
 
-    U   [n, r]   left basis  (columns of U of the fat SVD, Eq. fat)
-    R   [n, r]   right basis (columns of R of the thin SVD, Eq. thin)
+    U   [n, r]   left basis  (columns of U of the fat SVD, Eq. (10))
+    R   [n, r]   right basis (columns of R of the thin SVD, Eq. (11))
     C   [316, r, r]  compressed cores  K~_o = U~^T K_o R~
     sigma        singular values of K_fat (all n)
     lam          singular values of K_thin (all n)
@@ -112,10 +112,10 @@ def _fix_signs(m: np.ndarray) -> np.ndarray:
 
 def svd_factors(p: int, d: float, eps: float, r: int | None = None, kappa: float = 0.0,
                 h: float | None = None) -> SvdFactors:
-    """Fat and thin SVDs, truncation, compressed cores (Eqs. eq-kfat..eq-cmpM2Ls).
+    """Fat and thin SVDs, truncation, compressed cores (Eqs. (8) .. (13)).
 
-    K_fat = [K_1 ... K_316] = U Sigma [V_1^T ... V_316^T]   (Eq. fat)
-    K_thin = [K_1; ...; K_316] = [Q_1; ...; Q_316] Lambda R^T  (Eq. thin)
+    K_fat = [K_1 ... K_316] = U Sigma [V_1^T ... V_316^T]   (Eq. (10))
+    K_thin = [K_1; ...; K_316] = [Q_1; ...; Q_316] Lambda R^T  (Eq. (11))
     U~, R~ keep the columns whose singular value is >= eps * Sigma_00, and
     K~_o = U~^T K_o R~.  ``r`` overrides the rank when given.  With ``h``
     (needed for kappa > 0) the matrices are those of boxes of half-width h.
@@ -166,7 +166,7 @@ def _as3(q):
 
 def m2l_dense(box_ijk, level: int, r0: float, p: int, d: float, q_up, centre=None,
               targets=None, kappa: float = 0.0) -> np.ndarray:
-    """Uncompressed M2L, p^{t,d} = sum_{s in I^t} K(t,s) q^{s,u} (Eq. eq-m2l).
+    """Uncompressed M2L, p^{t,d} = sum_{s in I^t} K(t,s) q^{s,u} (Eq. (4)).
 
     Every pair's K(t,s)_ij = G(x_i^t, y_j^s) is formed from that pair's own
     surface coordinates at this level (no homogeneity shortcut); pairs are
@@ -199,11 +199,13 @@ def m2l_dense(box_ijk, level: int, r0: float, p: int, d: float, q_up, centre=Non
     return out[:, 0, :] if squeeze else out
 
 
-def m2l_dense_unit(box_ijk, level: int, r0: float, K: np.ndarray, q_up) -> np.ndarray:
+def m2l_dense_unit(box_ijk, level: int, r0: float, K: np.ndarray, q_up, lists=None) -> np.ndarray:
     """Uncompressed M2L through the unit matrices and level scaling
-    (Eq. eq-m2l with Sec. 3.1's homogeneity), grouped by offset."""
+    (Eq. (4) with Sec. 3.1's homogeneity), grouped by offset.  `lists`
+    (target, source, offset arrays of interaction_lists) may restrict the
+    pairs, e.g. to a sample of the targets."""
     q, squeeze = _as3(q_up)
-    tg, sr, ok = geo.interaction_lists(box_ijk)
+    tg, sr, ok = geo.interaction_lists(box_ijk) if lists is None else lists
     out = np.zeros_like(q)
     for k in np.unique(ok):
         sel = ok == k
@@ -213,7 +215,7 @@ def m2l_dense_unit(box_ijk, level: int, r0: float, K: np.ndarray, q_up) -> np.nd
 
 
 def m2l_svd(box_ijk, level: int, r0: float, f: SvdFactors, q_up, lists=None) -> np.ndarray:
-    """Compressed M2L, Eq. evalcmp1 restricted to the translation:
+    """Compressed M2L, Eq. (14) restricted to the translation:
 
         q~^s = R~^T q^{s,u}
         p~^t = (r0/2**l)^(-1) sum_{s in I^t} K~_{t-s} q~^s
@@ -235,7 +237,7 @@ def m2l_svd(box_ijk, level: int, r0: float, f: SvdFactors, q_up, lists=None) -> 
 
 def m2l_svd_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, pbar, lists=None) -> np.ndarray:
     """Transpose of ``m2l_svd``: q-bar^s = s_l R~ sum_{t: s in I^t} K~_{t-s}^T U~^T p-bar^t.
-    The transpose of Eq. evalcmp1 (Sec. 3.1)."""
+    The transpose of Eq. (14) (Sec. 3.1)."""
     pb, squeeze = _as3(pbar)
     tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
     pt = pb @ f.U                                    # [B, nrhs, r]
@@ -253,7 +255,7 @@ def m2l_svd_targets(box_ijk, level: int, r0: float, f: SvdFactors, q_up, targets
 
     For sampled checks at sizes where the full oracle is too slow.
     Returns [len(targets), nrhs, n].
-    Eq. evalcmp1 (Sec. 3.1)."""
+    Eq. (14) (Sec. 3.1)."""
     q, _ = _as3(q_up)
     box_ijk = np.asarray(box_ijk, dtype=np.int64)
     index = {tuple(b): i for i, b in enumerate(box_ijk)}
@@ -279,7 +281,7 @@ def m2l_svd_targets(box_ijk, level: int, r0: float, f: SvdFactors, q_up, targets
 def stage2_factors(f: SvdFactors, eps2: float):
     """K~_o = U_o S_o Q_o^T, drop singular values < eps2 * ||K_fat||_2, and
     return (Uhat_o [r,k_o], Vhat_o = Shat_o Qhat_o^T [k_o,r]) per offset
-    (Eq. eq-lra)."""
+    (Eq. (17))."""
     out = []
     thr = eps2 * f.sigma[0]
     for Ck in f.C:
@@ -290,7 +292,7 @@ def stage2_factors(f: SvdFactors, eps2: float):
 
 
 def m2l_svd_stage2(box_ijk, level: int, r0: float, f: SvdFactors, s2, q_up, lists=None) -> np.ndarray:
-    """Compressed M2L with the second stage of Sec. 3.2 (Eq. eq-lra): every
+    """Compressed M2L with the second stage of Sec. 3.2 (Eq. (17)): every
     core K~_o is replaced by its truncation Uhat_o Vhat_o (``s2`` from
     ``stage2_factors``), applied as two products:
 
@@ -312,7 +314,7 @@ def m2l_svd_stage2(box_ijk, level: int, r0: float, f: SvdFactors, s2, q_up, list
 
 def m2l_svd_stage2_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, s2, pbar, lists=None) -> np.ndarray:
     """Transpose of ``m2l_svd_stage2``: q-bar~^s = s_l sum_t Vhat_o^T (Uhat_o^T p-bar~^t).
-    The transpose of Eq. eq-lra's products (Sec. 3.2)."""
+    The transpose of Eq. (17)'s products (Sec. 3.2)."""
     pb, squeeze = _as3(pbar)
     tg, sr, ok = lists if lists is not None else geo.interaction_lists(box_ijk)
     pt = pb @ f.U
@@ -327,10 +329,10 @@ def m2l_svd_stage2_adjoint(box_ijk, level: int, r0: float, f: SvdFactors, s2, pb
 
 
 def eps2_from_c2(c2: float, eps1: float, r: int) -> float:
-    """eps2 = C2 eps1 / p~ with p~ the compressed dimension (Eq. eq-vareps2)."""
+    """eps2 = C2 eps1 / p~ with p~ the compressed dimension (Eq. (18))."""
     return c2 * eps1 / r
 
 
 def eps1_from_c1(c1: float, n_levels: int) -> float:
-    """eps1 = C1 2^(-L) / L (Eq. eq-vareps1)."""
+    """eps1 = C1 2^(-L) / L (Eq. (16))."""
     return c1 * 2.0 ** (-n_levels) / n_levels

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 The M2L translation consumes upward equivalent densities q^{s,u}.  To feed
 it realistic values, this module runs the KIFMM upward pass of Sec. 2.2
-(Eqs. eq-s2m, eq-m2m) on a point cloud.  Sec. 2.1 puts the upward
+(Eqs. (2), (3)) on a point cloud.  Sec. 2.1 puts the upward
 equivalent surface at half-width (1+d) h and the upward check surface at
 (3-2d) h.  The paper calls S and M "translating matrices" without giving
 their form; the reading used here is the KIFMM one: check potentials are
@@ -30,7 +30,7 @@ def check_to_equivalent(p: int, d: float, h: float, rcond: float = PINV_RCOND) -
 
 
 def s2m(tree, points: np.ndarray, p: int, d: float, q_points: np.ndarray) -> np.ndarray:
-    """Leaf upward equivalent densities q^{B,u} = S q (Eq. eq-s2m).
+    """Leaf upward equivalent densities q^{B,u} = S q (Eq. (2)).
 
     Check potentials on the leaf's upward check surface from the points
     inside the leaf, then the check-to-equivalent solve.  [B_leaf, n].
@@ -55,7 +55,7 @@ def s2m(tree, points: np.ndarray, p: int, d: float, q_points: np.ndarray) -> np.
 
 
 def m2m(tree, p: int, d: float, q_child: np.ndarray, level: int) -> np.ndarray:
-    """Parent densities at ``level`` from children at level+1 (Eq. eq-m2m).
+    """Parent densities at ``level`` from children at level+1 (Eq. (3)).
 
     Check potentials on the parent's upward check surface produced by the
     children's upward equivalent densities, then the check-to-equivalent
@@ -80,7 +80,7 @@ def m2m(tree, p: int, d: float, q_child: np.ndarray, level: int) -> np.ndarray:
 
 
 def upward_pass(tree, points: np.ndarray, p: int, d: float, q_points: np.ndarray) -> dict:
-    """Upward equivalent densities for every level 2..depth, {level: [B_l, n]}. Eqs. eq-s2m, eq-m2m (Sec. 2.2)."""
+    """Upward equivalent densities for every level 2..depth, {level: [B_l, n]}. Eqs. (2), (3) (Sec. 2.2)."""
     out = {tree.depth: s2m(tree, points, p, d, q_points)}
     for level in range(tree.depth - 1, 1, -1):
         out[level] = m2m(tree, p, d, out[level + 1], level)
@@ -90,7 +90,7 @@ def upward_pass(tree, points: np.ndarray, p: int, d: float, q_points: np.ndarray
 def direct_far_field(tree, points: np.ndarray, level: int, p: int, d: float, q_points: np.ndarray,
                      targets) -> np.ndarray:
     """Brute force: potential at each target box's downward check points from
-    every point in the boxes of its interaction list (Eq. eq_eval restricted
+    every point in the boxes of its interaction list (Eq. (1) restricted
     to I^t).  [len(targets), n]."""
     box_ijk = tree.levels[level].astype(np.int64)
     tg, sr, _ = geo.interaction_lists(box_ijk)

@@ -12,7 +12,7 @@
 // Device, per evaluate, in stream order:
 //   gather     densities into the leaf-ordered point array        (CUDA cores)
 //   check      h K(x^u, points) q for every leaf (double layer: h dG/dn(y),
-//              the first step of S2M, Eq. eq-doubles2m)           (CUDA cores)
+//              the first step of S2M, Eq. (26))           (CUDA cores)
 //   S~         q~_leaf = Ws (h K q): split + identity-row GEMM    (tensor cores)
 //   M~         level by level, children -> parents: gather GEMM over the
 //              8 octant groups with FP32 reductions, then split   (tensor cores)

@@ -1,4 +1,4 @@
-// The core products of the compressed M2L (Sec. 3.1, Eq. evalcmp1:
+// The core products of the compressed M2L (Sec. 3.1, Eq. (14):
 // p~^t += s_l K~_o q~^s over every box pair (t, s = t - o)), with the
 // scatter into p~ handed to the TMA unit.
 //

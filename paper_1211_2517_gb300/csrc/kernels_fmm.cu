@@ -2,7 +2,7 @@
 // density gather, the leaf check potentials that feed S~, and the leaf sums
 // of L2T and of the near field (S2T).  G = 1 / (4 pi |x - y|) (Sec. 4);
 // for a double layer, dG/dn(y) = n(y) . (x - y) / (4 pi |x - y|^3) in the
-// check potentials and the near field (Sec. 4, Eq. eq-doubles2m), with the
+// check potentials and the near field (Sec. 4, Eq. (26)), with the
 // densities in the hi words' w and the normals n_j as two FP32 words.
 //
 // Points live in leaf order in leaf units: s = (x - c) / h with c the

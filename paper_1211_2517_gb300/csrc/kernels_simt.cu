@@ -4,7 +4,7 @@
 //                    box pairs, a row gather from the sources and an atomic
 //                    scatter-add into the targets: the FP32 core
 //                    sum_o K~_o q~ and the dense baseline sum_o K_o q
-//                    (Eq. eq-m2l).
+//                    (Eq. (4)).
 //  * split_bf16      FP32 -> sum of BF16 pieces for the tensor-core modes.
 //
 // Tiling: a 256-thread block computes a 128 x 128 output tile in K-steps of

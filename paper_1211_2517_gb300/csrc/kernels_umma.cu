@@ -1,6 +1,6 @@
 // tcgen05 (5th-generation tensor core) kernels of the compressed M2L.
 //
-// One kernel template computes the three products of Eq. evalcmp1 restricted
+// One kernel template computes the three products of Eq. (14) restricted
 // to M2L, each as a split-BF16 GEMM with FP32 accumulation in tensor memory:
 //
 //   compress  q~ = R~^T q        A = FP32 rows of q, split to BF16 pieces
@@ -1226,7 +1226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 
 // ---------------------------------------------------------------------------
-// Stage-2 core (Sec. 3.2, Eq. eq-lra).  With K~_o = Uhat_o Vhat_o (rank k_o,
+// Stage-2 core (Sec. 3.2, Eq. (17)).  With K~_o = Uhat_o Vhat_o (rank k_o,
 // rounded up to k16 <= 96), a tile's product is two skinny GEMMs:
 //   T = Q~_rows Vhat_o^T   (128 x k16, K = r_pad)     split products, hi/lo
 //   P = T Uhat_o^T         (128 x r_pad, K = k16)     split products

@@ -27,7 +27,7 @@ int offset_index(int ox, int oy, int oz);
 // Points of the [-1,1]^3 cube boundary (lexicographic grid order), [n][3].
 std::vector<double> unit_surface(int p);
 
-// Entry (i, j) of the unit-level translation matrix K_o (Sec. 2.2 Eq. eq-m2l,
+// Entry (i, j) of the unit-level translation matrix K_o (Sec. 2.2 Eq. (4),
 // surfaces of Sec. 2.1): g(|2 o + (1+d)(u_i - u_j)|) with g(r) = exp(-kh r) /
 // (4 pi r); kh = 0 is the Laplace kernel, kh = kappa h the Yukawa kernel at
 // box half-width h (times h).
@@ -52,9 +52,9 @@ int compute_factors(const kifmm_m2l_params& prm, Factors& f);
 // The same without the in-process memo.
 int compute_factors_uncached(const kifmm_m2l_params& prm, Factors& f);
 
-// Stage-2 per-offset factors (Sec. 3.2, Eq. eq-lra): K~_o = U_o S_o Q_o^T,
+// Stage-2 per-offset factors (Sec. 3.2, Eq. (17)): K~_o = U_o S_o Q_o^T,
 // keep the k_o singular values >= eps2 * sigma_0(K_fat) with
-// eps2 = c2 * eps1 / r (Eq. eq-vareps2); Uhat_o = U_o[:, :k_o] (r x k_o),
+// eps2 = c2 * eps1 / r (Eq. (18)); Uhat_o = U_o[:, :k_o] (r x k_o),
 // Vhat_o = S Q^T restricted to those k_o (k_o x r), both row-major.
 struct Stage2 {
     double c2 = 0, eps2 = 0;

@@ -11,6 +11,7 @@
 // is the array below, which every GPU that loads this module holds until the
 // process exits.  The plan and the level registrations (made earlier with
 // kifmm_m2l_precompute / kifmm_m2l_set_level) are used as they are.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -78,10 +79,31 @@ __global__ void build_tiles_kernel(const TilePrefix pre, int nrhs, int n_tiles, 
 }
 
 std::mutex g_setup_mutex;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+    CUcontext ctx;        // the context the address belongs to
+    unsigned char* ptr;   // device address of g_noalloc_scratch in it
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the static scratch on the current device (looked up
-// once per device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
+
+// Device address of the static scratch on the current device: looked up
+// once per device and context (a context destroyed and created again, e.g.
+// after cudaDeviceReset, gets its own lookup), with that device current.
 int scratch_address(unsigned char** out) {
     int dev = -1;
     KIFMM_CUDA_TRY(cudaGetDevice(&dev));
@@ -90,12 +112,17 @@ int scratch_address(unsigned char** out) {
         return KIFMM_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    CUcontext ctx = nullptr;
+    const CtxGetCurrentFn fn = ctx_get_current();
+    const bool known_ctx = fn && fn(&ctx) == CUDA_SUCCESS && ctx != nullptr;
+    ScratchAddr& e = g_scratch_addr[dev];
+    if (!known_ctx || !e.ptr || e.ctx != ctx) {
         void* p = nullptr;
         KIFMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        e.ptr = static_cast<unsigned char*>(p);
+        e.ctx = known_ctx ? ctx : nullptr;
     }
-    *out = g_scratch_ptr[dev];
+    *out = e.ptr;
     return KIFMM_OK;
 }
 
@@ -220,6 +247,15 @@ extern "C" int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int le
         a.b_groups = kOffsets;
         a.ndim = rp;
         a.n_chunk = core_chunk(plan);
+        // the plan's core variant, as kifmm_m2l_apply launches it
+        a.contiguous = plan->tune_contig;
+        a.core_resident = plan->tune_variant == 1;
+        a.core_drain = plan->variant_drain();
+        a.red_bulk = plan->variant_bulk();
+        a.mma_pair = plan->variant_pair();
+        a.direct_rows = plan->variant_direct();
+        a.core_bres = plan->variant_bres();
+        a.wait_ns = plan->core_wait_ns;
         a.s2_on = plan->s2_on;
         a.s2_V = plan->s2V.ptr;
         a.s2_U = plan->s2U.ptr;

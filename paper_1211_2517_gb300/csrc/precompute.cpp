@@ -1,9 +1,9 @@
 // Host FP64 precompute of the SVD-compressed M2L operators (Sec. 3.1).
 //
-//   K_fat = [K_1 ... K_316] = U Sigma [V_1^T ... V_316^T]          (Eq. fat)
-//   U~ = columns of U with sigma_i >= eps sigma_0                    (Eq. eq-cmpM2Ls)
+//   K_fat = [K_1 ... K_316] = U Sigma [V_1^T ... V_316^T]          (Eq. (10))
+//   U~ = columns of U with sigma_i >= eps sigma_0                    (Eq. (13))
 //   R~ = U~  because K_o^T = K_{-o} (G radial, same surfaces), so
-//        K_thin is a row-block permutation of K_fat^T (Eq. thin) and the
+//        K_thin is a row-block permutation of K_fat^T (Eq. (11)) and the
 //        right basis of K_thin spans the left basis of K_fat.
 //   K~_o = U~^T K_o R~
 //

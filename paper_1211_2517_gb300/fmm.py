@@ -2,7 +2,7 @@
 
 Binding of the ``kifmm_fmm_*`` entry points (include/kifmm_m2l.h): the
 complete algorithm of Sec. 4 for point sources, p_i = sum_{j != i}
-G(x_i, x_j) q_j (Eq. eq_eval), with the near field summed directly and the
+G(x_i, x_j) q_j (Eq. (1)), with the near field summed directly and the
 far field through S~, M~, the compressed M2L, L~ and T~ (Sec. 3.3).  Every
 step runs in the library's kernels; this module only marshals arguments.
 """
@@ -38,7 +38,7 @@ class PointFMM:
     precision).  ``points``: float64 [N, 3]; ``depth``: leaf level; the root
     cube is (centre, r0) when given, else the padded bounding cube.
     ``normals`` (float64 [N, 3]) makes the sources dipoles: the double-layer
-    potential sum_j dG(x_i, x_j)/dn(x_j) q_j (Sec. 4, Eq. eq-doubles2m)."""
+    potential sum_j dG(x_i, x_j)/dn(x_j) q_j (Sec. 4, Eq. (26))."""
 
     def __init__(self, plan: M2LPlan, points, depth: int, centre=None, r0: float | None = None, normals=None):
         pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)

@@ -12,7 +12,7 @@ Tolerances (relative L2 over the compared points):
                    at 3e-7 of the total potential
     total          1e-6   (split6 and f16x3; split3 3e-5, bf16 1e-2 as for the
                           M2L)
-  against the direct sum (Eq. eq_eval): the method's own error (p = 8,
+  against the direct sum (Eq. (1)): the method's own error (p = 8,
   eps = 1e-7: ~1e-7 in FP64) plus the above, 1e-6.
 """
 import os
@@ -183,7 +183,7 @@ def test_edge_cases(g):
 @pytest.fixture(scope="module")
 def sphere_dl_case(sphere_case):
     """The 65,536-point sphere with its outward normals as dipole sources
-    (the double layer of Sec. 4, Eq. eq-doubles2m): the oracle's near field
+    (the double layer of Sec. 4, Eq. (26)): the oracle's near field
     and compressed far field at p = 8."""
     pts, q, tree, _, _ = sphere_case
     nrm = pts / np.linalg.norm(pts, axis=1, keepdims=True)

@@ -1,6 +1,6 @@
 """Pins of the FMM oracle (``oracle/fmm.py``): complete potential evaluation
 with the compressed passes of Sec. 3.3, checked against closed forms, brute
-force, potential theory and the direct sum (Eq. eq_eval).  CPU only."""
+force, potential theory and the direct sum (Eq. (1)).  CPU only."""
 from __future__ import annotations
 
 import numpy as np
@@ -181,7 +181,7 @@ def test_compressed_fmm_operator_is_symmetric(cube_case):
 
 
 # ---------------------------------------------------------------------------
-# double layer (Sec. 4, Eq. eq-doubles2m): dG/dn(y) in S2T and in S2M's
+# double layer (Sec. 4, Eq. (26)): dG/dn(y) in S2T and in S2M's
 # first step
 # ---------------------------------------------------------------------------
 def _sphere_quadrature(nt, nphi):
@@ -246,7 +246,7 @@ def test_double_layer_near_field_bruteforce():
 def test_double_layer_s2m_reproduces_far_potential(c):
     # dipoles inside child c of a unit parent: single-layer equivalent
     # densities solved from their double-layer check potentials
-    # (Eq. eq-doubles2m) reproduce their potential beyond the far-field
+    # (Eq. (26)) reproduce their potential beyond the far-field
     # boundary
     p, hc = 6, 0.5
     centre = np.array([(c >> 2) & 1, (c >> 1) & 1, c & 1], dtype=np.float64) - 0.5

@@ -204,7 +204,7 @@ def _small_case(seed=0, n=4000, depth=3, p=4):
 
 def test_dense_m2l_matches_direct_sum():
     # M2L(S2M(q)) at the downward check points equals the direct potential of
-    # the interaction-list points (Eq. eq_eval) within the KIFMM
+    # the interaction-list points (Eq. (1)) within the KIFMM
     # discretisation error; p = 6, d = 0.1 measured ~1e-5.
     pts, tree, q, _ = _small_case(n=3000, p=6)
     p, d = 6, 0.1
@@ -358,7 +358,7 @@ def test_stage2_m2l_reduces_to_stage1_without_truncation(oracle_factors):
 
 def test_stage2_m2l_error_bound(oracle_factors):
     # per target t: |p_s2 - p_1| <= s_l |U~|_2 sum_s sigma_{k_o+1}(K~_o) |q~_s|
-    # with |U~|_2 = 1 and sigma_{k_o+1} < eps2 sigma_0 (Eq. eq-lra truncation)
+    # with |U~|_2 = 1 and sigma_{k_o+1} < eps2 sigma_0 (Eq. (17) truncation)
     tree, box, qq, p = _stage2_case()
     f = oracle_factors(p, 0.1, 1e-6)
     eps2 = 3e-4
