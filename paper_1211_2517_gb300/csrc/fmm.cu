@@ -11,17 +11,26 @@
 //
 // Device, per evaluate, in stream order:
 //   gather     densities into the leaf-ordered point array        (CUDA cores)
-//   check      h K(x^u, points) q for every leaf (double layer: h dG/dn(y),
-//              the first step of S2M, Eq. (26))           (CUDA cores)
-//   S~         q~_leaf = Ws (h K q): split + identity-row GEMM    (tensor cores)
+//   S~         q~_leaf = sum_j q_j s_j over the leaf's points, s_j the
+//              point's compressed row (below)                      (CUDA cores)
 //   M~         level by level, children -> parents: gather GEMM over the
 //              8 octant groups with FP32 reductions, then split   (tensor cores)
 //   M2L        the plan's core over every level's pairs           (tensor cores)
 //   L~         level by level, parents -> children: split of the
 //              parents' p~, gather GEMM adding into the children  (tensor cores)
-//   T~ factor  e_leaf = h Ws^T p~_leaf: split + identity-row GEMM (tensor cores)
-//   leaf sums  L2T from e_leaf plus the near field (double layer: dG/dn(y)),
-//              in the caller's order
+//   leaf sums  far field t_i . p~_leaf (T~ and L2T in one dot product per
+//              point) plus the near field (double layer: dG/dn(y)), in the
+//              caller's order                                      (CUDA cores)
+//
+// The per-point rows are formed once per tree (and per set of normals) in
+// FP64 from the FP64 S~ factor Ws and stored in FP32: t(s) = 1/(4 pi) Ws g(s)
+// with g_i = 1 / |x_i - s| over the check points x_i of the leaf (leaf
+// units), which is both the T~ row (far field at s) and, since the upward
+// check surface is the downward equivalent surface and G is symmetric, the
+// S~ row of a unit charge at s; dipoles get their own S~ rows from
+// n . (x_i - y) / |x_i - y|^3 (Eq. (26)).  Ws carries the pseudo-inverse
+// cutoff's large entries; forming the rows in FP64 keeps that amplification
+// out of the FP32 evaluation, which then sees well-conditioned r-vectors.
 //
 // Layout (rows = boxes of levels 2..depth back to back, level order):
 //   qb3  BF16 [3][rows + 1][rp]  q~ pieces, last row zero
@@ -29,8 +38,7 @@
 //   qf   FP32 [rows][rp]          q~ of every level (M~ accumulates into it)
 //   qh, qs  f16x3 plans: the core's FP16 pieces [2][rows + 1][rp] of qf, row factors
 //   sl   BF16 [3][(tiles + 1) * 128][rp]   one level's p~ pieces (L~ input)
-//   pc   FP32 [leaves][n_pad]    check potentials, then e_leaf
-//   sp   BF16 split scratch of the S~ and T~ GEMMs
+//   trows, drows  FP32 [points][rp]  the per-point T~ rows and the dipoles' S~ rows
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -86,19 +94,15 @@ int ensure_pass_ops(kifmm_m2l_plan plan) {
     PassOps ops;
     int st = compute_pass_ops(plan->prm.p, plan->prm.d, plan->r, plan->U64, kPassRcond, ops);
     if (st != KIFMM_OK) return st;
-    const size_t n = plan->n, r = plan->r, rp = plan->rp, np = plan->n_pad;
-    // S~ factor Ws as B [rp][np]: output coefficient a, input check point i
-    st = upload_pieces(plan->Wsb, rp * np, [&](size_t e) -> double {
-        const size_t a = e / np, i = e % np;
-        return (a < r && i < n) ? ops.Ws[a * n + i] : 0.0;
-    });
-    if (st != KIFMM_OK) return st;
-    // T~ factor Ws^T as B [np][rp]: output equivalent point i, input coefficient a
-    st = upload_pieces(plan->Wtb, np * rp, [&](size_t e) -> double {
-        const size_t i = e / rp, a = e % rp;
-        return (a < r && i < n) ? ops.Ws[a * n + i] : 0.0;
-    });
-    if (st != KIFMM_OK) return st;
+    const size_t n = plan->n, r = plan->r, rp = plan->rp;
+    // Ws in FP64 [rp][n]: output coefficient a, check point i (the per-point
+    // S~ / T~ rows are formed from it on the device)
+    {
+        std::vector<double> w(rp * n, 0.0);
+        for (size_t a = 0; a < r; ++a)
+            for (size_t i = 0; i < n; ++i) w[a * n + i] = ops.Ws[a * n + i];
+        KIFMM_CUDA_TRY(plan->Ws64.upload(w.data(), w.size()));
+    }
     // M~_c as B [8][rp][rp] (B[a][b] = M~_c[a][b]) and L~_c = M~_c^T
     st = upload_pieces(plan->Mb, 8 * rp * rp, [&](size_t e) -> double {
         const size_t c = e / (rp * rp), a = (e / rp) % rp, b = e % rp;
@@ -131,14 +135,19 @@ struct kifmm_fmm_s {
     };
     std::vector<Pass> up, down;  // indexed by the parent level
     DevBuf<int> up_src, up_dst, up_k, dn_src, dn_dst, dn_k;
-    DevBuf<float4> hi, lo, usurf;  // points in leaf units: hi (w = density) + lo
+    DevBuf<float4> hi, lo;  // points in leaf units: hi (w = density) + lo
     DevBuf<float4> nhi, nlo;       // double layer: normals as two FP32 words (leaf order)
     bool dl = false;
     std::vector<int32_t> h_perm;   // caller's index of every leaf-ordered point
     DevBuf<int> perm, leaf_start, near_start, near_idx;
     DevBuf<int4> leaf_ijk;
-    DevBuf<__nv_bfloat16> qb3, sl, sp;
-    DevBuf<float> qf, pt, pc, qs;
+    DevBuf<__nv_bfloat16> qb3, sl;
+    DevBuf<float> qf, pt, qs;
+    // per-point compressed rows [n_points][rp] (FP64-formed, stored FP32):
+    // T~ rows (far field at a point; for point charges also their S~ rows)
+    // and, with normals, the dipoles' S~ rows
+    DevBuf<float> trows, drows;
+    DevBuf<double> s64, xsurf64;  // points [n_points][3] and check points [n][3] in leaf units
     DevBuf<__nv_bfloat16> qh;
     int max_level_boxes = 0, max_down_tiles = 0;
 };
@@ -316,6 +325,7 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
     const std::vector<int32_t> lijk = box_ijk(L);
     std::vector<int4> h_lijk(B);
     std::vector<float4> h_hi(N), h_lo(N);
+    std::vector<double> h_s64((size_t)N * 3);
     std::vector<int32_t> near_start(B + 1, 0), near_idx;
     for (int b = 0; b < B; ++b) {
         h_lijk[b] = make_int4(lijk[3 * b], lijk[3 * b + 1], lijk[3 * b + 2], 0);
@@ -328,6 +338,7 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
             float hv[3], lv[3];
             for (int t = 0; t < 3; ++t) {
                 const double v = (points[3 * i + t] - c[t]) / h;
+                h_s64[3 * (size_t)s + t] = v;
                 hv[t] = (float)(std::nearbyint(v * 1048576.0) / 1048576.0);
                 lv[t] = (float)(v - (double)hv[t]);
             }
@@ -359,12 +370,21 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
     KIFMM_CUDA_TRY(f->near_start.upload(near_start.data(), near_start.size()));
     KIFMM_CUDA_TRY(f->near_idx.upload(near_idx.data(), near_idx.size()));
     const std::vector<double> u = unit_surface(plan->prm.p);
-    std::vector<float4> h_u(plan->n);
-    for (int i = 0; i < plan->n; ++i) h_u[i] = make_float4((float)u[3 * i], (float)u[3 * i + 1], (float)u[3 * i + 2], 0.f);
-    KIFMM_CUDA_TRY(f->usurf.upload(h_u.data(), h_u.size()));
+    std::vector<double> h_x(3 * (size_t)plan->n);
+    const double a_surf = 3.0 - 2.0 * plan->prm.d;  // upward check = downward equivalent surface, leaf units
+    for (int i = 0; i < plan->n; ++i)
+        for (int t = 0; t < 3; ++t) h_x[3 * i + t] = a_surf * u[3 * i + t];
+    KIFMM_CUDA_TRY(f->xsurf64.upload(h_x.data(), h_x.size()));
+    KIFMM_CUDA_TRY(f->s64.upload(h_s64.data(), h_s64.size()));
+    // T~ rows of every point, in FP64: t(s)[a] = 1/(4 pi) sum_i Ws[a][i] / |x_i - s|
+    // (leaf units).  For point charges the same row is the point's S~ row: the
+    // upward check surface is the downward equivalent surface and G is symmetric.
+    const size_t rp = plan->rp;
+    KIFMM_CUDA_TRY(f->trows.ensure((size_t)N * rp));
+    KIFMM_CUDA_TRY(launch_point_rows(f->s64.ptr, nullptr, (int)N, plan->Ws64.ptr, (int)rp, plan->n, f->xsurf64.ptr,
+                                     0.0795774715459476679, f->trows.ptr, 0));
+    KIFMM_CUDA_TRY(cudaStreamSynchronize(0));
     // scratch
-    const size_t rp = plan->rp, np = plan->n_pad;
-    const long leaf_tiles = (B + kTileRows - 1) / kTileRows;
     KIFMM_CUDA_TRY(f->qb3.ensure((size_t)3 * (f->rows + 1) * rp));
     KIFMM_CUDA_TRY(cudaMemset(f->qb3.ptr, 0, f->qb3.count * sizeof(__nv_bfloat16)));
     KIFMM_CUDA_TRY(f->pt.ensure((size_t)f->rows * rp));
@@ -374,57 +394,25 @@ int build_tree(kifmm_fmm f, const double* points, const double* centre, double r
         KIFMM_CUDA_TRY(f->qs.ensure((size_t)f->rows + 1));
     }
     KIFMM_CUDA_TRY(f->sl.ensure((size_t)3 * (f->max_down_tiles + 1) * kTileRows * rp));
-    KIFMM_CUDA_TRY(f->sp.ensure((size_t)3 * leaf_tiles * kTileRows * std::max(rp, np)));
-    KIFMM_CUDA_TRY(f->pc.ensure((size_t)B * np));
     return KIFMM_OK;
 }
 
 int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s) {
     kifmm_m2l_plan plan = f->plan;
     const int L = f->depth, B = f->nbox[L];
-    const int n = plan->n, rp = plan->rp, np = plan->n_pad;
+    const int rp = plan->rp;
     const double h = f->r0 / (double)(1u << L);
-    const float a_surf = (float)(3.0 - 2.0 * plan->prm.d);  // (3-2d) h in leaf units
     const int N = (int)f->n_points;
     KIFMM_CUDA_TRY(launch_gather_density(q, f->perm.ptr, f->hi.ptr, N, s));
     const float4* nhi = f->dl ? f->nhi.ptr : nullptr;
     const float4* nlo = f->dl ? f->nlo.ptr : nullptr;
     if (parts & KIFMM_FMM_FAR) {
         const long qstride = (f->rows + 1) * rp;
-        const int leaf_tiles = (B + kTileRows - 1) / kTileRows;
-        // S~: check potentials h K(x^u, points) q (= sum q / (4 pi |.|) in leaf units;
-        // double layer: h dG/dn = sum q n . d / (4 pi h |d|^3)), then q~ = Ws (.)
-        // into the leaf rows of qb3
-        KIFMM_CUDA_TRY(launch_leaf_check(f->hi.ptr, f->lo.ptr, nhi, f->leaf_start.ptr, B, f->usurf.ptr, n, a_surf,
-                                         (float)(f->dl ? 0.0795774715459476679 / h : 0.0795774715459476679),
-                                         f->pc.ptr, np, s));
-        {
-            const long sstride = (long)leaf_tiles * kTileRows * np;
-            KIFMM_CUDA_TRY(launch_split_rows(f->pc.ptr, B, np, np, np, nullptr, 0, leaf_tiles, f->sp.ptr, sstride, 3, s));
-            UmmaArgs a{};
-            a.A = f->sp.ptr;
-            a.a_piece_stride = sstride;
-            a.kdim = np;
-            a.B = plan->Wsb.ptr;
-            a.b_groups = 1;
-            a.ndim = rp;
-            a.n_chunk = rows_chunk(rp, leaf_tiles, plan->num_sms);
-            a.row_identity = 1;
-            a.n_tiles = leaf_tiles;
-            a.m_rows = B;
-            a.ldd = rp;
-            a.alpha = 1.0f;
-            a.Dp = f->qb3.ptr + f->off[L] * rp;
-            a.dp_piece_stride = qstride;
-            a.dp_pieces = 3;
-            // f16x3: the leaves' FP32 q~ joins the array the core's FP16 split reads
-            if (plan->prm.precision == KIFMM_PREC_F16X3) a.Df = f->qf.ptr + f->off[L] * rp;
-            a.n_products = 6;
-            a.hilo = 1;
-            a.core_drain = 1;
-            a.error_flag = plan->err_flag.ptr;
-            KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_SPLIT, a, plan->num_sms, s));
-        }
+        // S~ at the leaves through the per-point rows: q~_b = sum_{j in b} q_j s_j
+        // (point charges: s_j is the point's T~ row; dipoles: its own S~ row),
+        // into the leaf rows of qf and their BF16 pieces in qb3
+        KIFMM_CUDA_TRY(launch_leaf_rows_sum(f->dl ? f->drows.ptr : f->trows.ptr, f->hi.ptr, f->leaf_start.ptr, B, rp,
+                                            f->qf.ptr + f->off[L] * rp, f->qb3.ptr + f->off[L] * rp, qstride, s));
         // M~: q~_parent = sum_c M~_c q~_child, level by level towards the root
         for (int lp = L - 1; lp >= 2; --lp) {
             const auto& ps = f->up[lp];
@@ -470,38 +458,13 @@ int evaluate(kifmm_fmm f, const float* q, float* out, int parts, cudaStream_t s)
                                f->dn_k.ptr + ps.tile0, ps.n_tiles, f->pt.ptr, s);
             if (st != KIFMM_OK) return st;
         }
-        // T~ factor: e_leaf = h Ws^T p~_leaf (downward equivalent densities)
-        {
-            const long sstride = (long)leaf_tiles * kTileRows * rp;
-            KIFMM_CUDA_TRY(launch_split_rows(f->pt.ptr + f->off[L] * rp, B, rp, rp, rp, nullptr, 0, leaf_tiles, f->sp.ptr,
-                                             sstride, 3, s));
-            UmmaArgs a{};
-            a.A = f->sp.ptr;
-            a.a_piece_stride = sstride;
-            a.kdim = rp;
-            a.B = plan->Wtb.ptr;
-            a.b_groups = 1;
-            a.ndim = np;
-            a.n_chunk = rows_chunk(np, leaf_tiles, plan->num_sms);
-            a.row_identity = 1;
-            a.n_tiles = leaf_tiles;
-            a.m_rows = B;
-            a.D = f->pc.ptr;
-            a.ldd = np;
-            a.alpha = (float)h;
-            a.beta = 0.0f;
-            a.n_valid = np;
-            a.n_products = 6;
-            a.hilo = 1;
-            a.core_drain = 1;
-            a.error_flag = plan->err_flag.ptr;
-            KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_STORE, a, plan->num_sms, s));
-        }
     }
+    // leaf sums: the far field as T~ row . p~_leaf (T~ and L2T of Sec. 3.3 in one
+    // r-long dot product per point) plus the near field, in the caller's order
     KIFMM_CUDA_TRY(launch_leaf_eval(f->hi.ptr, f->lo.ptr, nhi, nlo, f->leaf_start.ptr, f->leaf_ijk.ptr, f->near_start.ptr,
-                                    f->near_idx.ptr, B, f->usurf.ptr, n, a_surf, (float)(0.0795774715459476679 / h),
-                                    (float)(0.0795774715459476679 / (h * h)), f->pc.ptr, np, f->perm.ptr, out, parts,
-                                    s));
+                                    f->near_idx.ptr, B, f->trows.ptr, rp, f->pt.ptr + f->off[L] * rp,
+                                    (float)(0.0795774715459476679 / h), (float)(0.0795774715459476679 / (h * h)),
+                                    f->perm.ptr, out, parts, s));
     return KIFMM_OK;
 }
 
@@ -634,18 +597,33 @@ int kifmm_fmm_set_normals(kifmm_fmm fmm, const double* normals) {
     }
     try {
         std::vector<float4> vh((size_t)N), vl((size_t)N);
+        std::vector<double> v64((size_t)N * 3);
         for (int64_t s = 0; s < N; ++s) {
             const double* v = normals + 3 * (int64_t)fmm->h_perm[s];
             float w[3], r[3];
             for (int t = 0; t < 3; ++t) {
                 w[t] = (float)v[t];
                 r[t] = (float)(v[t] - (double)w[t]);
+                v64[3 * s + t] = v[t];
             }
             vh[s] = make_float4(w[0], w[1], w[2], 0.f);
             vl[s] = make_float4(r[0], r[1], r[2], 0.f);
         }
         KIFMM_CUDA_TRY(fmm->nhi.upload(vh.data(), vh.size()));
         KIFMM_CUDA_TRY(fmm->nlo.upload(vl.data(), vl.size()));
+        if (fmm->plan) {
+            // the dipoles' S~ rows in FP64: s(y)[a] = 1/(4 pi h) sum_i Ws[a][i]
+            // n . (x_i - y) / |x_i - y|^3 (leaf units; the first step of S2M for a
+            // double layer, Eq. (26))
+            kifmm_m2l_plan plan = fmm->plan;
+            const double h = fmm->r0 / (double)(1u << fmm->depth);
+            DevBuf<double> n64;
+            KIFMM_CUDA_TRY(n64.upload(v64.data(), v64.size()));
+            KIFMM_CUDA_TRY(fmm->drows.ensure((size_t)N * plan->rp));
+            KIFMM_CUDA_TRY(launch_point_rows(fmm->s64.ptr, n64.ptr, (int)N, plan->Ws64.ptr, plan->rp, plan->n,
+                                             fmm->xsurf64.ptr, 0.0795774715459476679 / h, fmm->drows.ptr, 0));
+            KIFMM_CUDA_TRY(cudaStreamSynchronize(0));
+        }
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed");
         return KIFMM_ERR_OOM;

@@ -49,20 +49,25 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_b
 // of the [-1,1]^3 cube surface.
 // hi[i].w = q[perm[i]].
 cudaError_t launch_gather_density(const float* q, const int* perm, float4* hi, int n_points, cudaStream_t stream);
-// out[b][i] = scale * sum_{j in leaf b} q_j / |a u_i - s_j| (i < n <= 512),
-// or, with the normals' hi words nhi (double layer), scale * sum_j q_j
-// nhi_j . (a u_i - s_j) / |a u_i - s_j|^3; out[b][n..ld) = 0.
-cudaError_t launch_leaf_check(const float4* hi, const float4* lo, const float4* nhi, const int* leaf_start,
-                              int n_leaves, const float4* usurf, int n, float a, float scale, float* out, int ld,
-                              cudaStream_t stream);
-// out[perm[i]] = scale * (L2T from e[b][0..n) on a u, parts & 2) + near field
-// over near_idx[near_start[b]..near_start[b+1]) (parts & 1): scale * sum q_j /
+// rows[j][a] = scale * sum_i Ws[a][i] g(x_i, s_j) in FP64, stored as FP32
+// ([n_points][rp]; Ws [rp][n] with zero rows past the rank; x_i the n
+// check points in leaf units [n][3]; pts the points in leaf units
+// [n_points][3]): g = 1 / |x_i - s_j|, or with normals nrm [n_points][3]
+// g = n_j . (x_i - s_j) / |x_i - s_j|^3.  rp <= 288, a multiple of 16.
+cudaError_t launch_point_rows(const double* pts, const double* nrm, int n_points, const double* ws, int rp, int n,
+                              const double* xsurf, double scale, float* rows, cudaStream_t stream);
+// qf[b][a] = sum_{j in leaf b} hi[j].w rows[j][a] (compensated FP32 sum) and
+// its three BF16 pieces qb[pc][b][a] (piece stride pstride elements).
+cudaError_t launch_leaf_rows_sum(const float* rows, const float4* hi, const int* leaf_start, int n_leaves, int rp,
+                                 float* qf, __nv_bfloat16* qb, long pstride, cudaStream_t stream);
+// out[perm[i]] = trows[i] . pleaf[b] (parts & 2) + near field over
+// near_idx[near_start[b]..near_start[b+1]) (parts & 1): scale * sum q_j /
 // |d|, or, with the normals' two words nhi + nlo (double layer), scale_dl *
 // sum q_j n_j . d / |d|^3.
 cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const float4* nhi, const float4* nlo,
                              const int* leaf_start, const int4* leaf_ijk, const int* near_start, const int* near_idx,
-                             int n_leaves, const float4* usurf, int n, float a, float scale, float scale_dl,
-                             const float* e, int lde, const int* perm, float* out, int parts, cudaStream_t stream);
+                             int n_leaves, const float* trows, int rp, const float* pleaf, float scale, float scale_dl,
+                             const int* perm, float* out, int parts, cudaStream_t stream);
 
 // Rows of A (FP32, m_rows x cols, ld lda) -> two FP16 pieces [2][m_rows][ldo]
 // (piece stride piece_stride) of sigma_r x with sigma_r the power of two that

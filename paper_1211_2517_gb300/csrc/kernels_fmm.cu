@@ -1,6 +1,7 @@
 // CUDA-core kernels of the point-source evaluation (fmm.cu): the
-// density gather, the leaf check potentials that feed S~, and the leaf sums
-// of L2T and of the near field (S2T).  G = 1 / (4 pi |x - y|) (Sec. 4);
+// density gather, the per-point compressed S~ / T~ rows (FP64, once per tree
+// and per set of normals), the S~ sums over a leaf's points, and the leaf
+// sums of the far field (a row against p~) and of the near field (S2T).  G = 1 / (4 pi |x - y|) (Sec. 4);
 // for a double layer, dG/dn(y) = n(y) . (x - y) / (4 pi |x - y|^3) in the
 // check potentials and the near field (Sec. 4, Eq. (26)), with the
 // densities in the hi words' w and the normals n_j as two FP32 words.
@@ -26,6 +27,7 @@
 // (emulated: 3.7e-7).  The check potentials (sources at least 1.8 leaf
 // units from the check points) use a plain FP32 dot product.
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "kernels.h"
 
@@ -33,7 +35,6 @@ namespace kifmm {
 namespace {
 
 constexpr float kInv4Pi = 0.0795774715459476679f;
-constexpr int kCheckThreads = 256;  // leaf check kernel: up to 2 * 256 surface points
 constexpr int kEvalThreads = 64;    // leaf sum kernel: threads, each with up to two targets
 constexpr int kNearCap = 512;       // leaf sum kernel: staged sources per pass (>= n surface points)
 
@@ -44,61 +45,132 @@ __global__ void gather_density_kernel(const float* __restrict__ q, const int* __
         w[4 * (long)i + 3] = __ldg(q + __ldg(perm + i));
 }
 
-// Block b: out[b][i] = scale * sum_{j in leaf b} q_j / |a u_i - s_j| for the
-// n upward check points a u_i (leaf units: a = 3 - 2d), columns n..ld-1 zero;
-// double layer (DL): scale * sum_j q_j n_j . (a u_i - s_j) / |a u_i - s_j|^3.
-// Thread t takes check points t and t + blockDim.x (blockDim.x >= n / 2).
-template <bool DL>
-__global__ void __launch_bounds__(kCheckThreads) leaf_check_kernel(const float4* __restrict__ hi,
-                                                                   const float4* __restrict__ lo,
-                                                                   const float4* __restrict__ nhi,
-                                                                   const int* __restrict__ leaf_start,
-                                                                   const float4* __restrict__ usurf, int n, float a,
-                                                                   float scale, float* __restrict__ out, int ld) {
-    __shared__ float4 src[kCheckThreads];
-    __shared__ float4 srcm[DL ? kCheckThreads : 1];
-    const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const int beg = __ldg(leaf_start + b), end = __ldg(leaf_start + b + 1);
-    float3 x[2];
-    float acc[2] = {0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * nt;
-        const float4 u = i < n ? __ldg(usurf + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        x[k] = make_float3(a * u.x, a * u.y, a * u.z);
+// Per-point compressed rows (Sec. 3.3's S~ = R~^T S and T~ = T U~ applied to
+// one point), in FP64: rows[j][a] = scale * sum_i Ws[a][i] g(x_i, s_j) for
+// the n check points x_i (leaf units) and the point s_j, with
+//   g = 1 / |x_i - s_j|                        (point charges; the same row
+//                                               serves S~ and T~ + L2T)
+//   g = n_j . (x_i - s_j) / |x_i - s_j|^3      (dipoles: S~ of the double layer)
+// Ws is [rp][n] (rows past the rank zero).  Block: 32 points x all rp
+// coefficients; the check points go through shared memory 16 at a time with
+// the matching columns of Ws (transposed, coefficient-contiguous); thread
+// (ty, tx) accumulates points 2 ty, 2 ty + 1 and coefficients tx + 16 k.
+constexpr int kRowPts = 32, kRowChunk = 16, kRowMaxK = 18;  // rp <= 288
+
+__global__ void __launch_bounds__(256) point_rows_kernel(const double* __restrict__ pts, const double* __restrict__ nrm,
+                                                         int n_points, const double* __restrict__ ws, int rp, int n,
+                                                         const double* __restrict__ xsurf, double scale,
+                                                         float* __restrict__ rows) {
+    __shared__ double g_s[kRowPts][kRowChunk + 1];
+    __shared__ double w_s[kRowChunk][kRowMaxK * 16];
+    __shared__ double x_s[kRowChunk][3];
+    __shared__ double p_s[kRowPts][6];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int j0 = blockIdx.x * kRowPts;
+    const int ka = (rp + 15) / 16;
+    if (tid < kRowPts) {
+        const int j = j0 + tid;
+        for (int t = 0; t < 3; ++t) {
+            p_s[tid][t] = j < n_points ? pts[3 * (long)j + t] : 0.0;
+            p_s[tid][3 + t] = (nrm && j < n_points) ? nrm[3 * (long)j + t] : 0.0;
+        }
     }
-    for (int c0 = beg; c0 < end; c0 += nt) {
+    double acc[2][kRowMaxK];
+#pragma unroll
+    for (int k = 0; k < kRowMaxK; ++k) acc[0][k] = acc[1][k] = 0.0;
+    for (int i0 = 0; i0 < n; i0 += kRowChunk) {
         __syncthreads();
-        const int j = c0 + tid;
-        if (j < end) {
-            const float4 h4 = __ldg(hi + j), l4 = __ldg(lo + j);
-            src[tid] = make_float4(h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w);
-            if (DL) srcm[tid] = __ldg(nhi + j);
+        if (tid < kRowChunk * 3) {
+            const int i = i0 + tid / 3;
+            x_s[tid / 3][tid % 3] = i < n ? xsurf[3 * i + tid % 3] : 0.0;
+        }
+        for (int e = tid; e < kRowChunk * ka * 16; e += blockDim.x) {
+            const int ii = e / (ka * 16), a = e % (ka * 16), i = i0 + ii;
+            w_s[ii][a] = (i < n && a < rp) ? ws[(long)a * n + i] : 0.0;
         }
         __syncthreads();
-        const int cnt = min(nt, end - c0);
+        for (int e = tid; e < kRowPts * kRowChunk; e += blockDim.x) {
+            const int pt = e / kRowChunk, ii = e % kRowChunk;
+            double g = 0.0;
+            if (i0 + ii < n && j0 + pt < n_points) {
+                const double dx = x_s[ii][0] - p_s[pt][0], dy = x_s[ii][1] - p_s[pt][1], dz = x_s[ii][2] - p_s[pt][2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double ri = 1.0 / sqrt(r2);
+                g = nrm ? (p_s[pt][3] * dx + p_s[pt][4] * dy + p_s[pt][5] * dz) * ri * ri * ri : ri;
+            }
+            g_s[pt][ii] = g;
+        }
+        __syncthreads();
 #pragma unroll 4
-        for (int jj = 0; jj < cnt; ++jj) {
-            const float4 y = src[jj];
+        for (int ii = 0; ii < kRowChunk; ++ii) {
+            const double g0 = g_s[2 * ty][ii], g1 = g_s[2 * ty + 1][ii];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float dx = x[k].x - y.x, dy = x[k].y - y.y, dz = x[k].z - y.z;
-                if (DL) {
-                    const float4 m = srcm[jj];
-                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    acc[k] = fmaf(y.w * fmaf(m.x, dx, fmaf(m.y, dy, m.z * dz)), ri * ri * ri, acc[k]);
-                } else {
-                    acc[k] = fmaf(y.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), acc[k]);
+            for (int k = 0; k < kRowMaxK; ++k) {
+                if (k < ka) {
+                    const double w = w_s[ii][tx + 16 * k];
+                    acc[0][k] = fma(w, g0, acc[0][k]);
+                    acc[1][k] = fma(w, g1, acc[1][k]);
                 }
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * nt;
-        if (i < n) out[(long)b * ld + i] = scale * acc[k];
+    for (int t = 0; t < 2; ++t) {
+        const int j = j0 + 2 * ty + t;
+        if (j >= n_points) continue;
+#pragma unroll
+        for (int k = 0; k < kRowMaxK; ++k) {
+            const int a = tx + 16 * k;
+            if (k < ka && a < rp) rows[(long)j * rp + a] = (float)(scale * acc[t][k]);
+        }
     }
-    for (int i = n + tid; i < ld; i += nt) out[(long)b * ld + i] = 0.f;
+}
+
+// S~ through the rows: q~_b[a] = sum_{j in leaf b} q_j rows[j][a] (q_j in the
+// hi words' w), FP32 with Neumaier's compensated summation (TwoSum of
+// Knuth / Moller, explicitly rounded so that no contraction breaks it).
+// One block per leaf, thread t takes coefficients 4 t .. 4 t + 3.  Writes the
+// FP32 row qf[b] and its three BF16 pieces qb[pc][b] (piece stride pstride).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float e = fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s);
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+__global__ void leaf_rows_sum_kernel(const float* __restrict__ rows, const float4* __restrict__ hi,
+                                     const int* __restrict__ leaf_start, int rp, float* __restrict__ qf,
+                                     __nv_bfloat16* __restrict__ qb, long pstride) {
+    const int b = blockIdx.x, t = threadIdx.x;
+    if (4 * t >= rp) return;
+    const int beg = __ldg(leaf_start + b), end = __ldg(leaf_start + b + 1);
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* wq = reinterpret_cast<const float*>(hi) + 3;
+    for (int j = beg; j < end; ++j) {
+        const float q = __ldg(wq + 4 * (long)j);
+        const float4 r = __ldg(reinterpret_cast<const float4*>(rows + (long)j * rp) + t);
+        two_sum_acc(s[0], c[0], __fmul_rn(q, r.x));
+        two_sum_acc(s[1], c[1], __fmul_rn(q, r.y));
+        two_sum_acc(s[2], c[2], __fmul_rn(q, r.z));
+        two_sum_acc(s[3], c[3], __fmul_rn(q, r.w));
+    }
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __fadd_rn(s[k], c[k]);
+    reinterpret_cast<float4*>(qf + (long)b * rp)[t] = make_float4(v[0], v[1], v[2], v[3]);
+    // three BF16 pieces, each the rounding of what the earlier ones left
+#pragma unroll
+    for (int pc = 0; pc < 3; ++pc) {
+        __nv_bfloat16 o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o[k] = __float2bfloat16_rn(v[k]);
+            v[k] = __fsub_rn(v[k], __bfloat162float(o[k]));
+        }
+        __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(qb + pc * pstride + (long)b * rp + 4 * t);
+        dst[0] = __halves2bfloat162(o[0], o[1]);
+        dst[1] = __halves2bfloat162(o[2], o[3]);
+    }
 }
 
 // Interactions of T targets (leaf units, hi + lo words) with the staged
@@ -218,12 +290,13 @@ __device__ __forceinline__ void self_run(const float4* __restrict__ sh, const fl
 }
 
 // Block b, every point i of leaf b (leaf units):
-//   out[perm[i]] = scale * ( sum_{j < n} e[b][j] / |s_i - a u_j|                    (L2T, parts & 2)
-//                          + sum_{s near b} sum_{j in s, j != i} q_j / |s_i - 2 delta_s - s_j| )
+//   out[perm[i]] = trows[i] . p~_b                                                   (far field, parts & 2)
+//                + scale * sum_{s near b} sum_{j in s, j != i} q_j / |s_i - 2 delta_s - s_j|
 //                                                                                     (S2T, parts & 1)
-// with a = 3 - 2d the downward equivalent surface and scale = 1 / (4 pi h);
-// double layer (DL): the near sum is scale_dl * sum q_j n_j . d / |d|^3 with
-// scale_dl = 1 / (4 pi h^2), the L2T part unchanged.
+// with trows[i] the point's T~ row (T~ + L2T of Sec. 3.3 for that point,
+// formed in FP64 by point_rows_kernel), p~_b the leaf's compressed downward
+// check potentials and scale = 1 / (4 pi h); double layer (DL): the near sum
+// is scale_dl * sum q_j n_j . d / |d|^3 with scale_dl = 1 / (4 pi h^2).
 // Each thread takes two targets (i and i + kEvalThreads) when the pass has
 // more than kEvalThreads of them, one otherwise.  The near sources are
 // staged kNearCap at a time, every neighbour's hi word shifted by its
@@ -233,8 +306,8 @@ template <bool DL>
 __global__ void __launch_bounds__(kEvalThreads) leaf_eval_kernel(
     const float4* __restrict__ hi, const float4* __restrict__ lo, const float4* __restrict__ nhi,
     const float4* __restrict__ nlo, const int* __restrict__ leaf_start, const int4* __restrict__ leaf_ijk, const int* __restrict__ near_start,
-    const int* __restrict__ near_idx, const float4* __restrict__ usurf, int n, float a, float scale, float scale_dl,
-    const float* __restrict__ e, int lde, const int* __restrict__ perm, float* __restrict__ out, int parts) {
+    const int* __restrict__ near_idx, const float* __restrict__ trows, int rp, const float* __restrict__ pleaf,
+    float scale, float scale_dl, const int* __restrict__ perm, float* __restrict__ out, int parts) {
     __shared__ float4 src_hi[kNearCap];
     __shared__ float4 src_lo[kNearCap];
     __shared__ float4 src_nh[DL ? kNearCap : 1];
@@ -255,17 +328,28 @@ __global__ void __launch_bounds__(kEvalThreads) leaf_eval_kernel(
         }
         float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
         float accd[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // double layer: the near sum
+        float far[2] = {0.f, 0.f};
         if (parts & 2) {
-            // L2T: the surface points as sources with lo = 0 and the targets' own lo
+            // far field: the target's T~ row against the leaf's p~ (staged)
+            float* pbuf = reinterpret_cast<float*>(src_lo);
             __syncthreads();
-            for (int j = tid; j < n; j += kEvalThreads) {
-                const float4 u = __ldg(usurf + j);
-                src_hi[j] = make_float4(a * u.x, a * u.y, a * u.z, __ldg(e + (long)b * lde + j));
-                src_lo[j] = zero4;
+            for (int j = tid; j < rp; j += kEvalThreads) pbuf[j] = __ldg(pleaf + (long)b * rp + j);
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (it[t] >= end) continue;
+                const float4* row = reinterpret_cast<const float4*>(trows + (long)it[t] * rp);
+                const float4* pv = reinterpret_cast<const float4*>(pbuf);
+                float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int k = 0; k < rp / 4; ++k) {
+                    const float4 w = __ldg(row + k), pk = pv[k];
+                    d.x = fmaf(w.x, pk.x, d.x);
+                    d.y = fmaf(w.y, pk.y, d.y);
+                    d.z = fmaf(w.z, pk.z, d.z);
+                    d.w = fmaf(w.w, pk.w, d.w);
+                }
+                far[t] = (d.x + d.y) + (d.z + d.w);
             }
-            __syncthreads();
-            if (two) near_run<2>(src_hi, src_lo, 0, n, xh, xl, acc);
-            else near_run<1>(src_hi, src_lo, 0, n, xh, xl, acc);
         }
         if (parts & 1) {
             int k = nb, seg_off = 0;  // next near leaf and the part of it already staged
@@ -330,7 +414,7 @@ __global__ void __launch_bounds__(kEvalThreads) leaf_eval_kernel(
 #pragma unroll
         for (int t = 0; t < 2; ++t)
             if (it[t] < end) {
-                float v = scale * (acc[t][0] + acc[t][1]);
+                float v = fmaf(scale, acc[t][0] + acc[t][1], far[t]);
                 if (DL) v = fmaf(scale_dl, accd[t][0] + accd[t][1], v);
                 out[__ldg(perm + it[t])] = v;
             }
@@ -347,34 +431,39 @@ cudaError_t launch_gather_density(const float* q, const int* perm, float4* pts, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_check(const float4* hi, const float4* lo, const float4* nhi, const int* leaf_start,
-                              int n_leaves, const float4* usurf, int n, float a, float scale, float* out, int ld,
-                              cudaStream_t stream) {
+cudaError_t launch_point_rows(const double* pts, const double* nrm, int n_points, const double* ws, int rp, int n,
+                              const double* xsurf, double scale, float* rows, cudaStream_t stream) {
+    if (n_points <= 0) return cudaSuccess;
+    if (rp > kRowMaxK * 16 || rp % 16 != 0 || n < 1) return cudaErrorInvalidValue;
+    const int blocks = (n_points + kRowPts - 1) / kRowPts;
+    point_rows_kernel<<<blocks, 256, 0, stream>>>(pts, nrm, n_points, ws, rp, n, xsurf, scale, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_rows_sum(const float* rows, const float4* hi, const int* leaf_start, int n_leaves, int rp,
+                                 float* qf, __nv_bfloat16* qb, long pstride, cudaStream_t stream) {
     if (n_leaves <= 0) return cudaSuccess;
-    if (n > 2 * kCheckThreads || ld < n) return cudaErrorInvalidValue;
-    const int threads = ((n + 1) / 2 + 31) / 32 * 32;  // two check points per thread
-    if (nhi)
-        leaf_check_kernel<true><<<n_leaves, threads, 0, stream>>>(hi, lo, nhi, leaf_start, usurf, n, a, scale, out, ld);
-    else
-        leaf_check_kernel<false><<<n_leaves, threads, 0, stream>>>(hi, lo, nhi, leaf_start, usurf, n, a, scale, out, ld);
+    if (rp % 16 != 0 || rp > 1024) return cudaErrorInvalidValue;
+    const int threads = ((rp / 4) + 31) / 32 * 32;
+    leaf_rows_sum_kernel<<<n_leaves, threads, 0, stream>>>(rows, hi, leaf_start, rp, qf, qb, pstride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const float4* nhi, const float4* nlo,
                              const int* leaf_start, const int4* leaf_ijk, const int* near_start, const int* near_idx,
-                             int n_leaves, const float4* usurf, int n, float a, float scale, float scale_dl,
-                             const float* e, int lde, const int* perm, float* out, int parts, cudaStream_t stream) {
+                             int n_leaves, const float* trows, int rp, const float* pleaf, float scale, float scale_dl,
+                             const int* perm, float* out, int parts, cudaStream_t stream) {
     if (n_leaves <= 0) return cudaSuccess;
-    if ((parts & 2) && (!e || lde < n || n > kNearCap)) return cudaErrorInvalidValue;
+    if ((parts & 2) && (!trows || !pleaf || rp % 16 != 0 || rp > 4 * kNearCap)) return cudaErrorInvalidValue;
     if ((nhi == nullptr) != (nlo == nullptr)) return cudaErrorInvalidValue;
     if (nhi)
         leaf_eval_kernel<true><<<n_leaves, kEvalThreads, 0, stream>>>(hi, lo, nhi, nlo, leaf_start, leaf_ijk,
-                                                                      near_start, near_idx, usurf, n, a, scale,
-                                                                      scale_dl, e, lde, perm, out, parts);
+                                                                      near_start, near_idx, trows, rp, pleaf, scale,
+                                                                      scale_dl, perm, out, parts);
     else
         leaf_eval_kernel<false><<<n_leaves, kEvalThreads, 0, stream>>>(hi, lo, nhi, nlo, leaf_start, leaf_ijk,
-                                                                       near_start, near_idx, usurf, n, a, scale,
-                                                                       scale_dl, e, lde, perm, out, parts);
+                                                                       near_start, near_idx, trows, rp, pleaf, scale,
+                                                                       scale_dl, perm, out, parts);
     return cudaGetLastError();
 }
 

@@ -147,10 +147,12 @@ struct kifmm_m2l_plan_s {
     float core_inv_scale = 1.0f;               // 1 / tau (F16X3), else 1
     std::vector<double> U64;                   // [n][r] FP64 basis U~ (= R~)
     // compressed pass operators of Sec. 3.3 (point-source evaluation), on first use:
-    // Ws [rp][n_pad] (S~ factor), Wt [n_pad][rp] (T~ factor), M~ and L~ [8][rp][rp]
+    // Ws in FP64 [rp][n] (rows past the rank zero; the per-point S~ / T~ rows
+    // are formed from it), M~ and L~ [8][rp][rp] as 3 BF16 pieces each
     double pass_rcond = 0;
     int pass_kept = 0;
-    kifmm::DevBuf<__nv_bfloat16> Wsb, Wtb, Mb, Lb;  // 3 BF16 pieces each
+    kifmm::DevBuf<double> Ws64;
+    kifmm::DevBuf<__nv_bfloat16> Mb, Lb;
     int next_fmm_instance = 0;
     std::set<kifmm_fmm_s*> fmms;  // live point-source trees on this plan
     // stage 2 (Sec. 3.2): per-offset low-rank cores, off until kifmm_m2l_set_stage2
