@@ -241,6 +241,20 @@ int kifmm_m2l_apply_batch(int n_items, const kifmm_m2l_batch_item* items, int us
 int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                           const float* q_up, float* p_down, float beta, void* stream);
 
+/* The same uncompressed M2L (Eq. (4)) on the tensor cores, in the plan's
+ * f16x3 arithmetic: the q_up rows as two FP16 pieces after per-row
+ * power-of-two scaling, K_o as two FP16 pieces of tau K_o, the products
+ * hi*lo + lo*hi + hi*hi accumulated in FP32 (the compressed core's kernel
+ * with K = N = n_pad), so that compressed and uncompressed M2L compare at
+ * equal accuracy on equal hardware.  The first call forms the FP16 pieces
+ * of K_o (2 * 316 * n_pad^2 halfs, 117 MB at p = 8) and its operand buffers
+ * grow with the level's rows like kifmm_m2l_apply's.  Same layouts and beta
+ * rule as kifmm_m2l_apply; rows reduced with TMA bulk additions (summation
+ * order not fixed).  Errors: KIFMM_ERR_UNSUPPORTED unless the plan's
+ * precision is KIFMM_PREC_F16X3 and its kernel Laplace. */
+int kifmm_m2l_apply_dense_tc(kifmm_m2l_plan plan, int instance, int level, int nrhs,
+                             const float* q_up, float* p_down, float beta, void* stream);
+
 /* Synchronise `stream` and report device-side failures of earlier applies
  * on this plan: KIFMM_ERR_TIMEOUT when a bounded wait inside the
  * tensor-core kernel ran out (results of that apply are invalid; the flag

@@ -29,7 +29,7 @@ N_OFFSETS = 316
 # every symbol include/kifmm_m2l.h declares
 EXPORTED = (
     "kifmm_m2l_precompute", "kifmm_m2l_destroy", "kifmm_m2l_plan_rank", "kifmm_m2l_set_level",
-    "kifmm_m2l_level_pairs", "kifmm_m2l_apply", "kifmm_m2l_apply_adjoint", "kifmm_m2l_apply_dense",
+    "kifmm_m2l_level_pairs", "kifmm_m2l_apply", "kifmm_m2l_apply_adjoint", "kifmm_m2l_apply_dense", "kifmm_m2l_apply_dense_tc",
     "kifmm_m2l_apply_noalloc", "kifmm_m2l_apply_levels", "kifmm_m2l_apply_levels_adjoint",
     "kifmm_m2l_apply_batch",
     "kifmm_m2l_set_stage2", "kifmm_m2l_stage2_ranks", "kifmm_m2l_stage2_host",
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_apply": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_adjoint": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_dense": [vp, i32, i32, i32, vp, vp, f32, vp],
+        "kifmm_m2l_apply_dense_tc": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_noalloc": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_levels": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_levels_adjoint": [vp, i32, i32, i32, i32, vp, vp, f32, vp],

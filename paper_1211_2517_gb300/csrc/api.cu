@@ -1142,4 +1142,111 @@ int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs
     return KIFMM_OK;
 }
 
+int kifmm_m2l_apply_dense_tc(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* q_up,
+                             float* p_down, float beta, void* stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if (plan->prm.precision != KIFMM_PREC_F16X3 || plan->prm.kernel_id != KIFMM_KERNEL_LAPLACE) {
+        set_error("the tensor-core dense M2L runs the f16x3 arithmetic of Laplace plans (KIFMM_PREC_F16X3)");
+        return KIFMM_ERR_UNSUPPORTED;
+    }
+    LevelState* ls = find_level(plan, instance, level);
+    if (!ls) {
+        set_error("level not registered: call kifmm_m2l_set_level first");
+        return KIFMM_ERR_STATE;
+    }
+    if (nrhs < 1 || (ls->n_boxes > 0 && (!q_up || !p_down))) {
+        set_error("invalid nrhs or NULL density pointer");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(q_up) & 15) || (reinterpret_cast<uintptr_t>(p_down) & 15)) {
+        set_error("density pointers must be 16-byte aligned");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    int st = check_device(plan);
+    if (st != KIFMM_OK) return st;
+    const int n = plan->n, np = plan->n_pad;
+    if (!plan->Kd.ptr) {
+        // K_o as two FP16 pieces of tau K_o, tau the power of two that puts
+        // max |K_o| in [2^13, 2^14); the core divides by tau in its output scale
+        int offs[kOffsets][3];
+        offsets316(offs);
+        const std::vector<double> u = unit_surface(plan->prm.p);
+        std::vector<double> kd((size_t)kOffsets * n * n);
+        for (int k = 0; k < kOffsets; ++k)
+            unit_m2l_matrix(plan->prm.p, plan->prm.d, offs[k], u, kd.data() + (size_t)k * n * n, 0.0);
+        double kmax = 0;
+        for (double v : kd) kmax = std::max(kmax, std::fabs(v));
+        int e2 = 0;
+        std::frexp(kmax > 0 ? kmax : 1.0, &e2);
+        const double tau = std::ldexp(1.0, 14 - e2);
+        const size_t per = (size_t)kOffsets * np * np;
+        std::vector<uint16_t> h(per * 2, 0);
+        for (int k = 0; k < kOffsets; ++k)
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) {
+                    const double v = tau * kd[((size_t)k * n + a) * n + b];
+                    const size_t e = ((size_t)k * np + a) * np + b;
+                    h[e] = f16_bits_rn(v);
+                    h[per + e] = f16_bits_rn(v - f16_bits_to_double(h[e]));
+                }
+        KIFMM_CUDA_TRY(plan->Kd.ensure(h.size()));
+        KIFMM_CUDA_TRY(cudaMemcpy(plan->Kd.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
+        plan->dense_inv_scale = (float)(1.0 / tau);
+    }
+    if (ls->n_boxes == 0) return KIFMM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long rows = (long)ls->n_boxes * nrhs;
+    if (rows + 1 > (long)INT32_MAX / 2) {
+        set_error("too many box rows");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    const long pstride = (rows + 1) * np;
+    KIFMM_CUDA_TRY(plan->dq.ensure((size_t)2 * pstride));
+    KIFMM_CUDA_TRY(plan->dq_inv.ensure((size_t)rows + 1));
+    KIFMM_CUDA_TRY(plan->dp.ensure((size_t)rows * np));
+    // operand: the q_up rows as scaled FP16 pieces (zero row last), output zeroed
+    KIFMM_CUDA_TRY(launch_split_rows_f16_scaled(q_up, (int)rows, n, n, np, reinterpret_cast<__half*>(plan->dq.ptr),
+                                                pstride, plan->dq_inv.ptr, s));
+    for (int pc = 0; pc < 2; ++pc)
+        KIFMM_CUDA_TRY(cudaMemsetAsync(plan->dq.ptr + pc * pstride + rows * np, 0, np * sizeof(__nv_bfloat16), s));
+    KIFMM_CUDA_TRY(cudaMemsetAsync(plan->dq_inv.ptr + rows, 0, sizeof(float), s));
+    KIFMM_CUDA_TRY(launch_zero(plan->dp.ptr, rows * np, s));
+    TileSet* ts = nullptr;
+    st = get_tiles(ls->fwd, nrhs, &ts);
+    if (st != KIFMM_OK) return st;
+    UmmaArgs a{};
+    a.A = plan->dq.ptr;
+    a.a_piece_stride = pstride;
+    a.kdim = np;
+    a.B = plan->Kd.ptr;
+    a.b_groups = kOffsets;
+    a.ndim = np;
+    a.n_chunk = ((np / 2 + 15) / 16) * 16;
+    a.core_bres = 1;
+    a.core_drain = 3;
+    a.contiguous = 1;
+    a.row_src = ts->row_src.ptr;
+    a.row_dst = ts->row_dst.ptr;
+    a.tile_k = ts->tile_k.ptr;
+    a.n_tiles = ts->n_tiles;
+    a.nrhs = nrhs;
+    a.zero_row = (int)rows;
+    a.level_scale[0] = (float)std::ldexp(1.0 / ls->r0, level) * plan->dense_inv_scale;
+    a.D = plan->dp.ptr;
+    a.ldd = np;
+    a.n_products = 3;
+    a.hilo = 1;
+    a.f16 = 1;
+    a.row_scale = plan->dq_inv.ptr;
+    a.error_flag = plan->err_flag.ptr;
+    a.wait_ns = plan->core_wait_ns;
+    KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
+    // p_down = beta p_down + the first n columns
+    KIFMM_CUDA_TRY(launch_copy_rows(p_down, n, plan->dp.ptr, np, rows, n, beta, s));
+    return KIFMM_OK;
+}
+
 }  // extern "C"

@@ -75,6 +75,10 @@ cudaError_t launch_leaf_eval(const float4* hi, const float4* lo, const float4* n
 cudaError_t launch_split_rows_f16_scaled(const float* A, int m_rows, int lda, int cols, int ldo, __half* out,
                                          long piece_stride, float* inv, cudaStream_t stream);
 
+// dst[r][c] = src[r][c] + beta dst[r][c] for r < rows, c < cols.
+cudaError_t launch_copy_rows(float* dst, int ldd, const float* src, int lds, long rows, int cols, float beta,
+                             cudaStream_t stream);
+
 // Zero `count` floats.
 cudaError_t launch_zero(float* x, long count, cudaStream_t stream);
 

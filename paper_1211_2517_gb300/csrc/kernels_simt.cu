@@ -307,6 +307,28 @@ cudaError_t launch_split_rows_f16_scaled(const float* A, int m_rows, int lda, in
     return cudaGetLastError();
 }
 
+// dst[r][c] = src[r][c] + beta * dst[r][c] for c < cols (beta == 0: no read
+// of dst), rows of ldd and lds floats.
+__global__ void copy_rows_kernel(float* __restrict__ dst, int ldd, const float* __restrict__ src, int lds, long rows,
+                                 int cols, float beta) {
+    const long total = rows * cols;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long r = e / cols;
+        const int c = (int)(e % cols);
+        const float v = src[r * lds + c];
+        dst[r * ldd + c] = beta == 0.f ? v : fmaf(beta, dst[r * ldd + c], v);
+    }
+}
+
+cudaError_t launch_copy_rows(float* dst, int ldd, const float* src, int lds, long rows, int cols, float beta,
+                             cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    long blocks = (rows * cols + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    copy_rows_kernel<<<(int)blocks, 256, 0, stream>>>(dst, ldd, src, lds, rows, cols, beta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_zero(float* x, long count, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
     if ((count & 3) != 0 || (reinterpret_cast<uintptr_t>(x) & 15) != 0)

@@ -143,6 +143,11 @@ struct kifmm_m2l_plan_s {
     int variant_bres() const { return tune_variant == 13 ? 1 : 0; }
     int variant_bulk() const { return (tune_variant == 4 || tune_variant == 5) ? 1 : 0; }
     kifmm::DevBuf<float> C, K;
+    // tensor-core dense baseline (f16x3 plans): K_o as two FP16 pieces of
+    // tau_K K_o [2][316][n_pad][n_pad], 1 / tau_K, and its operand / output buffers
+    kifmm::DevBuf<__nv_bfloat16> Kd, dq;
+    kifmm::DevBuf<float> dq_inv, dp;
+    float dense_inv_scale = 1.0f;
     kifmm::DevBuf<__nv_bfloat16> Cb, Rtb, Ub;  // 3 BF16 pieces each (Cb: 2 FP16 pieces of tau K~ for F16X3)
     float core_inv_scale = 1.0f;               // 1 / tau (F16X3), else 1
     std::vector<double> U64;                   // [n][r] FP64 basis U~ (= R~)

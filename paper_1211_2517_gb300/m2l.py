@@ -201,6 +201,10 @@ class M2LPlan:
         """Uncompressed FP32 M2L (the baseline)."""
         return self._run("kifmm_m2l_apply_dense", q_up, level, instance, out, beta, stream)
 
+    def apply_dense_tc(self, q_up, level: int, instance: int = 0, out=None, beta: float = 0.0, stream=None):
+        """Uncompressed M2L on the tensor cores in f16x3 arithmetic (the baseline at equal accuracy)."""
+        return self._run("kifmm_m2l_apply_dense_tc", q_up, level, instance, out, beta, stream)
+
     def profile(self, enable: bool = True) -> None:
         """Turn per-stage CUDA-event tracing on or off."""
         call("kifmm_m2l_profile_enable", self._h, 1 if enable else 0)

@@ -111,6 +111,41 @@ def test_dense_parity(g, cube):
         assert err <= 1e-6, err
 
 
+def test_dense_tensor_core_parity(g, cube, sphere_small):
+    """The uncompressed M2L on the tensor cores (f16x3 pieces of q^u and K_o,
+    K = N = n_pad: p = 6 -> 160, p = 8 -> 304 in two N parts) against the
+    oracle's FP64 dense M2L: cube levels 2-3 and sphere levels 2-4 with 3
+    rhs, both beta rules."""
+    wl, qup = cube
+    K6 = om.unit_m2l_matrices(wl.p, wl.d)
+    plan = make_plan(g, wl.p, wl.eps, "f16x3", wl.tree, (2, 3))
+    for l in (2, 3):
+        ref = om.m2l_dense_unit(wl.tree.levels[l], l, wl.tree.r0, K6, qup[l].astype(np.float64))
+        out = plan.apply_dense_tc(torch.from_numpy(qup[l]).cuda(), l)
+        plan.sync()
+        err = rel(out.cpu().numpy(), ref)
+        print(f"dense tensor-core p=6 level {l}: rel L2 {err:.3e}")
+        assert err <= 1e-6, err
+    plan.close()
+    tree, qs = sphere_small
+    K8 = om.unit_m2l_matrices(8, 0.1)
+    plan = make_plan(g, 8, 1e-7, "f16x3", tree, (2, 3, 4))
+    for l in (2, 3, 4):
+        ref = om.m2l_dense_unit(tree.levels[l], l, tree.r0, K8, qs[l].astype(np.float64))
+        x = torch.from_numpy(qs[l]).cuda()
+        out = plan.apply_dense_tc(x, l)
+        plan.sync()
+        err = rel(out.cpu().numpy(), ref)
+        prev = torch.randn_like(out)
+        acc = prev.clone()
+        plan.apply_dense_tc(x, l, out=acc, beta=1.0)
+        plan.sync()
+        err_b = rel((acc - prev).cpu().numpy(), ref)
+        print(f"dense tensor-core p=8 level {l} (3 rhs): rel L2 {err:.3e}, accumulate {err_b:.3e}")
+        assert err <= 1e-6 and err_b <= 1e-6, (err, err_b)
+    plan.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "split6", "f16x3"])
 def test_adjoint_parity_and_dot_product(g, oracle_factors, sphere_small, precision):
     tree, qs = sphere_small
