@@ -170,7 +170,12 @@ int kifmm_m2l_level_pairs(kifmm_m2l_plan plan, int instance, int level, int64_t*
  * q_up, p_down: DEVICE float32 [n_boxes][nrhs][n]; they must not overlap.
  * beta is 0 (overwrite; p_down need not be initialised) or any value
  * (accumulate, Step 3.1 "add to the downward check potentials").
- * nrhs >= 1.  Runs on `stream`. */
+ * nrhs >= 1.  Runs on `stream`.
+ * Reproducibility: the core adds every pair's contribution into its
+ * target's p~ row with global atomic or TMA bulk reductions, whose order is
+ * not fixed, so two calls on the same input can differ in the last bits
+ * (well inside the stated error; an iterative solver or an adjoint check
+ * that needs bit-identical repeats must not rely on them). */
 int kifmm_m2l_apply(kifmm_m2l_plan plan, int instance, int level, int nrhs,
                     const float* q_up, float* p_down, float beta, void* stream);
 
