@@ -461,8 +461,9 @@ def run_ours(args, rank, world, local_rank):
     # counterpart, and the plan that stage 2 and the point-source evaluation
     # (BF16 modes) run on ----------------------------------------------------
     plan6, split6 = plan, None
-    legs = not args.headline_only
-    if args.precision == "f16x3" and legs:
+    legs = {"split6", "noalloc", "stage2", "fmm", "yukawa", "torus", "batch64"} if args.legs == "all" else \
+        set(x for x in args.legs.split(",") if x and x != "none")
+    if args.precision == "f16x3" and legs & {"split6", "noalloc", "stage2"}:
         plan6 = M2LPlan(wl.p, wl.eps, wl.d, "split6")
         for l in LEVELS:
             plan6.set_level(l, tree.levels[l], tree.r0)
@@ -487,7 +488,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- the allocation-free apply beside kifmm_m2l_apply: level 6 of the
     # workload (its scratch fits the 64 MiB static array), split6 -----------
     noalloc = None
-    if args.precision != "fp32" and legs:
+    if args.precision != "fp32" and "noalloc" in legs:
         import ctypes
 
         from paper_1211_2517_gb300 import _lib
@@ -514,8 +515,9 @@ def run_ours(args, rank, world, local_rank):
                    "note": "kifmm_m2l_apply_noalloc against kifmm_m2l_apply on the same level and plan"}
 
     # ---- stage 2 (Sec. 3.2): per-offset low-rank cores, c2 = 10 ----------
+    plan_main = plan
     stage2 = None
-    if args.precision != "fp32" and legs:
+    if args.precision != "fp32" and "stage2" in legs:
         plan, plan_main = plan6, plan
         step_main = step
         step = step6
@@ -542,7 +544,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- complete evaluation for the workload's points (Sec. 4 with the
     # compressed passes of Sec. 3.3): near field + S~, M~, M2L, L~, T~ ------
     fmm = None
-    if args.precision != "fp32" and legs:
+    if args.precision != "fp32" and "fmm" in legs:
         from paper_1211_2517_gb300 import PointFMM
 
         ftree = PointFMM(plan_main, wl.points, wl.depth)
@@ -584,7 +586,7 @@ def run_ours(args, rank, world, local_rank):
     # kernel exp(-kappa r) / (4 pi r), one plan per level, the same levels and
     # densities as the headline --------------------------------------------
     yukawa = None
-    if args.precision != "fp32" and not args.no_yukawa and legs:
+    if args.precision != "fp32" and not args.no_yukawa and "yukawa" in legs:
         try:
             kappa = 3.0
             t0 = time.time()
@@ -618,11 +620,12 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- config 3 (p = 10 torus) and config 4 (64-instance batch) ----------
     torus = batch64 = None
-    if args.precision != "fp32" and not args.no_extra and legs:
+    if args.precision != "fp32" and not args.no_extra and "torus" in legs:
         try:
             torus = torus_measure(args, dev, min(args.steps, 50), bf16_peak)
         except Exception as exc:  # a secondary leg: reported, the headline line still prints
             torus = {"error": f"{type(exc).__name__}: {exc}"}
+    if args.precision != "fp32" and not args.no_extra and "batch64" in legs:
         try:
             kb = min(args.steps, 10)
             bv, bms, bpairs, bach, _ = batch64_measure(args, rank, world, dev, kb, 3, False)
@@ -631,7 +634,9 @@ def run_ours(args, rank, world, local_rank):
                        "roofline": {"bound": "tensor", "achieved": bach, "peak": bf16_peak, "unit": "TFLOP/s",
                                     "frac": bach / bf16_peak, "flops_per_unit": "2 r^2 per box pair and rhs",
                                     "time": "whole batch (compression, core and expansion of three operators)"},
-                       "parity": "tests/test_gpu_m2l.py::test_batch64_full_config"}
+                       "parity": "tests/test_gpu_m2l.py::test_batch64_full_config",
+                       "arithmetic": "config 4 names FP32; the batch runs the plan's tensor-core arithmetic "
+                                     f"({args.precision}), which meets the FP32 gate of 1e-6 against the oracle"}
         except Exception as exc:
             batch64 = {"error": f"{type(exc).__name__}: {exc}"}
 
@@ -845,9 +850,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle leg")
     ap.add_argument("--no-yukawa", action="store_true", help="skip the per-level Yukawa leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the torus4m_p10 and batch64 legs")
-    ap.add_argument("--headline-only", action="store_true",
-                    help="time the headline step only (no split6, stage-2, allocation-free, point-source, Yukawa, "
-                         "torus or batch legs; for profiler runs)")
+    ap.add_argument("--legs", default="all",
+                    help="secondary legs to run besides the headline step, comma-separated from split6, noalloc, "
+                         "stage2, fmm, yukawa, torus, batch64; 'all' (default) or 'none' (profiler runs)")
     ap.add_argument("--workload", choices=("sphere2m_p8", "batch64"), default="sphere2m_p8",
                     help="sphere2m_p8: the headline configuration; batch64: the 64-instance mixed batch")
     args = ap.parse_args()
