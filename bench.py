@@ -596,13 +596,15 @@ def run_ours(args, rank, world, local_rank):
                 yp.set_level(l, tree.levels[l], tree.r0)
                 yplans[l] = yp
             setup_s = time.time() - t0
-            if not args.no_autotune:
-                for l, yp in yplans.items():
-                    yp.autotune(q[l], l, l, reps=2, out=out[l])
+            from paper_1211_2517_gb300 import apply_batch
+
+            # the five level plans as one batch: one grouped core launch,
+            # replayed from a CUDA graph
+            yitems = [{"plan": yp, "level_lo": l, "level_hi": l, "x": q[l], "out": out[l]}
+                      for l, yp in yplans.items()]
 
             def ystep():
-                for l, yp in yplans.items():
-                    yp.apply(q[l], l, out=out[l])
+                apply_batch(yitems, use_graph=True)
 
             for _ in range(3):
                 ystep()
@@ -610,9 +612,10 @@ def run_ours(args, rank, world, local_rank):
             k_y = min(args.steps, 20)
             y_ms = timed(ystep, k_y)
             yukawa = {"value": total_pairs * k_y / (y_ms / 1e3), "unit": UNIT, "ms_per_step": y_ms / k_y,
+                      "mode": "one batch of the level plans (one grouped core launch) from a CUDA graph",
                       "kappa": kappa, "ranks_by_level": {str(l): yp.r for l, yp in yplans.items()},
                       "precompute_s_all_levels": setup_s, "precision": args.precision,
-                      "parity": "tests/test_gpu_m2l.py::test_yukawa_per_level_plans"}
+                      "parity": "tests/test_gpu_m2l.py::test_yukawa_per_level_plans, ::test_yukawa_levels_one_batch"}
             for yp in yplans.values():
                 yp.close()
         except Exception as exc:  # a secondary leg: reported, the headline line still prints

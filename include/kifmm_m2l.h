@@ -224,9 +224,14 @@ typedef struct kifmm_m2l_batch_item {
 /* Compressed M2L of many FMM instances of uneven sizes (and of several
  * operators, e.g. different p) in one batch (Step 3.1 for every instance).
  * Items are grouped by plan; for each plan one split and one persistent
- * compression launch, one core launch, and one split and one expansion
- * launch cover all its items (the core walks one
- * offset-ordered tile list merged over every item and level).  Tables and
+ * compression launch and one split and one expansion launch cover all its
+ * items, and the cores of all plans are one launch (each plan a group with
+ * its own cores, rank and offset-ordered tile list merged over its items and
+ * levels; the launch's CTAs split the summed work) when the plans share an
+ * arithmetic with 1 or 2 pieces (bf16, split3, f16x3), use no stage 2 and
+ * number at most 8; otherwise one core launch per plan.  A bounded-wait
+ * timeout of a grouped core launch is reported by kifmm_m2l_sync of the
+ * first plan in item order.  Tables and
  * scratch of a batch are built on its first call and cached by the batch's
  * signature (plans, instances, levels, nrhs, pointers, beta); the cached
  * batches of a plan are dropped by kifmm_m2l_set_level and by

@@ -2,14 +2,18 @@
 // sizes, several operators p, several right-hand-side counts) as one
 // grouped batch.
 //
-// Items are grouped by plan (one operator each).  Per plan, three
-// persistent launches cover every item of the group:
+// Items are grouped by plan (one operator each).  Per plan, persistent
+// launches cover every item of the group:
 //   compression  one rows-mode launch over the items' rows (a segment table
 //                maps row tiles to each item's input buffer),
 //   core         one offset-ordered tile list merged over all items and
 //                levels (row tables in a batch-wide row space, a scale table
 //                with s_l of every (item, level)),
 //   expansion    one rows-mode launch writing each item's output buffer.
+// When every plan's core runs on the staged-epilogue kernel (1 or 2 pieces,
+// the same arithmetic, no stage 2, at most 8 plans), the cores of all plans
+// are one launch: each plan is a group with its own K~_o, rank and tile
+// list, and the launch's CTAs share the summed work.
 // With use_graph the whole batch is captured once into a CUDA graph, cached
 // by the batch's signature, and replayed by later calls.
 #include <cuda_runtime.h>
@@ -49,6 +53,7 @@ struct PlanGroup {
 
 struct BatchEntry {
     std::vector<std::unique_ptr<PlanGroup>> groups;
+    bool one_core = false;  // the cores of all groups in one grouped launch
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture_stream = nullptr;
     ~BatchEntry() {
@@ -158,13 +163,11 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     return KIFMM_OK;
 }
 
-// Enqueue the launches of one plan group on stream s: split and
-// compression (plus the scaled FP16 split for f16x3), core, split and
-// expansion.
-int enqueue_group(PlanGroup& g, cudaStream_t s) {
+// Split and compression of one plan group (plus the scaled FP16 split for
+// f16x3): the core's q~ pieces, p~ cleared.
+int enqueue_compress(PlanGroup& g, cudaStream_t s) {
     kifmm_m2l_plan plan = g.plan;
-    if (g.rows_total == 0) return KIFMM_OK;
-    const int n = plan->n, rp = plan->rp;
+    const int rp = plan->rp;
     const bool f16 = plan->prm.precision == KIFMM_PREC_F16X3;
     const long piece_stride = (g.rows_total + 1) * rp;
     {
@@ -180,8 +183,17 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
             KIFMM_CUDA_TRY(cudaMemsetAsync(g.qb.ptr + pc * piece_stride + g.rows_total * rp, 0,
                                            rp * sizeof(__nv_bfloat16), s));
     }
+    return KIFMM_OK;
+}
+
+// The core operands of one plan group.
+UmmaArgs core_args(PlanGroup& g) {
+    kifmm_m2l_plan plan = g.plan;
+    const int rp = plan->rp;
+    const bool f16 = plan->prm.precision == KIFMM_PREC_F16X3;
+    const long piece_stride = (g.rows_total + 1) * rp;
+    UmmaArgs a{};
     {
-        UmmaArgs a{};
         a.A = g.qb.ptr;
         a.a_piece_stride = piece_stride;
         a.kdim = rp;
@@ -215,19 +227,57 @@ int enqueue_group(PlanGroup& g, cudaStream_t s) {
         a.row_scale = f16 ? g.qs.ptr : nullptr;
         a.error_flag = plan->err_flag.ptr;
         a.wait_ns = plan->core_wait_ns;
-        KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, plan->num_sms, s));
     }
-    {
-        const int st = run_expand(plan, nullptr, 0, g.seg_out.ptr, (int)g.items.size(), g.in_tiles, g.sp.ptr,
-                                  nullptr, 1.0f, 0.0f, s);
-        if (st != KIFMM_OK) return st;
+    return a;
+}
+
+int enqueue_expand(PlanGroup& g, cudaStream_t s) {
+    return run_expand(g.plan, nullptr, 0, g.seg_out.ptr, (int)g.items.size(), g.in_tiles, g.sp.ptr, nullptr, 1.0f,
+                      0.0f, s);
+}
+
+// Whether the cores of all groups can be one grouped launch.
+bool one_core_launch(const BatchEntry& e) {
+    if (e.groups.empty() || e.groups.size() > 8) return false;
+    const kifmm_m2l_plan p0 = e.groups[0]->plan;
+    for (const auto& g : e.groups) {
+        const kifmm_m2l_plan p = g->plan;
+        if (p->s2_on || (p->products != 1 && p->products != 3) || p->products != p0->products ||
+            p->prm.precision != p0->prm.precision || p->num_sms != p0->num_sms || p->rp % 16 != 0)
+            return false;
     }
-    return KIFMM_OK;
+    return true;
 }
 
 int enqueue_all(BatchEntry& e, cudaStream_t s) {
+    if (!e.one_core) {
+        for (auto& g : e.groups) {
+            if (g->rows_total == 0) continue;
+            int st = enqueue_compress(*g, s);
+            if (st != KIFMM_OK) return st;
+            const UmmaArgs a = core_args(*g);
+            KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, g->plan->num_sms, s));
+            st = enqueue_expand(*g, s);
+            if (st != KIFMM_OK) return st;
+        }
+        return KIFMM_OK;
+    }
+    std::vector<UmmaArgs> args;
     for (auto& g : e.groups) {
-        int st = enqueue_group(*g, s);
+        if (g->rows_total == 0) continue;
+        int st = enqueue_compress(*g, s);
+        if (st != KIFMM_OK) return st;
+        args.push_back(core_args(*g));
+    }
+    if (args.empty()) return KIFMM_OK;
+    int dev = 0, max_smem = 0;
+    KIFMM_CUDA_TRY(cudaGetDevice(&dev));
+    KIFMM_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KIFMM_CUDA_TRY(launch_core_stage_grouped(args.data(), (int)args.size(), e.groups[0]->plan->num_sms, max_smem,
+                                             dev, s));
+    for (auto& g : e.groups) {
+        if (g->rows_total == 0) continue;
+        int st = enqueue_expand(*g, s);
         if (st != KIFMM_OK) return st;
     }
     return KIFMM_OK;
@@ -305,6 +355,7 @@ extern "C" int kifmm_m2l_apply_batch(int n_items, const kifmm_m2l_batch_item* it
             int st = build_group(*g, items);
             if (st != KIFMM_OK) return st;
         }
+        ne->one_core = one_core_launch(*ne);
         if (g_batches.size() >= 16) g_batches.clear();
         e = ne.get();
         g_batches[sig] = std::move(ne);

@@ -185,6 +185,12 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& args, int num_sms,
 // p~ by TMA bulk reductions (kernels_core.cu): 1 or 2 pieces (n_products 1
 // or 3); cudaErrorNotSupported when the operands do not fit.
 cudaError_t launch_core_stage(const UmmaArgs& args, int num_sms, int max_smem, int dev, cudaStream_t stream);
+// The same kernel over up to 8 operators at once (one launch for a batch of
+// plans): group i takes its operands, tile list, scale table (required when
+// n_groups > 1) and p~ from args[i]; every group has the same piece count
+// and FP16 flag, and the launch's error flag and wait bound are args[0]'s.
+cudaError_t launch_core_stage_grouped(const UmmaArgs* args, int n_groups, int num_sms, int max_smem, int dev,
+                                      cudaStream_t stream);
 // Its shared-memory need (0: does not fit max_smem), ring stages in *stages.
 size_t core_stage_smem(int pieces, int kdim, int ndim, int max_smem, int* stages);
 

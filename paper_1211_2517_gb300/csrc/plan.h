@@ -125,7 +125,8 @@ struct kifmm_m2l_plan_s {
     // two K-chunks drained into registers, 3 / 5 of one, 6 / 10 of three
     // (f16x3); 4 / 5 reduce the rows into p~ with TMA bulk reductions
     // instead of vector atomics; 9 / 10 issue two K-chunks per MMA step,
-    // 11 (f16x3) a whole partial of three; 13 keeps K~_o in shared memory
+    // 11 (f16x3) a whole partial of three; 13 (1 or 2 pieces) the staged
+    // epilogue whose rows reach p~ by TMA bulk reductions (kernels_core.cu)
     int variant_drain() const {
         switch (tune_variant) {
             case 2: case 4: return 2;
@@ -139,7 +140,6 @@ struct kifmm_m2l_plan_s {
         return (tune_variant == 11 || tune_variant == 12) ? 3 : (tune_variant == 9 || tune_variant == 10) ? 2 : 1;
     }
     int variant_direct() const { return tune_variant == 12 ? 1 : 0; }
-    // 13 (1 or 2 pieces): K~_o resident in shared memory, only the A rows streamed
     int variant_bres() const { return tune_variant == 13 ? 1 : 0; }
     int variant_bulk() const { return (tune_variant == 4 || tune_variant == 5) ? 1 : 0; }
     kifmm::DevBuf<float> C, K;

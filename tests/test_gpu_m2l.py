@@ -713,11 +713,14 @@ def _ellipsoid_batch(n_inst, seed0=0):
     return out
 
 
-@pytest.mark.parametrize("precision", ["split6", "f16x3"])
+@pytest.mark.parametrize("precision", ["split6", "split3", "f16x3"])
 def test_batch_matches_levels_and_graph_replay(g, oracle_factors, precision):
     """kifmm_m2l_apply_batch over instances of uneven sizes and three
     operators (p = 6, 8, 10) against each instance's own batched-levels
-    apply, in eager and CUDA-graph mode, and one instance against the oracle."""
+    apply, in eager and CUDA-graph mode, and one instance against the oracle.
+    In split3 and f16x3 the three operators' cores are one grouped launch
+    (ranks 271 > 192 and smaller ones side by side); split6 runs one core
+    launch per operator."""
     from paper_1211_2517_gb300 import apply_batch
 
     inst = _ellipsoid_batch(9, 11)
@@ -760,7 +763,7 @@ def test_batch_matches_levels_and_graph_replay(g, oracle_factors, precision):
     for l in range(2, depth + 1):
         nb = tree.levels[l].shape[0]
         ref = om.m2l_svd(tree.levels[l], l, tree.r0, f, x[row:row + nb])
-        assert rel(o[row:row + nb], ref) <= 1e-6
+        assert rel(o[row:row + nb], ref) <= TOL[precision]
         row += nb
     for pl in plans.values():
         pl.close()
@@ -825,6 +828,40 @@ def test_batch64_full_config(g, oracle_factors):
 
 
 _YUKAWA = {}
+
+
+@pytest.mark.parametrize("precision", ["split3", "f16x3"])
+def test_yukawa_levels_one_batch(g, sphere_small, precision):
+    """The per-level Yukawa plans of levels 2-4 (each its own rank r_l and
+    cores, Sec. 3.1's O(L) case) applied as one batch, whose cores run as one
+    grouped launch, eager and replayed from a CUDA graph; each level against
+    the oracle's per-level factors."""
+    from paper_1211_2517_gb300 import apply_batch
+
+    tree, qs = sphere_small
+    kappa = 3.0
+    items, refs, ranks = [], [], []
+    for l in (2, 3, 4):
+        h = tree.r0 / (1 << l)
+        f = _yukawa_factors(kappa, h)
+        plan = g.M2LPlan(8, 1e-7, 0.1, precision, "yukawa", kappa, h)
+        plan.set_level(l, tree.levels[l], tree.r0)
+        ranks.append(plan.r)
+        x = torch.from_numpy(qs[l]).cuda()
+        items.append({"plan": plan, "level_lo": l, "level_hi": l, "x": x, "out": torch.empty_like(x)})
+        refs.append(om.m2l_svd(tree.levels[l], l, tree.r0, f, qs[l].astype(np.float64)))
+    assert len(set(ranks)) > 1, ranks  # the groups differ in rank
+    for use_graph in (False, True, True):
+        for it in items:
+            it["out"].fill_(float("nan"))
+        apply_batch(items, use_graph=use_graph)
+        torch.cuda.synchronize()
+        for l, it, ref in zip((2, 3, 4), items, refs):
+            err = rel(it["out"].cpu().numpy(), ref)
+            print(f"yukawa batch level {l} (r = {it['plan'].r}) {precision} graph={use_graph}: {err:.3e}")
+            assert err <= TOL[precision], (l, err)
+    for it in items:
+        it["plan"].close()
 
 
 def _yukawa_factors(kappa, h):
