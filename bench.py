@@ -604,7 +604,9 @@ def run_ours(args, rank, world, local_rank):
                       for l, yp in yplans.items()]
 
             def ystep():
+                torch.cuda.nvtx.range_push("yukawa_step")
                 apply_batch(yitems, use_graph=True)
+                torch.cuda.nvtx.range_pop()
 
             for _ in range(3):
                 ystep()
@@ -785,9 +787,11 @@ def batch64_measure(args, rank, world, dev, steps, warmup, sample_clocks):
     for _ in range(steps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("batch64_step")
         e0.record(stream)
         apply_batch(items, use_graph=True)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         evs.append((e0, e1))
     torch.cuda.synchronize()
     if world > 1:
