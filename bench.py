@@ -540,6 +540,28 @@ def run_ours(args, rank, world, local_rank):
                   "core_ms_per_step": s2_stage["core"] / min(k_s2, 20), "precision": "split6",
                   "parity": "tests/test_gpu_m2l.py::test_stage2_parity against the oracle's two-product M2L"}
         plan, step = plan_main, step_main
+        if args.precision == "f16x3":
+            # the same c2 on the headline plan's f16x3 arithmetic, against its
+            # single-stage core
+            plan.set_stage2(c2)
+            for _ in range(3):
+                step()
+            plan.sync()
+            f_ms = timed(step, k_s2)
+            plan.profile(True)
+            timed(step, min(k_s2, 20))
+            f_stage, _ = plan.profile_read()
+            plan.profile(False)
+            plan.set_stage2(0.0)
+            plan.profile(True)
+            timed(step, min(k_s2, 20))
+            one_stage, _ = plan.profile_read()
+            plan.profile(False)
+            plan.sync()
+            stage2["f16x3"] = {"value": total_pairs * k_s2 / (f_ms / 1e3), "unit": UNIT, "ms_per_step": f_ms / k_s2,
+                               "core_ms_per_step": f_stage["core"] / min(k_s2, 20),
+                               "single_stage_core_ms_per_step": one_stage["core"] / min(k_s2, 20),
+                               "parity": "tests/test_gpu_m2l.py::test_stage2_parity[f16x3]"}
 
     # ---- complete evaluation for the workload's points (Sec. 4 with the
     # compressed passes of Sec. 3.3): near field + S~, M~, M2L, L~, T~ ------

@@ -93,8 +93,10 @@ extern "C" {
                                        its largest entry in [2^14, 2^15), the cores by one
                                        that puts theirs in [2^13, 2^14), so both FP16 pieces
                                        stay normal where they matter; dropped terms <= 2^-22.
-                                       apply, apply_levels (and adjoints), apply_batch and
-                                       point-source evaluation; not stage 2 or apply_noalloc */
+                                       apply, apply_levels (and adjoints), apply_batch,
+                                       stage 2 (its factors and the rank-k_o intermediate
+                                       scaled the same way) and point-source evaluation;
+                                       not apply_noalloc */
 
 #define KIFMM_N_OFFSETS        316  /* unique M2L offsets per level, Sec. 3.1 */
 
@@ -337,10 +339,14 @@ int kifmm_m2l_apply_noalloc(kifmm_m2l_plan plan, int instance, int level, int nr
  * apply_noalloc on this plan (the adjoint uses the reversed offset's factors).
  * c2 <= 0 switches back to the single-stage cores.  Tensor-core precisions
  * only (KIFMM_PREC_FP32: KIFMM_ERR_UNSUPPORTED); every k_o must be <= 96 and
- * r_pad <= 320 (else KIFMM_ERR_UNSUPPORTED: take a larger c2).  Host work:
- * the FP64 factors (from the plan's cache if $KIFMM_M2L_CACHE is set, else
- * recomputed) and 316 r x r SVDs; device memory: 2 x 3 x 316 x 96 x r_pad
- * BF16 values. */
+ * r_pad <= 320 (else KIFMM_ERR_UNSUPPORTED: take a larger c2).  In
+ * KIFMM_PREC_F16X3 the factors are two FP16 pieces of tau_V Vhat and tau_U
+ * Uhat (powers of two, largest entry in [2^13, 2^14)) and each row of the
+ * intermediate Vhat_o q~ is split into two FP16 pieces after its own power
+ * of two; the output row undoes all of them.  Drops this plan's cached
+ * batches.  Host work: the FP64 factors (from the plan's cache if
+ * $KIFMM_M2L_CACHE is set, else recomputed) and 316 r x r SVDs; device
+ * memory: 2 x 3 x 316 x 96 x r_pad 2-byte values. */
 int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2);
 
 /* The per-offset ranks k_o of stage 2 (k[316], HOST memory, offsets in the

@@ -400,7 +400,7 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     a.n_tiles = ts.n_tiles;
     a.nrhs = nrhs;
     a.zero_row = zero_row;
-    for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i] * plan->core_inv_scale;
+    for (int i = 0; i < 32; ++i) a.level_scale[i] = scales.s[i] * plan->out_inv_scale();
     a.D = pt;
     a.ldd = plan->rp;
     a.n_products = plan->products;
@@ -457,11 +457,11 @@ int core_chunk_default(kifmm_m2l_plan plan) {
     return rp;
 }
 
-// N per work item of the identity-row GEMMs: <= 192 (96 running sums per
-// thread in the drained epilogue), split further while the tiles would not
-// fill two waves of CTAs.
-int rows_chunk(int ndim, long n_tiles, int num_sms) {
-    int c = (ndim + 191) / 192;
+// N per work item of the identity-row GEMMs: <= max_n (at most 192: 96
+// running sums per thread in the drained epilogue), split further while the
+// tiles would not fill two waves of CTAs.
+int rows_chunk(int ndim, long n_tiles, int num_sms, int max_n) {
+    int c = (ndim + max_n - 1) / max_n;
     while (n_tiles * c < 2L * num_sms && ndim / (c + 1) >= 64) ++c;
     return ((ndim + c - 1) / c + 15) / 16 * 16;
 }
@@ -483,7 +483,7 @@ int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* 
     a.B = plan->Rtb.ptr;
     a.b_groups = 1;
     a.ndim = rp;
-    a.n_chunk = rows_chunk(rp, n_tiles, plan->num_sms);
+    a.n_chunk = rows_chunk(rp, n_tiles, plan->num_sms, 128);
     a.row_identity = 1;
     a.n_tiles = n_tiles;
     a.m_rows = m_rows;
@@ -499,7 +499,10 @@ int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* 
     a.Z = pt;
     a.n_products = 6;
     a.hilo = 1;
-    a.core_drain = 1;  // one K-chunk per drained partial: the long K of these GEMMs
+    // three K-chunks per drained partial, the (0,0) product in its own half of
+    // the slot (N <= 128 so that two slots of 2 N columns fit): 6
+    // full-magnitude MMAs per accumulator chain
+    a.core_drain = 3;
     a.error_flag = plan->err_flag.ptr;
     KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_SPLIT, a, plan->num_sms, s));
     return KIFMM_OK;
@@ -518,7 +521,7 @@ int run_expand(kifmm_m2l_plan plan, const float* pt, int m_rows, const RowSeg* s
     a.B = plan->Ub.ptr;
     a.b_groups = 1;
     a.ndim = np;
-    a.n_chunk = rows_chunk(np, n_tiles, plan->num_sms);
+    a.n_chunk = rows_chunk(np, n_tiles, plan->num_sms, 192);
     a.row_identity = 1;
     a.n_tiles = n_tiles;
     a.m_rows = m_rows;
@@ -532,7 +535,10 @@ int run_expand(kifmm_m2l_plan plan, const float* pt, int m_rows, const RowSeg* s
     a.n_valid = n;
     a.n_products = 6;
     a.hilo = 1;
-    a.core_drain = 1;  // one K-chunk per drained partial: the long K of these GEMMs
+    // three K-chunks per drained partial with the (0,0) product apart where
+    // two slots of 2 N columns fit (N <= 128); wider N parts (n_pad / 2 at
+    // p = 8) fall back to one K-chunk per partial in the launcher
+    a.core_drain = 3;
     a.error_flag = plan->err_flag.ptr;
     KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_STORE, a, plan->num_sms, s));
     return KIFMM_OK;
@@ -859,14 +865,17 @@ int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2) {
         set_error("plan is NULL");
         return KIFMM_ERR_INVALID_ARG;
     }
+    // cached batches hold scale tables made for the previous operator
+    forget_batches_of(plan);
     if (!(c2 > 0)) {
         plan->s2_on = 0;
         plan->s2_c2 = 0;
         plan->s2_k.clear();
+        plan->s2_inv_scale = 1.0f;
         return KIFMM_OK;
     }
-    if (plan->prm.precision == KIFMM_PREC_FP32 || plan->prm.precision == KIFMM_PREC_F16X3) {
-        set_error("stage 2 runs on the BF16 tensor-core precisions only (FP32 plans use the SIMT core)");
+    if (plan->prm.precision == KIFMM_PREC_FP32) {
+        set_error("stage 2 runs on the tensor-core precisions only (FP32 plans use the SIMT core)");
         return KIFMM_ERR_UNSUPPORTED;
     }
     if (plan->rp > 512 - 2 * 96) {
@@ -892,12 +901,31 @@ int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2) {
         const int r = plan->r, rp = plan->rp;
         std::vector<int> k16(kOffsets);
         for (int o = 0; o < kOffsets; ++o) k16[o] = std::max(16, (s2.k[o] + 15) / 16 * 16);
-        // Vhat_o rows, [3][316][96][rp]; Uhat_o rows, [3][316][rp][96]; zero padding
-        auto split_upload = [&](kifmm::DevBuf<__nv_bfloat16>& dst, size_t per, auto value_at) -> int {
+        // Vhat_o rows, [3][316][96][rp]; Uhat_o rows, [3][316][rp][96]; zero
+        // padding.  BF16 modes: three BF16 pieces.  F16X3: two FP16 pieces of
+        // tau x (tau the power of two that puts the factor's largest entry in
+        // [2^13, 2^14)), the third piece zero; the core divides by both taus.
+        const bool f16 = plan->prm.precision == KIFMM_PREC_F16X3;
+        auto split_upload = [&](kifmm::DevBuf<__nv_bfloat16>& dst, size_t per, auto value_at, double* inv) -> int {
+            double tau = 1.0;
+            if (f16) {
+                double vmax = 0;
+                for (size_t e = 0; e < per; ++e) vmax = std::max(vmax, std::fabs(value_at(e)));
+                int e2 = 0;
+                std::frexp(vmax > 0 ? vmax : 1.0, &e2);  // vmax in [2^(e2-1), 2^e2)
+                tau = std::ldexp(1.0, 14 - e2);
+            }
+            *inv = 1.0 / tau;
             std::vector<uint16_t> h(per * 3, 0);
             for (size_t e = 0; e < per; ++e) {
                 double v = value_at(e);
                 if (v == 0.0) continue;
+                if (f16) {
+                    v *= tau;
+                    h[e] = f16_bits_rn(v);
+                    h[per + e] = f16_bits_rn(v - f16_bits_to_double(h[e]));
+                    continue;
+                }
                 for (int pc = 0; pc < 3; ++pc) {
                     const uint16_t b = bf16_bits_rn((float)v);
                     h[pc * per + e] = b;
@@ -908,16 +936,18 @@ int kifmm_m2l_set_stage2(kifmm_m2l_plan plan, double c2) {
             KIFMM_CUDA_TRY(cudaMemcpy(dst.ptr, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
             return KIFMM_OK;
         };
+        double inv_v = 1.0, inv_u = 1.0;
         st = split_upload(plan->s2V, (size_t)kOffsets * 96 * rp, [&](size_t e) -> double {
             const size_t o = e / ((size_t)96 * rp), j = (e / rp) % 96, b = e % rp;
             return (j < (size_t)s2.k[o] && b < (size_t)r) ? s2.Vh[o][j * r + b] : 0.0;
-        });
+        }, &inv_v);
         if (st != KIFMM_OK) return st;
         st = split_upload(plan->s2U, (size_t)kOffsets * rp * 96, [&](size_t e) -> double {
             const size_t o = e / ((size_t)rp * 96), a = (e / 96) % rp, j = e % 96;
             return (a < (size_t)r && j < (size_t)s2.k[o]) ? s2.Uh[o][a * s2.k[o] + j] : 0.0;
-        });
+        }, &inv_u);
         if (st != KIFMM_OK) return st;
+        plan->s2_inv_scale = (float)(inv_v * inv_u);
         KIFMM_CUDA_TRY(plan->s2_k16.upload(k16.data(), k16.size()));
         plan->s2_k = s2.k;
         plan->s2_c2 = c2;

@@ -100,7 +100,7 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
         if (st != KIFMM_OK) return st;
         ItemPairs p{ms, x.nrhs, rows, (int)scales.size()};
         for (int l = x.level_lo; l <= x.level_hi; ++l)
-            scales.push_back((float)(std::ldexp(1.0 / find_level(plan, x.instance, l)->r0, l) * plan->core_inv_scale));
+            scales.push_back((float)(std::ldexp(1.0 / find_level(plan, x.instance, l)->r0, l) * plan->out_inv_scale()));
         const long item_rows = ms->total_boxes * x.nrhs;
         g.row_base.push_back(rows);
         RowSeg si{x.q_up, nullptr, (int)item_rows, tiles_so_far, (int)rows, 1.0f, 0.0f};

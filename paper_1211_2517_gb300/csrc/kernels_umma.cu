@@ -81,6 +81,7 @@ struct Layout {
     int stages, na, nc, c_rows_alloc, n_acc, acc_cols, n_items, n_chunks, kc_count;
     int prod_warps;  // A_GATHER: producer warps in use; divides `stages`
     int drain;       // A_GATHER: K-chunks per partial drained by 8 epilogue warps (0: no drain; see the epilogue)
+    int dhilo;       // drained partials keep the (0,0) product in its own half of the slot (2 N columns per slot)
     uint32_t a_bytes, c_bytes, stage_bytes, trans_off;
 };
 
@@ -356,7 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // drain (core): every product into one per-K-chunk partial
                 const bool drain = AMODE == A_GATHER && L.drain;
                 const int group_max = drain && args.mma_pair > 1 ? (args.mma_pair < S - 1 ? args.mma_pair : S - 1) : 1;
-                const bool split_lo = AMODE == A_ROWS || (args.hilo && !drain);
+                const bool split_lo = AMODE == A_ROWS || (args.hilo && !drain) || (drain && L.dhilo);
+                const uint32_t slot_cols = (uint32_t)((L.dhilo ? 2 : 1) * args.n_chunk);
                 int s = 0, tcount = 0, pcount = 0;
                 uint32_t ph = 0;
                 bool ok = true;
@@ -392,9 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 ok = false;
                                 break;
                             }
-                            d_hi = tmem + (uint32_t)(ps * args.n_chunk);
-                            if (drain) d_lo = d_hi;
+                            d_hi = tmem + (uint32_t)ps * slot_cols;
+                            if (drain) d_lo = L.dhilo ? d_hi + (uint32_t)args.n_chunk : d_hi;
                             hi_on = false;
+                            if (drain && L.dhilo) lo_on = false;  // rows modes: lo spans the item
                         }
                         // with mma_pair > 1 the next chunks of the same partial (up to
                         // mma_pair in all, leaving a ring slot to the producers) are
@@ -565,22 +568,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t pcol = (uint32_t)(ps * args.n_chunk);
+                const uint32_t pcol = (uint32_t)(ps * (L.dhilo ? 2 : 1) * args.n_chunk);
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
                     const int c = (c_beg + jj) * 32;
                     if (c_beg + jj < c_end) {
-                        uint32_t r[32];
-                        if (c + 32 <= nthis) {
-                            tmem_ld32(tmem + lane_base + pcol + (uint32_t)c, r);
-                        } else {
-                            tmem_ld16(tmem + lane_base + pcol + (uint32_t)c, r);
+                        // the slot's (0,0) half, then (dhilo) its small products' half
+                        for (int hl = 0; hl < (L.dhilo ? 2 : 1); ++hl) {
+                            const uint32_t col = pcol + (uint32_t)(hl * args.n_chunk + c);
+                            uint32_t r[32];
+                            if (c + 32 <= nthis) {
+                                tmem_ld32(tmem + lane_base + col, r);
+                            } else {
+                                tmem_ld16(tmem + lane_base + col, r);
 #pragma unroll
-                            for (int j = 16; j < 32; ++j) r[j] = 0u;
+                                for (int j = 16; j < 32; ++j) r[j] = 0u;
+                            }
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) sums[jj * 32 + j] += __uint_as_float(r[j]);
                         }
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) sums[jj * 32 + j] += __uint_as_float(r[j]);
                     }
                 }
                 tc_fence_before();
@@ -1242,12 +1249,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 //   warp 11     TMEM allocation and the MMA-issuing thread
 // TMEM columns: T hi [0, 96), T lo [96, 192), P [192, 192 + r_pad).
 // The next tile's first GEMM runs while the epilogue reduces P.
-constexpr int kS2Stages = 3, kS2Kmax = 96, kS2Part = 96;
+constexpr int kS2Prod = 3, kS2MaxStages = 6, kS2Kmax = 96, kS2Part = 96;
 constexpr int kOffsetsHost = KIFMM_N_OFFSETS;
 
 struct S2Smem {
-    uint64_t full[kS2Stages], empty[kS2Stages];
+    uint64_t full[kS2MaxStages], empty[kS2MaxStages];
     uint64_t t_full, t_empty, tsplit, tbuf_free, p_full, p_empty, drain;
+    uint64_t tinv_full[2], tinv_empty[2];  // the T rows' powers of two, T warps -> P warps (f16x3)
     uint32_t tmem_base;
     volatile int abort_flag;
     unsigned long long wait_ns;  // bound of every mbarrier wait of this launch
@@ -1257,9 +1265,11 @@ struct S2Layout {
     int kc1;                 // K chunks of the first GEMM (r_pad / 32, rounded up)
     int nh;                  // 96-row parts of N in the second GEMM
     int n_items;             // tiles
-    uint32_t stage_bytes;    // A pieces (3 x 8 KB) + B pieces (3 x 96 rows x 64 B)
+    int stages;              // ring stages (at least the 3 producer warps, at most kS2MaxStages)
+    uint32_t stage_bytes;    // A pieces (pieces x 8 KB) + B pieces (pieces x 96 rows x 64 B)
     uint32_t tbuf_off;       // T pieces [3 chunks][pieces][128 x 64 B], from the stage ring base
-    uint32_t trans_off;      // epilogue transpose buffers, from the stage ring base
+    uint32_t trans_off;      // epilogue transpose buffers (one per P-draining warp), from the stage ring base
+    uint32_t tmax_off;       // the T rows' inverse powers of two, 2 slots of 128 floats
 };
 
 template <int NP>
@@ -1275,10 +1285,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int PC = NP == 6 ? 3 : (NP == 3 ? 2 : 1);  // BF16 pieces
     constexpr int P0 = 6 - NP;
     constexpr bool HILO = NP > 1;
+    // epilogue warps: 8 (warps 0-3 split T, the idle producer warps 7-10
+    // drain P) for 1 or 2 pieces; split6 keeps one set of 4 doing both
+    constexpr int EW = NP == 6 ? 4 : 8;
     constexpr uint32_t kAPiece = kTileM * CH * 2;            // 8 KB
     constexpr uint32_t kBPiece = kS2Kmax * RB;               // 6 KB
-    constexpr uint32_t kBOff = 3 * kAPiece;                  // B pieces follow 3 A pieces
-    const int S = kS2Stages, KC1 = L.kc1, NH = L.nh;
+    constexpr uint32_t kBOff = PC * kAPiece;                 // B pieces follow the A pieces
+    const int S = L.stages, KC1 = L.kc1, NH = L.nh;
     const bool contig = args.contiguous != 0;
     const int i_beg = contig ? (int)((long)L.n_items * blockIdx.x / gridDim.x) : (int)blockIdx.x;
     const int i_end = contig ? (int)((long)L.n_items * (blockIdx.x + 1) / gridDim.x) : L.n_items;
@@ -1295,6 +1308,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&sm->tbuf_free, 1);
         mbar_init(&sm->p_full, 1);
         mbar_init(&sm->p_empty, kEpiWarps * 32);
+        for (int sl = 0; sl < 2; ++sl) {
+            mbar_init(&sm->tinv_full[sl], kEpiWarps * 32);
+            mbar_init(&sm->tinv_empty[sl], kEpiWarps * 32);
+        }
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
         sm->wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
@@ -1311,10 +1328,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = sm->tmem_base;
     auto stage_base = [&](int b) -> uint8_t* { return ring + (size_t)b * L.stage_bytes; };
-    auto tbuf = [&](int c2, int pc) -> uint8_t* { return ring + L.tbuf_off + (size_t)(c2 * 3 + pc) * kAPiece; };
+    auto tbuf = [&](int c2, int pc) -> uint8_t* { return ring + L.tbuf_off + (size_t)(c2 * PC + pc) * kAPiece; };
     auto k16_of = [&](int item) -> int { return __ldg(args.s2_k16 + (__ldg(args.tile_k + item) & 0xFFFF)); };
 
-    if (warp >= kEpiWarps && warp < kEpiWarps + kS2Stages) {
+    if (warp >= kEpiWarps && warp < kEpiWarps + kS2Prod) {
         // ================= producers =================
         const int pw = warp - kEpiWarps;
         constexpr int CPR = CH / 8, RPI = 32 / CPR, NR = kTileM / RPI;
@@ -1332,7 +1349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 srow[i] = r < 0 ? args.zero_row : r;
             }
             for (int j = 0; j < nst; ++j, ++it) {
-                if (it % S != pw) continue;
+                if (it % kS2Prod != pw) continue;
                 const int b = it % S;
                 const uint32_t ph = (uint32_t)(it / S) & 1u;
                 if (!mbar_wait(&sm->empty[b], ph ^ 1u, sm, args.error_flag)) {
@@ -1368,10 +1385,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         (pc * KIFMM_N_OFFSETS + group) * args.ndim + h * kS2Part, &sm->full[b]);
                     }
                 }
-                cp_async_commit();
-                cp_async_wait_0();
-                fence_proxy_async();
-                mbar_arrive(&sm->full[b]);
+                // the lanes arrive as their copies land (the MMA thread fences
+                // them into the async proxy), so a warp keeps several stages
+                // in flight
+                if (j < KC1) cp_async_mbar_arrive(&sm->full[b]);
+                else mbar_arrive(&sm->full[b]);
             }
         }
         cp_async_wait_0();
@@ -1399,7 +1417,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t idT = umma_idesc_bf16(k16);
+                const uint32_t idT = umma_idesc(k16, args.f16);
                 const uint32_t d_hi = tmem, d_lo = HILO ? tmem + (uint32_t)kS2Kmax : tmem;
                 bool hi_on = false, lo_on = false;
                 for (int kc = 0; kc < KC1; ++kc) {
@@ -1407,6 +1425,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
+                    fence_proxy_async();  // cp.async data -> tensor-core reads
                     tc_fence_after();
                     const uint64_t sd = ring_desc + (uint64_t)((uint32_t)b * stage_u);
                     if (args.kdim - kc * CH >= 32) {
@@ -1456,10 +1475,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         tc_fence_after();
                         const int nh_cols = min(kS2Part, args.ndim - h * kS2Part);
-                        const uint32_t idP = umma_idesc_bf16(nh_cols);
+                        const uint32_t idP = umma_idesc(nh_cols, args.f16);
                         const uint32_t dP = tmem + (uint32_t)(2 * kS2Kmax + h * kS2Part);
                         const uint64_t sd = ring_desc + (uint64_t)((uint32_t)b * stage_u);
-                        const uint64_t td = tdesc + (uint64_t)((uint32_t)(c2 * 3) * a_u);
+                        const uint64_t td = tdesc + (uint64_t)((uint32_t)(c2 * PC) * a_u);
 #pragma unroll
                         for (int pi = P0; pi < 6; ++pi) {
                             const uint64_t ad = td + (uint64_t)(kA[pi] * a_u), bd = sd + (uint64_t)(bo_u + kB[pi] * bp_u);
@@ -1484,103 +1503,172 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
-    } else if (warp < kEpiWarps) {
+    } else if (warp < kEpiWarps || (EW == 8 && warp >= kEpiWarps + kS2Prod && warp < kEpiWarps + kProdWarps)) {
         // ================= epilogue =================
-        float* trans = reinterpret_cast<float*>(ring + L.trans_off) + warp * 32 * kTransStride;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        const int m = warp * 32 + lane;  // tile row = TMEM lane
+        // Warp w < 4 and (EW = 8) warp 7-10 read TMEM lane quarter w mod 4,
+        // one whole tile row per lane.  With EW = 4 each warp splits T and
+        // then drains P, tile after tile.  With EW = 8 the roles run side by
+        // side: warps 0-3 split T (and hand each row's power of two to the P
+        // warps through a 2-slot ring of shared-memory rows), warps 7-10
+        // drain P, so the split of tile i + 1 overlaps the drain of tile i.
+        const int q = warp & 3;
+        const bool t_role = EW == 4 || warp < kEpiWarps;
+        const bool p_role = EW == 4 || warp >= kEpiWarps;
+        float* trans = reinterpret_cast<float*>(ring + L.trans_off) + q * 32 * kTransStride;
+        float* tinv_rows = reinterpret_cast<float*>(ring + L.tmax_off);  // [2 slots][128 rows]
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int m = q * 32 + lane;  // tile row = TMEM lane
+        const bool f16t = NP == 3 && args.f16 != 0;
         int ic = 0;
         bool ok = true;
         for (int item = i_beg; item < i_end && ok; item += i_step, ++ic) {
-            const long orow = __ldg(args.row_dst + (long)item * kTileM + m);
             const int code = __ldg(args.tile_k + item);
-            const float oscale = args.scale_table ? __ldg(args.scale_table + (code >> 16)) : args.level_scale[(code >> 16) & 31];
             const int k16 = __ldg(args.s2_k16 + (code & 0xFFFF));
-            // T: TMEM -> hi + lo -> BF16 pieces in shared memory
-            bool got = mbar_wait(&sm->tbuf_free, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag);
-            got = got && mbar_wait(&sm->t_full, (uint32_t)(ic & 1), sm, args.error_flag);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            for (int c = 0; c < k16; c += 32) {
-                uint32_t r[32], r2[32];
-                const bool full32 = c + 32 <= k16;
-                if (full32) tmem_ld32(tmem + lane_base + (uint32_t)c, r);
-                else tmem_ld16(tmem + lane_base + (uint32_t)c, r);
-                if (HILO) {
-                    if (full32) tmem_ld32(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
-                    else tmem_ld16(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+            float tinv = 1.f;
+            if (t_role) {
+                // T: TMEM -> hi + lo -> pieces in shared memory
+                bool got = mbar_wait(&sm->tbuf_free, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag);
+                got = got && mbar_wait(&sm->t_full, (uint32_t)(ic & 1), sm, args.error_flag);
+                if (EW == 8 && f16t)
+                    got = got && mbar_wait(&sm->tinv_empty[ic & 1], (uint32_t)((ic >> 1) & 1) ^ 1u, sm,
+                                           args.error_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
                 }
-                tmem_wait_ld();
+                tc_fence_after();
+                // FP16 pieces (f16x3): this row of T scaled by the power of two
+                // tsc that puts its largest entry in [2^14, 2^15), undone by
+                // tinv on the row of P
+                float tsc = 1.f;
+                if (f16t) {
+                    float mx = 0.f;
+                    for (int c = 0; c < k16; c += 16) {
+                        uint32_t r[32], r2[32];
+                        tmem_ld16(tmem + lane_base + (uint32_t)c, r);
+                        tmem_ld16(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+                        tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (!full32 && q >= 2) break;
-                    uint32_t pk[3][4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        float x = __uint_as_float(r[8 * q + 2 * e]), y = __uint_as_float(r[8 * q + 2 * e + 1]);
-                        if (HILO) {
-                            x += __uint_as_float(r2[8 * q + 2 * e]);
-                            y += __uint_as_float(r2[8 * q + 2 * e + 1]);
-                        }
-                        uint32_t hh[3];
-                        split3x2(x, y, hh, PC);
-#pragma unroll
-                        for (int pc = 0; pc < 3; ++pc) pk[pc][e] = hh[pc];
+                        for (int j = 0; j < 16; ++j)
+                            mx = fmaxf(mx, fabsf(__uint_as_float(r[j]) + __uint_as_float(r2[j])));
                     }
+                    int e = mx > 0.f ? ((__float_as_int(mx) >> 23) & 0xFF) - 127 : 0;
+                    e = max(-112, min(127, e));  // tsc and tinv both normal powers of two
+                    tsc = __int_as_float((127 + 14 - e) << 23);
+                    tinv = __int_as_float((127 + e - 14) << 23);
+                }
+                for (int c = 0; c < k16; c += 32) {
+                    uint32_t r[32], r2[32];
+                    const bool full32 = c + 32 <= k16;
+                    if (full32) tmem_ld32(tmem + lane_base + (uint32_t)c, r);
+                    else tmem_ld16(tmem + lane_base + (uint32_t)c, r);
+                    if (HILO) {
+                        if (full32) tmem_ld32(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+                        else tmem_ld16(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+                    }
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int pc = 0; pc < PC; ++pc)
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(tbuf(c / 32, pc)) +
-                                                                                        swz<CH>(m, q)),
-                                     "r"(pk[pc][0]), "r"(pk[pc][1]), "r"(pk[pc][2]), "r"(pk[pc][3])
-                                     : "memory");
+                    for (int qq = 0; qq < 4; ++qq) {
+                        if (!full32 && qq >= 2) break;
+                        uint32_t pk[3][4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float x = __uint_as_float(r[8 * qq + 2 * e]), y = __uint_as_float(r[8 * qq + 2 * e + 1]);
+                            if (HILO) {
+                                x += __uint_as_float(r2[8 * qq + 2 * e]);
+                                y += __uint_as_float(r2[8 * qq + 2 * e + 1]);
+                            }
+                            uint32_t hh[3];
+                            if (f16t) {
+                                const float xs = x * tsc, ys = y * tsc;
+                                const __half2 h = __floats2half2_rn(xs, ys);
+                                const __half2 l = __floats2half2_rn(xs - __low2float(h), ys - __high2float(h));
+                                hh[0] = *reinterpret_cast<const uint32_t*>(&h);
+                                hh[1] = *reinterpret_cast<const uint32_t*>(&l);
+                                hh[2] = 0u;
+                            } else {
+                                split3x2(x, y, hh, PC);
+                            }
+#pragma unroll
+                            for (int pc = 0; pc < 3; ++pc) pk[pc][e] = hh[pc];
+                        }
+#pragma unroll
+                        for (int pc = 0; pc < PC; ++pc)
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(tbuf(c / 32, pc)) +
+                                                                                            swz<CH>(m, qq)),
+                                         "r"(pk[pc][0]), "r"(pk[pc][1]), "r"(pk[pc][2]), "r"(pk[pc][3])
+                                         : "memory");
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&sm->t_empty);
+                fence_proxy_async();
+                mbar_arrive(&sm->tsplit);
+                if (EW == 8 && f16t) {
+                    tinv_rows[(ic & 1) * kTileM + m] = tinv;
+                    mbar_arrive(&sm->tinv_full[ic & 1]);
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&sm->t_empty);
-            fence_proxy_async();
-            mbar_arrive(&sm->tsplit);
-            // P: TMEM -> transpose -> reductions into p~
-            got = mbar_wait(&sm->p_full, (uint32_t)(ic & 1), sm, args.error_flag);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            long prow[8];
-#pragma unroll
-            for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
-            const int c4 = lane % 8;
-            for (int c = 0; c < args.ndim; c += 32) {
-                uint32_t r[32];
-                const bool full32 = c + 32 <= args.ndim;
-                const uint32_t a0 = tmem + lane_base + (uint32_t)(2 * kS2Kmax + c);
-                if (full32) tmem_ld32(a0, r);
-                else tmem_ld16(a0, r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * q) =
-                        make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                    __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-                __syncwarp();
-                const int ncols = full32 ? 32 : 16;
-#pragma unroll
-                for (int pass = 0; pass < 8; ++pass) {
-                    const int rr = pass * 4 + lane / 8;
-                    const long grow = prow[pass];
-                    if (grow < 0 || 4 * c4 >= ncols) continue;
-                    const float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
-                    red_add_v4(args.D + grow * args.ldd + c + 4 * c4, __float_as_uint(oscale * x.x),
-                               __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
-                               __float_as_uint(oscale * x.w));
+            if (p_role) {
+                // P: TMEM -> transpose -> reductions into p~
+                const long orow = __ldg(args.row_dst + (long)item * kTileM + m);
+                const float oscale =
+                    args.scale_table ? __ldg(args.scale_table + (code >> 16)) : args.level_scale[(code >> 16) & 31];
+                // this row's factor besides s_l: the FP16 scaling of its q~ row
+                // (row_scale) and of its T row (tinv)
+                float qf = 1.f;
+                if (args.row_scale) {
+                    const int sr = __ldg(args.row_src + (long)item * kTileM + m);
+                    qf = sr >= 0 ? __ldg(args.row_scale + sr) : 0.f;
                 }
-                __syncwarp();
+                bool got = true;
+                if (EW == 8 && f16t) {
+                    got = mbar_wait(&sm->tinv_full[ic & 1], (uint32_t)(ic >> 1) & 1u, sm, args.error_flag);
+                    if (got) {
+                        tinv = tinv_rows[(ic & 1) * kTileM + m];
+                        mbar_arrive(&sm->tinv_empty[ic & 1]);
+                    }
+                }
+                got = got && mbar_wait(&sm->p_full, (uint32_t)(ic & 1), sm, args.error_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const float rowf = qf * tinv;
+                long prow[8];
+#pragma unroll
+                for (int pass = 0; pass < 8; ++pass) prow[pass] = __shfl_sync(0xffffffffu, orow, pass * 4 + lane / 8);
+                const int c4 = lane % 8;
+                for (int c = 0; c < args.ndim; c += 32) {
+                    uint32_t r[32];
+                    const bool full32 = c + 32 <= args.ndim;
+                    const uint32_t a0 = tmem + lane_base + (uint32_t)(2 * kS2Kmax + c);
+                    if (full32) tmem_ld32(a0, r);
+                    else tmem_ld16(a0, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int qv = 0; qv < 8; ++qv)
+                        *reinterpret_cast<float4*>(trans + lane * kTransStride + 4 * qv) =
+                            make_float4(rowf * __uint_as_float(r[4 * qv]), rowf * __uint_as_float(r[4 * qv + 1]),
+                                        rowf * __uint_as_float(r[4 * qv + 2]), rowf * __uint_as_float(r[4 * qv + 3]));
+                    __syncwarp();
+                    const int ncols = full32 ? 32 : 16;
+#pragma unroll
+                    for (int pass = 0; pass < 8; ++pass) {
+                        const int rr = pass * 4 + lane / 8;
+                        const long grow = prow[pass];
+                        if (grow < 0 || 4 * c4 >= ncols) continue;
+                        const float4 x = *reinterpret_cast<const float4*>(trans + rr * kTransStride + 4 * c4);
+                        red_add_v4(args.D + grow * args.ldd + c + 4 * c4, __float_as_uint(oscale * x.x),
+                                   __float_as_uint(oscale * x.y), __float_as_uint(oscale * x.z),
+                                   __float_as_uint(oscale * x.w));
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                mbar_arrive(&sm->p_empty);
             }
-            tc_fence_before();
-            mbar_arrive(&sm->p_empty);
         }
     }
 
@@ -1756,11 +1844,17 @@ cudaError_t launch_core_stage2(const UmmaArgs& a, int num_sms, cudaStream_t stre
     L.kc1 = (a.kdim + 31) / 32;
     L.nh = (a.ndim + kS2Part - 1) / kS2Part;
     L.n_items = a.n_tiles;
-    L.stage_bytes = 3u * kTileM * 32u * 2u + 3u * kS2Kmax * 64u;
-    L.tbuf_off = kS2Stages * L.stage_bytes;
-    L.trans_off = L.tbuf_off + 9u * kTileM * 32u * 2u;
-    const uint32_t trans_bytes = kEpiWarps * 32 * kTransStride * 4;
-    const size_t smem = 2048 + (size_t)L.trans_off + trans_bytes;
+    const uint32_t pc = a.n_products == 6 ? 3u : (a.n_products == 3 ? 2u : 1u);  // pieces
+    L.stage_bytes = pc * (kTileM * 32u * 2u + kS2Kmax * 64u);
+    // the fixed part: T pieces, transpose buffers, T row maxima; the ring
+    // takes the rest (3 to kS2MaxStages stages)
+    const uint32_t fixed = 3u * pc * kTileM * 32u * 2u + kEpiWarps * 32 * kTransStride * 4 + 2u * kTileM * 4u;
+    L.stages = (int)std::min<long>(kS2MaxStages, ((long)max_smem - 2048 - (long)fixed) / (long)L.stage_bytes);
+    if (L.stages < kS2Prod) return cudaErrorInvalidConfiguration;
+    L.tbuf_off = (uint32_t)L.stages * L.stage_bytes;
+    L.trans_off = L.tbuf_off + 3u * pc * kTileM * 32u * 2u;
+    L.tmax_off = L.trans_off + kEpiWarps * 32 * kTransStride * 4;
+    const size_t smem = 2048 + (size_t)L.tmax_off + 2u * kTileM * 4u;
     if ((long)smem > (long)max_smem) return cudaErrorInvalidConfiguration;
     if (L.n_items <= 0) return cudaSuccess;
     CUtensorMap vmap, umap;
@@ -1778,7 +1872,11 @@ cudaError_t launch_core_stage2(const UmmaArgs& a, int num_sms, cudaStream_t stre
                 g_smem_granted[slot][dev] = (int)smem;
             }
         }
-        kern<<<grid, kThreads, smem, stream>>>(vmap, umap, a, L);
+        // round-robin tiles: the per-offset ranks k_o make tile costs uneven
+        // along the offset-major list, so contiguous runs would not balance
+        UmmaArgs b = a;
+        b.contiguous = 0;
+        kern<<<grid, kThreads, smem, stream>>>(vmap, umap, b, L);
         return cudaGetLastError();
     };
     if (a.n_products == 6) return go(core_stage2_kernel<6>, 4);
@@ -1806,8 +1904,10 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (a.ldd % 4 != 0) return cudaErrorInvalidValue;
     EncodeTiledFn encode = get_encode_fn();
     if (!encode) return cudaErrorNotSupported;
-    // FP16 operands and per-row factors: the gather kernel's classic and drain paths only
-    if ((a.f16 || a.row_scale) && (!gather || a.s2_on || (a.row_scale && emode != E_RED))) return cudaErrorNotSupported;
+    // FP16 operands and per-row factors: the gather kernel's classic and drain
+    // paths and the 3-product stage-2 core only
+    if ((a.f16 || a.row_scale) && (!gather || (a.s2_on && a.n_products != 3) || (a.row_scale && emode != E_RED)))
+        return cudaErrorNotSupported;
     if (gather && a.s2_on) return launch_core_stage2(a, num_sms, stream, encode);
     if (gather && a.core_resident && !a.f16 && !a.row_scale) {
         const cudaError_t e = launch_core_resident(a, num_sms, stream, encode);
@@ -1862,6 +1962,15 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     L.drain = gather && a.core_drain > 0 && (a.n_products == 6 || a.n_products == 3) && a.n_chunk <= 192
                   ? std::min(a.core_drain, 3)
                   : 0;
+    // compression / expansion with hilo: the (0,0) product gets its own half
+    // of each partial slot (two slots of 2 N columns in the 512), so a partial
+    // may span several K-chunks with only 2 full-magnitude MMAs per chunk;
+    // where the slots do not fit, one K-chunk per partial
+    L.dhilo = 0;
+    if (L.drain && gather && emode != E_RED && a.hilo && a.n_products > 1) {
+        if (4 * a.n_chunk <= 512) L.dhilo = 1;
+        else L.drain = 1;
+    }
     // the drained core that reduces rows straight from registers (direct_rows)
     // needs no transpose buffers: their room goes to the ring
     const bool no_trans = L.drain && gather && emode == E_RED && a.direct_rows;

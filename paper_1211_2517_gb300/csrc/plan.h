@@ -164,8 +164,12 @@ struct kifmm_m2l_plan_s {
     int s2_on = 0;
     double s2_c2 = 0;
     std::vector<int> s2_k;                     // [316] ranks k_o
-    kifmm::DevBuf<__nv_bfloat16> s2V, s2U;     // 3 BF16 pieces each
+    kifmm::DevBuf<__nv_bfloat16> s2V, s2U;     // 3 BF16 pieces each (F16X3: 2 FP16 pieces of tau_V Vhat, tau_U Uhat, third zero)
     kifmm::DevBuf<int> s2_k16;                 // [316] k_o rounded up to 16
+    float s2_inv_scale = 1.0f;                 // 1 / (tau_V tau_U) (F16X3), else 1
+    // the factor the core's output rows take besides s_l: undoes the powers
+    // of two of the FP16 operands (single stage: the cores'; stage 2: both factors')
+    float out_inv_scale() const { return s2_on ? s2_inv_scale : core_inv_scale; }
     kifmm::DevBuf<int> err_flag;
     unsigned long long core_wait_ns = 0;  // bound of the core kernels' waits (0: 2 s)
     std::map<std::pair<int, int>, std::unique_ptr<kifmm::LevelState>> levels;
@@ -239,7 +243,7 @@ int run_expand(kifmm_m2l_plan plan, const float* pt, int m_rows, const RowSeg* s
 // Elements the split buffer of run_compress / run_expand needs.
 size_t split_elems(kifmm_m2l_plan plan, long n_tiles);
 // N per work item of the identity-row GEMMs over n_tiles row tiles.
-int rows_chunk(int ndim, long n_tiles, int num_sms);
+int rows_chunk(int ndim, long n_tiles, int num_sms, int max_n);
 // Tile set of a multi-level state for nrhs (built on first use).
 int multi_tileset(MultiState& ms, int nrhs, TileSet** out);
 // The tensor-core core over a tile set: pt[dst] += scale K~_o qb[src], with

@@ -414,12 +414,21 @@ def test_f16x3_scaling_extremes(g, oracle_factors, sphere_small):
     assert err <= 1e-6
 
 
-def test_f16x3_unsupported_paths(g):
-    from paper_1211_2517_gb300 import KifmmError
+def test_f16x3_unsupported_paths(g, sphere_small):
+    """The allocation-free apply refuses f16x3 plans (its rows-mode kernels
+    have no per-row FP16 scaling); nothing is written."""
+    import ctypes
 
-    plan = g.M2LPlan(6, 1e-7, 0.1, "f16x3")
-    with pytest.raises(KifmmError, match="UNSUPPORTED"):
-        plan.set_stage2(10.0)
+    tree, qs = sphere_small
+    plan = make_plan(g, 8, 1e-7, "f16x3", tree, (3,))
+    x = torch.from_numpy(qs[3]).cuda()
+    out = torch.full_like(x, 7.0)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = g.lib().kifmm_m2l_apply_noalloc(plan._h, 0, 3, 3, ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), 0.0, stream)
+    torch.cuda.synchronize()
+    assert st == -2  # KIFMM_ERR_UNSUPPORTED
+    assert bool((out == 7.0).all())
     plan.close()
 
 
@@ -635,7 +644,7 @@ def test_core_variants_match_oracle(g, oracle_factors, sphere_small, monkeypatch
     plan.close()
 
 
-@pytest.mark.parametrize("precision", ["split6", "split3", "bf16"])
+@pytest.mark.parametrize("precision", ["split6", "split3", "bf16", "f16x3"])
 def test_stage2_parity(g, oracle_factors, sphere_small, precision):
     """Stage 2 (Sec. 3.2) with c2 = 1 on the p = 8 sphere: the library's
     per-offset ranks equal the oracle's, and apply_levels (forward and
