@@ -1338,17 +1338,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cch = lane % CPR, rl = lane / CPR;
         int it = 0;
         bool ok = true;
-        for (int item = i_beg; item < i_end && ok; item += i_step) {
+        // stages in the MMA thread's order: GEMM 1 of every tile, and (with
+        // EW = 8) GEMM 1 of tile s + 1 before GEMM 2 of tile s
+        auto produce = [&](int item, bool first_gemm) {
             const int group = __ldg(args.tile_k + item) & 0xFFFF;
             const int k16 = __ldg(args.s2_k16 + group);
-            const int nst = KC1 + ((k16 + 31) / 32) * NH;
+            const int nst = first_gemm ? KC1 : ((k16 + 31) / 32) * NH;
             int srow[NR];
+            if (first_gemm) {
 #pragma unroll
-            for (int i = 0; i < NR; ++i) {
-                const int r = __ldg(args.row_src + (long)item * kTileM + rl + RPI * i);
-                srow[i] = r < 0 ? args.zero_row : r;
+                for (int i = 0; i < NR; ++i) {
+                    const int r = __ldg(args.row_src + (long)item * kTileM + rl + RPI * i);
+                    srow[i] = r < 0 ? args.zero_row : r;
+                }
             }
-            for (int j = 0; j < nst; ++j, ++it) {
+            for (int j = 0; j < nst && ok; ++j, ++it) {
                 if (it % kS2Prod != pw) continue;
                 const int b = it % S;
                 const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -1357,7 +1361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 uint8_t* sb = stage_base(b);
-                if (j < KC1) {
+                if (first_gemm) {
                     const int col = j * CH + cch * 8;
                     const uint32_t bytes = col < args.kdim ? 16u : 0u;
                     const int colc = col < args.kdim ? col : 0;
@@ -1376,20 +1380,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 tma_load_2d(smem_u32(sb + kBOff + pc * kBPiece + rb * RB), &vmap, j * CH,
                                             (pc * KIFMM_N_OFFSETS + group) * kS2Kmax + rb, &sm->full[b]);
                     }
+                    // the lanes arrive as their copies land (the MMA thread
+                    // fences them into the async proxy), so a warp keeps
+                    // several stages in flight
+                    cp_async_mbar_arrive(&sm->full[b]);
                 } else {
-                    const int jj = j - KC1, c2 = jj / NH, h = jj % NH;
+                    const int c2 = j / NH, h = j % NH;
                     if (lane == 0) {
                         mbar_arrive_expect_tx(&sm->full[b], (uint32_t)(PC * kBPiece));
                         for (int pc = 0; pc < PC; ++pc)
                             tma_load_2d(smem_u32(sb + kBOff + pc * kBPiece), &umap, c2 * CH,
                                         (pc * KIFMM_N_OFFSETS + group) * args.ndim + h * kS2Part, &sm->full[b]);
                     }
+                    mbar_arrive(&sm->full[b]);
                 }
-                // the lanes arrive as their copies land (the MMA thread fences
-                // them into the async proxy), so a warp keeps several stages
-                // in flight
-                if (j < KC1) cp_async_mbar_arrive(&sm->full[b]);
-                else mbar_arrive(&sm->full[b]);
+            }
+        };
+        if (EW == 8) {
+            if (i_beg < i_end) produce(i_beg, true);
+            for (int item = i_beg; item < i_end && ok; item += i_step) {
+                if (item + i_step < i_end) produce(item + i_step, true);
+                if (ok) produce(item, false);
+            }
+        } else {
+            for (int item = i_beg; item < i_end && ok; item += i_step) {
+                produce(item, true);
+                if (ok) produce(item, false);
             }
         }
         cp_async_wait_0();
@@ -1404,18 +1420,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t ring_desc = umma_desc<CH>(smem_u32(ring));
             const uint32_t stage_u = L.stage_bytes >> 4, a_u = kAPiece >> 4, bo_u = kBOff >> 4, bp_u = kBPiece >> 4;
             const uint64_t tdesc = umma_desc<CH>(smem_u32(ring + L.tbuf_off));
-            int b = 0, ic = 0;
+            int b = 0;
             uint32_t ph = 0;
             bool ok = true;
             constexpr int8_t kA[6] = {2, 1, 0, 1, 0, 0}, kB[6] = {0, 1, 2, 0, 1, 0};
-            for (int item = i_beg; item < i_end && ok; item += i_step, ++ic) {
+            auto gemm1 = [&](int item, int ic) -> bool {
                 const int k16 = k16_of(item);
-                const int nc2 = (k16 + 31) / 32;
                 // first GEMM: T = Q~ Vhat^T
-                if (!mbar_wait(&sm->t_empty, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(&sm->t_empty, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag)) return false;
                 tc_fence_after();
                 const uint32_t idT = umma_idesc(k16, args.f16);
                 const uint32_t d_hi = tmem, d_lo = HILO ? tmem + (uint32_t)kS2Kmax : tmem;
@@ -1456,14 +1468,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ph ^= 1u;
                     }
                 }
-                if (!ok) break;
+                if (!ok) return false;
                 umma_commit(&sm->t_full);
+                return true;
+            };
+            auto gemm2 = [&](int item, int ic) -> bool {
+                const int k16 = k16_of(item);
+                const int nc2 = (k16 + 31) / 32;
                 // second GEMM: P = T Uhat^T, T pieces from shared memory
                 if (!mbar_wait(&sm->tsplit, (uint32_t)(ic & 1), sm, args.error_flag) ||
-                    !mbar_wait(&sm->p_empty, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag)) {
-                    ok = false;
-                    break;
-                }
+                    !mbar_wait(&sm->p_empty, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag))
+                    return false;
                 tc_fence_after();
                 uint32_t p_on = 0;  // bit h: part h of P has been written
                 for (int c2 = 0; c2 < nc2 && ok; ++c2) {
@@ -1493,9 +1508,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
-                if (!ok) break;
+                if (!ok) return false;
                 umma_commit(&sm->p_full);
                 umma_commit(&sm->tbuf_free);
+                return true;
+            };
+            // EW = 8: GEMM 1 of tile i + 1 runs while the T warps split tile i
+            // (they free the TMEM T columns as soon as they have read them)
+            int ic = 0;
+            if (EW == 8 && i_beg < i_end) ok = gemm1(i_beg, 0);
+            for (int item = i_beg; item < i_end && ok; item += i_step, ++ic) {
+                if (EW == 8) {
+                    if (item + i_step < i_end) ok = gemm1(item + i_step, ic + 1);
+                } else {
+                    ok = gemm1(item, ic);
+                }
+                if (ok) ok = gemm2(item, ic);
             }
             umma_commit(&sm->drain);
             const unsigned long long t0 = global_ns();
@@ -1525,7 +1553,95 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int code = __ldg(args.tile_k + item);
             const int k16 = __ldg(args.s2_k16 + (code & 0xFFFF));
             float tinv = 1.f;
-            if (t_role) {
+            if (EW == 8 && t_role) {
+                // T: TMEM -> registers (hi + lo), the TMEM columns released at
+                // once for the next tile's GEMM 1, then pieces in shared memory
+                // once GEMM 2 of the previous tile has read them
+                bool got = mbar_wait(&sm->t_full, (uint32_t)(ic & 1), sm, args.error_flag);
+                if (f16t)
+                    got = got && mbar_wait(&sm->tinv_empty[ic & 1], (uint32_t)((ic >> 1) & 1) ^ 1u, sm,
+                                           args.error_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                float tv[kS2Kmax];
+                float mx = 0.f;
+#pragma unroll
+                for (int c = 0; c < kS2Kmax; c += 16) {
+                    if (c < k16) {
+                        uint32_t r[16], r2[16];
+                        tmem_ld8(tmem + lane_base + (uint32_t)c, r);
+                        tmem_ld8(tmem + lane_base + (uint32_t)(c + 8), r + 8);
+                        if (HILO) {
+                            tmem_ld8(tmem + lane_base + (uint32_t)(kS2Kmax + c), r2);
+                            tmem_ld8(tmem + lane_base + (uint32_t)(kS2Kmax + c + 8), r2 + 8);
+                        }
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            tv[c + j] = __uint_as_float(r[j]) + (HILO ? __uint_as_float(r2[j]) : 0.f);
+                            mx = fmaxf(mx, fabsf(tv[c + j]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) tv[c + j] = 0.f;
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&sm->t_empty);
+                float tsc = 1.f;
+                if (f16t) {
+                    int e = mx > 0.f ? ((__float_as_int(mx) >> 23) & 0xFF) - 127 : 0;
+                    e = max(-112, min(127, e));  // tsc and tinv both normal powers of two
+                    tsc = __int_as_float((127 + 14 - e) << 23);
+                    tinv = __int_as_float((127 + e - 14) << 23);
+                }
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(&sm->tbuf_free, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag))) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll
+                for (int c = 0; c < kS2Kmax; c += 32) {
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        if (c + 8 * qq < k16) {
+                            uint32_t pk[3][4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float x = tv[c + 8 * qq + 2 * e], y = tv[c + 8 * qq + 2 * e + 1];
+                                uint32_t hh[3];
+                                if (f16t) {
+                                    const float xs = x * tsc, ys = y * tsc;
+                                    const __half2 h = __floats2half2_rn(xs, ys);
+                                    const __half2 l = __floats2half2_rn(xs - __low2float(h), ys - __high2float(h));
+                                    hh[0] = *reinterpret_cast<const uint32_t*>(&h);
+                                    hh[1] = *reinterpret_cast<const uint32_t*>(&l);
+                                    hh[2] = 0u;
+                                } else {
+                                    split3x2(x, y, hh, PC);
+                                }
+#pragma unroll
+                                for (int pc = 0; pc < 3; ++pc) pk[pc][e] = hh[pc];
+                            }
+#pragma unroll
+                            for (int pc = 0; pc < PC; ++pc)
+                                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                                 smem_u32(tbuf(c / 32, pc)) + swz<CH>(m, qq)),
+                                             "r"(pk[pc][0]), "r"(pk[pc][1]), "r"(pk[pc][2]), "r"(pk[pc][3])
+                                             : "memory");
+                        }
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(&sm->tsplit);
+                if (f16t) {
+                    tinv_rows[(ic & 1) * kTileM + m] = tinv;
+                    mbar_arrive(&sm->tinv_full[ic & 1]);
+                }
+            } else if (t_role) {
                 // T: TMEM -> hi + lo -> pieces in shared memory
                 bool got = mbar_wait(&sm->tbuf_free, (uint32_t)(ic & 1) ^ 1u, sm, args.error_flag);
                 got = got && mbar_wait(&sm->t_full, (uint32_t)(ic & 1), sm, args.error_flag);
