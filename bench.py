@@ -375,8 +375,9 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     plan.sync()
     value, max_ms, job_pairs = job_throughput(total_ms, total_pairs, args.steps, dev, world)
-    # split + compression (+ the scaled FP16 split for f16x3), core, split + expansion, over all levels
-    launches_per_step = 6 if args.precision == "f16x3" else 5
+    # split + compression (the f16x3 compression writes the core's FP16
+    # pieces itself), core, split + expansion, over all levels
+    launches_per_step = 5
 
     # ---- roofline of the core kernel (traced pass, same conditions) -----
     k_prof = min(args.steps, 20)
@@ -861,7 +862,9 @@ def run_batch64(args, rank, world, local_rank):
                      "frac": achieved / bf16_peak, "traffic": None,
                      "kernel": "whole batch (compression, core and expansion of three operators)",
                      "flops_per_unit": "2 r^2 per box pair and rhs"},
-        "clocks": clocks, "e2e": None, "gpu_launches": (18 if args.precision == "f16x3" else 15) * args.steps,
+        # per operator: split + compression, split + expansion; one grouped core
+        # launch where the plans allow it (f16x3, split3, bf16), else one per operator
+        "clocks": clocks, "e2e": None, "gpu_launches": (13 if args.precision != "split6" else 15) * args.steps,
         "cpu_baseline": None,
     }
     if rank == 0:

@@ -89,10 +89,12 @@ extern "C" {
 #define KIFMM_PREC_SPLIT3      2    /* 2-piece BF16 split, 3 products (hi*hi+hi*lo+lo*hi)  */
 #define KIFMM_PREC_SPLIT6      3    /* 3-piece BF16 split, 6 products (all terms <= 2^-16)  */
 #define KIFMM_PREC_F16X3       4    /* 2-piece FP16 split with per-box scaling, 3 products:
-                                       every q~ row is scaled by the power of two that puts
-                                       its largest entry in [2^14, 2^15), the cores by one
-                                       that puts theirs in [2^13, 2^14), so both FP16 pieces
-                                       stay normal where they matter; dropped terms <= 2^-22.
+                                       every q~ row is scaled by a power of two that keeps
+                                       its entries below 2^15 (from sqrt(n) max|q| >= |q|
+                                       >= |q~_i|; the point-source passes use q~'s largest
+                                       entry), the cores by one that puts their largest
+                                       entry in [2^13, 2^14), so both FP16 pieces stay
+                                       normal where they matter; dropped terms <= 2^-22.
                                        apply, apply_levels (and adjoints), apply_batch,
                                        stage 2 (its factors and the rank-k_o intermediate
                                        scaled the same way) and point-source evaluation;

@@ -193,7 +193,7 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
     const bool f16_core = plan->prm.precision == KIFMM_PREC_F16X3;
     const long piece_stride = (rows + 1) * rp;
     KIFMM_CUDA_TRY(plan->pt.ensure((size_t)rows * rp));
-    if (fp32_core || f16_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
+    if (fp32_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
     if (!fp32_core) KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
     if (f16_core) KIFMM_CUDA_TRY(plan->qs.ensure((size_t)rows + 1));
 
@@ -202,12 +202,12 @@ int apply_compressed(kifmm_m2l_plan plan, int instance, int level, int nrhs, con
     const long vtiles = (rows + 127) / 128;
     KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, f16_core ? 3 : 2);
+        StageTimer timer(plan, s, 0, 2);
         st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
-                          (fp32_core || f16_core) ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
+                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s, f16_core ? plan->qs.ptr : nullptr);
         if (st != KIFMM_OK) return st;
         if (f16_core) {
-            st = split_core_operand_f16(plan, plan->qt.ptr, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
+            st = zero_core_operand_row_f16(plan, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
             if (st != KIFMM_OK) return st;
         }
     }
@@ -314,7 +314,7 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
     const bool f16_core = plan->prm.precision == KIFMM_PREC_F16X3;
     const long piece_stride = (rows + 1) * rp;
     KIFMM_CUDA_TRY(plan->pt.ensure((size_t)rows * rp));
-    if (fp32_core || f16_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
+    if (fp32_core) KIFMM_CUDA_TRY(plan->qt.ensure((size_t)rows * rp));
     if (!fp32_core) KIFMM_CUDA_TRY(plan->qb.ensure((size_t)piece_stride * plan->pieces));
     if (f16_core) KIFMM_CUDA_TRY(plan->qs.ensure((size_t)rows + 1));
     TileSet* ts = nullptr;
@@ -323,12 +323,12 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
     const long vtiles = (rows + 127) / 128;
     KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, f16_core ? 3 : 2);
+        StageTimer timer(plan, s, 0, 2);
         st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
-                          (fp32_core || f16_core) ? plan->qt.ptr : nullptr, plan->pt.ptr, s);
+                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s, f16_core ? plan->qs.ptr : nullptr);
         if (st != KIFMM_OK) return st;
         if (f16_core) {
-            st = split_core_operand_f16(plan, plan->qt.ptr, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
+            st = zero_core_operand_row_f16(plan, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
             if (st != KIFMM_OK) return st;
         }
     }
@@ -411,6 +411,15 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
     return KIFMM_OK;
 }
 
+int zero_core_operand_row_f16(kifmm_m2l_plan plan, long rows, __nv_bfloat16* qb, long piece_stride, float* qs,
+                              cudaStream_t s) {
+    const int rp = plan->rp;
+    for (int pc = 0; pc < 2; ++pc)
+        KIFMM_CUDA_TRY(cudaMemsetAsync(qb + pc * piece_stride + rows * rp, 0, rp * sizeof(__nv_bfloat16), s));
+    KIFMM_CUDA_TRY(cudaMemsetAsync(qs + rows, 0, sizeof(float), s));
+    return KIFMM_OK;
+}
+
 int split_core_operand_f16(kifmm_m2l_plan plan, const float* qt, long rows, __nv_bfloat16* qb, long piece_stride,
                            float* qs, cudaStream_t s) {
     const int rp = plan->rp;
@@ -471,11 +480,12 @@ size_t split_elems(kifmm_m2l_plan plan, long n_tiles) {
 }
 
 int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* segs, int n_segs, int n_tiles,
-                 __nv_bfloat16* split, __nv_bfloat16* qb, long qb_stride, float* qt, float* pt, cudaStream_t s) {
+                 __nv_bfloat16* split, __nv_bfloat16* qb, long qb_stride, float* qt, float* pt, cudaStream_t s,
+                 float* f16_inv) {
     if (n_tiles <= 0) return KIFMM_OK;
     const int n = plan->n, np = plan->n_pad, rp = plan->rp;
     const long sp_stride = (long)n_tiles * 128 * np;
-    KIFMM_CUDA_TRY(launch_split_rows(x, m_rows, n, n, np, segs, n_segs, n_tiles, split, sp_stride, 3, s));
+    KIFMM_CUDA_TRY(launch_split_rows(x, m_rows, n, n, np, segs, n_segs, n_tiles, split, sp_stride, 3, s, 1, f16_inv));
     UmmaArgs a{};
     a.A = split;
     a.a_piece_stride = sp_stride;
@@ -494,7 +504,12 @@ int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* 
     a.alpha = 1.0f;
     a.Dp = qt ? nullptr : qb;
     a.dp_piece_stride = qb_stride;
-    a.dp_pieces = qt ? 0 : plan->pieces;
+    a.dp_pieces = qt ? 0 : (f16_inv ? 2 : plan->pieces);
+    // f16x3: q~ rows as two FP16 pieces after the power of two of the input
+    // row's 2-norm (|q~_i| <= ||q~|| <= ||q|| with orthonormal R~ columns, so
+    // the pieces stay below 2^15), written by the GEMM itself
+    a.dp_f16 = f16_inv ? 1 : 0;
+    a.dp_row_inv = f16_inv;
     a.Df = qt;
     a.Z = pt;
     a.n_products = 6;

@@ -48,7 +48,7 @@ struct PlanGroup {
     DevBuf<__nv_bfloat16> qb;     // pieces of q~ [pieces][rows_total + 1][r_pad]
     DevBuf<__nv_bfloat16> sp;     // BF16 pieces of the compression / expansion inputs
     DevBuf<float> pt;             // p~ [rows_total][r_pad]
-    DevBuf<float> qt, qs;         // f16x3: q~ in FP32 [rows_total][r_pad], row factors [rows_total + 1]
+    DevBuf<float> qs;             // f16x3: inverse row factors of the q~ pieces [rows_total + 1]
 };
 
 struct BatchEntry {
@@ -121,7 +121,6 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     KIFMM_CUDA_TRY(g.qb.ensure((size_t)(rows + 1) * plan->rp * std::max(plan->pieces, 1)));
     KIFMM_CUDA_TRY(g.sp.ensure(split_elems(plan, tiles_so_far)));
     if (plan->prm.precision == KIFMM_PREC_F16X3) {
-        KIFMM_CUDA_TRY(g.qt.ensure((size_t)std::max<long>(rows, 1) * plan->rp));
         KIFMM_CUDA_TRY(g.qs.ensure((size_t)rows + 1));
     }
     for (size_t i = 0; i < seg_out.size(); ++i) seg_out[i].Af = g.pt.ptr + ip[i].base * plan->rp;
@@ -163,8 +162,8 @@ int build_group(PlanGroup& g, const kifmm_m2l_batch_item* items) {
     return KIFMM_OK;
 }
 
-// Split and compression of one plan group (plus the scaled FP16 split for
-// f16x3): the core's q~ pieces, p~ cleared.
+// Split and compression of one plan group (for f16x3 the GEMM writes the
+// scaled FP16 pieces itself): the core's q~ pieces, p~ cleared.
 int enqueue_compress(PlanGroup& g, cudaStream_t s) {
     kifmm_m2l_plan plan = g.plan;
     const int rp = plan->rp;
@@ -172,11 +171,11 @@ int enqueue_compress(PlanGroup& g, cudaStream_t s) {
     const long piece_stride = (g.rows_total + 1) * rp;
     {
         const int st = run_compress(plan, nullptr, 0, g.seg_in.ptr, (int)g.items.size(), g.in_tiles, g.sp.ptr,
-                                    g.qb.ptr, piece_stride, f16 ? g.qt.ptr : nullptr, g.pt.ptr, s);
+                                    g.qb.ptr, piece_stride, nullptr, g.pt.ptr, s, f16 ? g.qs.ptr : nullptr);
         if (st != KIFMM_OK) return st;
     }
     if (f16) {
-        const int st = split_core_operand_f16(plan, g.qt.ptr, g.rows_total, g.qb.ptr, piece_stride, g.qs.ptr, s);
+        const int st = zero_core_operand_row_f16(plan, g.rows_total, g.qb.ptr, piece_stride, g.qs.ptr, s);
         if (st != KIFMM_OK) return st;
     } else {
         for (int pc = 0; pc < plan->pieces; ++pc)

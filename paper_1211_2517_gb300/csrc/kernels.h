@@ -115,9 +115,14 @@ enum UmmaEMode { E_RED = 0, E_STORE = 1, E_SPLIT = 2 };
 // [128 t, 128 t + 128) of m_rows) or of the segment that owns tile t.
 // Output rows past the input's rows are zeroed, or left alone when
 // pad_rows == 0.
+// With row_inv set, a bound on each input row's 2-norm also gives its power
+// of two for an FP16 split after a product with orthonormal columns:
+// ||x|| <= sqrt(cols) max |x| < 2^(e + 1) with e the exponent of max |x| plus
+// ceil(log2 sqrt(cols)); row_inv[out row] = 2^(e - 14) (e clamped to
+// [-112, 127]), the out row being the segment's out_row + its row (or the row).
 cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int ldo, const RowSeg* segs, int n_segs,
                               int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream,
-                              int pad_rows = 1);
+                              int pad_rows = 1, float* row_inv = nullptr);
 
 struct UmmaArgs {
     // A operand
@@ -164,6 +169,8 @@ struct UmmaArgs {
     float alpha, beta;
     int n_valid;              // E_STORE: columns < n_valid are written
     __nv_bfloat16* Dp;        // E_SPLIT: pieces [piece][m_rows][ldd]
+    int dp_f16;               // E_SPLIT: Dp holds 2 FP16 pieces of each output row times 1 / dp_row_inv[row]
+    const float* dp_row_inv;  // E_SPLIT with dp_f16: per output row, the inverse of its power of two
     long dp_piece_stride;
     int dp_pieces;
     float* Df;                // E_SPLIT: optional FP32 copy [m_rows][ldd]

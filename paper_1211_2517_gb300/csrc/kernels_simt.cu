@@ -157,12 +157,16 @@ __global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int col
 // with each piece rounded to nearest from the remaining residual.
 __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int lda, int cols, int ldo,
                                   const RowSeg* __restrict__ segs, int n_segs, __nv_bfloat16* __restrict__ out,
-                                  long piece_stride, int pieces, int pad_rows) {
+                                  long piece_stride, int pieces, int pad_rows, float* __restrict__ row_inv,
+                                  int norm_shift) {
     const int t = blockIdx.x;  // virtual tile; blockIdx.y: 16-row slab of it
     __shared__ int s_seg;
+    __shared__ unsigned s_max[16];  // row_inv: bits of the slab rows' largest |x| (ordered as integers)
     const float* src = A;
     int m = m_rows;
     long r0 = (long)t * 128;
+    long out0 = r0;  // output row of the tile's first row
+    if (row_inv && threadIdx.x < 16) s_max[threadIdx.x] = 0u;
     if (n_segs > 0) {
         if (threadIdx.x == 0) {
             int lo = 0, hi = n_segs - 1;
@@ -178,7 +182,9 @@ __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int l
         src = sg.Af;
         m = sg.m_rows;
         r0 = (long)(t - sg.tile_begin) * 128;
+        out0 = sg.out_row + r0;
     }
+    if (row_inv) __syncthreads();
     const int c4n = ldo / 4;
     for (int e = threadIdx.x; e < 16 * c4n; e += blockDim.x) {
         const int r = blockIdx.y * 16 + e / c4n, c = (e % c4n) * 4;
@@ -186,6 +192,9 @@ __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int l
         if (!pad_rows && row >= m) continue;
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < m && c < cols) x = __ldg(reinterpret_cast<const float4*>(src + row * lda + c));
+        if (row_inv && row < m)
+            atomicMax(&s_max[r - blockIdx.y * 16],
+                      __float_as_uint(fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w)))));
         __nv_bfloat16* o = out + ((long)t * 128 + r) * ldo + c;
         for (int p = 0; p < pieces; ++p) {
             const __nv_bfloat162 a = __floats2bfloat162_rn(x.x, x.y), b = __floats2bfloat162_rn(x.z, x.w);
@@ -197,6 +206,18 @@ __global__ void split_rows_kernel(const float* __restrict__ A, int m_rows, int l
             x.y -= __high2float(a);
             x.z -= __low2float(b);
             x.w -= __high2float(b);
+        }
+    }
+    if (row_inv) {
+        // |q~_i| <= ||q|| <= sqrt(cols) max |x| < 2^(e + 1 + norm_shift) with
+        // max |x| in [2^e, 2^(e+1)): the row's power of two 2^(14 - e - norm_shift)
+        __syncthreads();
+        const long row = r0 + blockIdx.y * 16 + threadIdx.x;
+        if (threadIdx.x < 16 && row < m) {
+            const unsigned mb = s_max[threadIdx.x];
+            int e = mb ? (int)((mb >> 23) & 0xFF) - 127 + norm_shift : 0;
+            e = max(-112, min(127, e));  // the power of two and its inverse both normal
+            row_inv[out0 + blockIdx.y * 16 + threadIdx.x] = __int_as_float((127 + e - 14) << 23);
         }
     }
 }
@@ -288,11 +309,13 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, int ld, __nv_b
 
 cudaError_t launch_split_rows(const float* A, int m_rows, int lda, int cols, int ldo, const RowSeg* segs, int n_segs,
                               int n_tiles, __nv_bfloat16* out, long piece_stride, int pieces, cudaStream_t stream,
-                              int pad_rows) {
+                              int pad_rows, float* row_inv) {
     if (n_tiles <= 0) return cudaSuccess;
     if ((lda & 3) || (cols & 3) || (ldo & 3) || cols > ldo || pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
+    int shift = 0;  // ceil(log2 sqrt(cols))
+    while ((1L << (2 * shift)) < (long)cols) ++shift;
     split_rows_kernel<<<dim3((unsigned)n_tiles, 8), 256, 0, stream>>>(A, m_rows, lda, cols, ldo, segs, n_segs, out,
-                                                                      piece_stride, pieces, pad_rows);
+                                                                      piece_stride, pieces, pad_rows, row_inv, shift);
     return cudaGetLastError();
 }
 

@@ -553,6 +553,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     e_beta = sg.beta;
                 }
                 orow = r < mrows ? (EMODE == E_SPLIT ? obase + r : r) : -1;
+                // FP16 pieces: this row times its power of two
+                if (EMODE == E_SPLIT && args.dp_f16 && orow >= 0) rsc = 1.f / __ldg(args.dp_row_inv + orow);
             }
             const int n0 = item_n0(item), nthis = item_nthis(item);
             const int nch = (nthis + 31) / 32;
@@ -693,8 +695,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (args.Z)
                                 *reinterpret_cast<float4*>(args.Z + grow * args.ldd + col) = make_float4(0.f, 0.f, 0.f, 0.f);
                             uint32_t lo[3], hi[3];
-                            split3x2(x.x, x.y, lo, args.dp_pieces);
-                            split3x2(x.z, x.w, hi, args.dp_pieces);
+                            if (args.dp_f16) {
+                                const __half2 a = __floats2half2_rn(x.x, x.y), b = __floats2half2_rn(x.z, x.w);
+                                const __half2 al = __floats2half2_rn(x.x - __low2float(a), x.y - __high2float(a));
+                                const __half2 bl = __floats2half2_rn(x.z - __low2float(b), x.w - __high2float(b));
+                                lo[0] = *reinterpret_cast<const uint32_t*>(&a);
+                                hi[0] = *reinterpret_cast<const uint32_t*>(&b);
+                                lo[1] = *reinterpret_cast<const uint32_t*>(&al);
+                                hi[1] = *reinterpret_cast<const uint32_t*>(&bl);
+                                lo[2] = hi[2] = 0u;
+                            } else {
+                                split3x2(x.x, x.y, lo, args.dp_pieces);
+                                split3x2(x.z, x.w, hi, args.dp_pieces);
+                            }
 #pragma unroll
                             for (int pc = 0; pc < 3; ++pc) {
                                 if (pc >= args.dp_pieces) break;

@@ -232,8 +232,12 @@ void detach_fmms(kifmm_m2l_plan plan);
 // pieces in `split` (>= 3 * 128 * n_tiles * n_pad elements), then a
 // tensor-core GEMM writes q~ as `pieces` BF16 pieces into qb (piece stride
 // qb_stride; or FP32 into qt when qt != nullptr) and zeroes p~ rows of pt.
+// With f16_inv set (f16x3 core), qb receives two FP16 pieces of every q~ row
+// times the power of two of its input row's 2-norm, f16_inv[row] its
+// inverse (qt must then be NULL).
 int run_compress(kifmm_m2l_plan plan, const float* x, int m_rows, const RowSeg* segs, int n_segs, int n_tiles,
-                 __nv_bfloat16* split, __nv_bfloat16* qb, long qb_stride, float* qt, float* pt, cudaStream_t s);
+                 __nv_bfloat16* split, __nv_bfloat16* qb, long qb_stride, float* qt, float* pt, cudaStream_t s,
+                 float* f16_inv = nullptr);
 // Expansion (p = alpha U~ p~ + beta p): the FP32 p~ rows (pt, ld r_pad, or
 // segments) are split into BF16 pieces in `split` (>= 3 * 128 * n_tiles *
 // r_pad elements), then a tensor-core GEMM writes y (ld n) or, with
@@ -254,6 +258,9 @@ int launch_core(kifmm_m2l_plan plan, const __nv_bfloat16* qb, long piece_stride,
 // F16X3 operand of the core: q~ (FP32 rows [rows][rp] in qt) -> two scaled
 // FP16 pieces in qb (piece stride piece_stride, row `rows` zero) and the
 // row factors 1 / sigma in qs[0..rows] (qs[rows] = 0).
+// The zero row (index rows) of the f16x3 core operand and its factor.
+int zero_core_operand_row_f16(kifmm_m2l_plan plan, long rows, __nv_bfloat16* qb, long piece_stride, float* qs,
+                              cudaStream_t s);
 int split_core_operand_f16(kifmm_m2l_plan plan, const float* qt, long rows, __nv_bfloat16* qb, long piece_stride,
                            float* qs, cudaStream_t s);
 // Upload value_at(e), e < per, as 3 BF16 pieces [3][per] (piece j = RN of
