@@ -82,6 +82,8 @@ struct Layout {
     int prod_warps;  // A_GATHER: producer warps in use; divides `stages`
     int drain;       // A_GATHER: K-chunks per partial drained by 8 epilogue warps (0: no drain; see the epilogue)
     int dhilo;       // drained partials keep the (0,0) product in its own half of the slot (2 N columns per slot)
+    int a_tma;       // identity-row gathers: the A pieces by TMA (amap) instead of per-lane cp.async
+    int a_rows;      // rows of one A piece in amap
     uint32_t a_bytes, c_bytes, stage_bytes, trans_off;
 };
 
@@ -116,7 +118,8 @@ __device__ __forceinline__ void split3x2(float x, float y, uint32_t (&h)[3], int
 
 template <int AMODE, int EMODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    umma_kernel(const __grid_constant__ CUtensorMap bmap, const UmmaArgs args, const Layout L) {
+    umma_kernel(const __grid_constant__ CUtensorMap bmap, const __grid_constant__ CUtensorMap amap, const UmmaArgs args,
+                const Layout L) {
     extern __shared__ __align__(1024) uint8_t smem_dyn[];
     uint8_t* smem_raw = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
     Smem* sm = reinterpret_cast<Smem*>(smem_raw);
@@ -248,6 +251,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!mbar_wait(&sm->empty[s], ph ^ 1u, sm, args.error_flag)) {
                         ok = false;
                         break;
+                    }
+                    if (L.a_tma) {
+                        // identity rows: the tile's 128 rows of every piece as
+                        // one TMA box each (columns past kdim read as zero); lane
+                        // 0 arrives twice (A and B bytes), the other lanes once
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(&sm->full[s], (uint32_t)L.na * L.a_bytes);
+                            const int t = item_tile(item);
+                            for (int pc = 0; pc < L.na; ++pc)
+                                tma_load_2d(a_smem(s, pc), &amap, kc * CH, pc * L.a_rows + t * kTileM, &sm->full[s]);
+                            issue_b(s, item, kc);
+                        } else {
+                            mbar_arrive(&sm->full[s]);
+                        }
+                        continue;
                     }
                     const int col = kc * CH + cch * 8;
                     const uint32_t bytes = col < args.kdim ? 16u : 0u;
@@ -1879,8 +1897,8 @@ cudaError_t get_bmap(const UmmaArgs& a, cuuint64_t rows_total, int ch, int box_r
 }
 
 template <int AM, int EM>
-cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L, size_t smem, int grid,
-                     cudaStream_t stream, int dev) {
+cudaError_t launch_t(const CUtensorMap& bmap, const CUtensorMap& amap, const UmmaArgs& a, const Layout& L, size_t smem,
+                     int grid, cudaStream_t stream, int dev) {
     const int inst = AM == A_GATHER ? (EM == E_RED ? 0 : (EM == E_STORE ? 7 : 8)) : (EM == E_STORE ? 1 : 2);
     {
         std::lock_guard<std::mutex> lock(g_cache_mutex);
@@ -1891,7 +1909,7 @@ cudaError_t launch_t(const CUtensorMap& bmap, const UmmaArgs& a, const Layout& L
             g_smem_granted[inst][dev] = (int)smem;
         }
     }
-    umma_kernel<AM, EM><<<grid, kThreads, smem, stream>>>(bmap, a, L);
+    umma_kernel<AM, EM><<<grid, kThreads, smem, stream>>>(bmap, amap, a, L);
     return cudaGetLastError();
 }
 
@@ -2128,11 +2146,21 @@ cudaError_t launch_umma(int amode, int emode, const UmmaArgs& a, int num_sms, cu
     if (ce != cudaSuccess) return ce;
 
     const int grid = num_sms < L.n_items ? num_sms : L.n_items;
-    if (gather && emode == E_STORE) return launch_t<A_GATHER, E_STORE>(bmap, a, L, smem, grid, stream, dev);
-    if (gather && emode == E_SPLIT) return launch_t<A_GATHER, E_SPLIT>(bmap, a, L, smem, grid, stream, dev);
-    if (gather) return launch_t<A_GATHER, E_RED>(bmap, a, L, smem, grid, stream, dev);
-    if (emode == E_STORE) return launch_t<A_ROWS, E_STORE>(bmap, a, L, smem, grid, stream, dev);
-    return launch_t<A_ROWS, E_SPLIT>(bmap, a, L, smem, grid, stream, dev);
+    // identity-row gathers read the A pieces as TMA boxes of 128 rows: the
+    // pieces [na][a_rows][kdim] as one 2D tensor
+    CUtensorMap amap = bmap;
+    L.a_tma = 0;
+    if (gather && a.row_identity && a.a_piece_stride % a.kdim == 0) {
+        L.a_rows = (int)(a.a_piece_stride / a.kdim);
+        ce = get_map2d(a.A, (cuuint64_t)L.na * L.a_rows, a.kdim, ch, kTileM, encode, &amap);
+        if (ce != cudaSuccess) return ce;
+        L.a_tma = 1;
+    }
+    if (gather && emode == E_STORE) return launch_t<A_GATHER, E_STORE>(bmap, amap, a, L, smem, grid, stream, dev);
+    if (gather && emode == E_SPLIT) return launch_t<A_GATHER, E_SPLIT>(bmap, amap, a, L, smem, grid, stream, dev);
+    if (gather) return launch_t<A_GATHER, E_RED>(bmap, amap, a, L, smem, grid, stream, dev);
+    if (emode == E_STORE) return launch_t<A_ROWS, E_STORE>(bmap, amap, a, L, smem, grid, stream, dev);
+    return launch_t<A_ROWS, E_SPLIT>(bmap, amap, a, L, smem, grid, stream, dev);
 }
 
 }  // namespace kifmm
