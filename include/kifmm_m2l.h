@@ -212,6 +212,22 @@ int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int 
 int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                                    const float* pbar_down, float* qbar_up, float beta, void* stream);
 
+/* kifmm_m2l_apply_levels (Eq. (14), Sec. 3.1, over several levels) on HOST
+ * buffers: q_up_host and p_down_host are HOST float32 arrays laid out as the
+ * device buffers of kifmm_m2l_apply_levels (page-locked memory lets the
+ * copies run asynchronously; pageable memory works, with synchronous
+ * copies).  The rows travel in up to four chunks of whole 128-row tiles on
+ * a copy stream of the plan; each chunk's split and compression start as
+ * soon as it has landed, and each chunk of the expansion's output goes back
+ * as soon as it is written, so the copies overlap the compression and the
+ * expansion.  Every copy and kernel is ordered on `stream`: p_down_host is
+ * complete when work enqueued on `stream` afterwards starts, or after
+ * kifmm_m2l_sync.  beta != 0 first copies p_down_host in.  The plan keeps
+ * device copies of both arrays (2 x rows x n floats) until destroyed.  The
+ * host arrays must stay valid until the stream has passed the call. */
+int kifmm_m2l_apply_levels_host(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                                const float* q_up_host, float* p_down_host, float beta, void* stream);
+
 /* One FMM instance's share of a batch: levels level_lo..level_hi of
  * `instance` of `plan`, nrhs right-hand sides, DEVICE buffers laid out as
  * for kifmm_m2l_apply_levels, p_down = beta * p_down + M2L(q_up). */

@@ -31,6 +31,7 @@ EXPORTED = (
     "kifmm_m2l_precompute", "kifmm_m2l_destroy", "kifmm_m2l_plan_rank", "kifmm_m2l_set_level",
     "kifmm_m2l_level_pairs", "kifmm_m2l_apply", "kifmm_m2l_apply_adjoint", "kifmm_m2l_apply_dense", "kifmm_m2l_apply_dense_tc",
     "kifmm_m2l_apply_noalloc", "kifmm_m2l_apply_levels", "kifmm_m2l_apply_levels_adjoint",
+    "kifmm_m2l_apply_levels_host",
     "kifmm_m2l_apply_batch",
     "kifmm_m2l_set_stage2", "kifmm_m2l_stage2_ranks", "kifmm_m2l_stage2_host",
     "kifmm_m2l_sync", "kifmm_m2l_set_wait_limit", "kifmm_m2l_profile_enable", "kifmm_m2l_profile_read", "kifmm_m2l_autotune",
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "kifmm_m2l_apply_noalloc": [vp, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_levels": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_levels_adjoint": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
+        "kifmm_m2l_apply_levels_host": [vp, i32, i32, i32, i32, vp, vp, f32, vp],
         "kifmm_m2l_apply_batch": [i32, ctypes.POINTER(BatchItem), i32, vp],
         "kifmm_m2l_sync": [vp, vp],
         "kifmm_m2l_set_wait_limit": [vp, ctypes.c_ulonglong],

@@ -270,8 +270,13 @@ int get_multi_tiles(MultiState& ms, int nrhs, TileSet** out) {
 // Levels lo..hi of one instance in five launches: split and compression of
 // all their rows, one core over the merged offset-ordered tiles (each tile
 // scaled by its level's s_l), split and expansion of all rows.
+// With x_host / y_host set, the densities are HOST buffers: the rows reach
+// the device in chunks on the plan's copy stream, each chunk's split and
+// compression starting as soon as it has landed, and the expansion hands
+// each chunk of results back the same way, so the copies overlap the
+// compression and the expansion.
 int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, const float* x_in, float* y_out,
-                 float beta, void* stream, bool adjoint) {
+                 float beta, void* stream, bool adjoint, const float* x_host = nullptr, float* y_host = nullptr) {
     if (!plan) {
         set_error("plan is NULL");
         return KIFMM_ERR_INVALID_ARG;
@@ -299,7 +304,8 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
     st = get_multi(plan, instance, lo, hi, adjoint, &ms);
     if (st != KIFMM_OK) return st;
     if (ms->total_boxes == 0) return KIFMM_OK;
-    if (!x_in || !y_out) {
+    const bool host = x_host != nullptr;
+    if (host ? !y_host : (!x_in || !y_out)) {
         set_error("NULL density pointer");
         return KIFMM_ERR_INVALID_ARG;
     }
@@ -309,6 +315,33 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
     if (rows + 1 > (long)INT32_MAX / 2) {
         set_error("too many box rows");
         return KIFMM_ERR_INVALID_ARG;
+    }
+    // host mode: device copies of the densities, chunks of whole 128-row tiles
+    const int n_chunks = host ? (int)std::min<long>(4, (rows + 127) / 128) : 1;
+    const long chunk_rows = ((rows + 127) / 128 + n_chunks - 1) / n_chunks * 128;
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> ev;
+    if (host) {
+        KIFMM_CUDA_TRY(plan->hx.ensure((size_t)rows * n));
+        KIFMM_CUDA_TRY(plan->hy.ensure((size_t)rows * n));
+        x_in = plan->hx.ptr;
+        y_out = plan->hy.ptr;
+        if (!plan->copy_stream) KIFMM_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+        cs = plan->copy_stream;
+        while (plan->sync_events.size() < (size_t)(2 * n_chunks + 2)) {
+            cudaEvent_t e = nullptr;
+            KIFMM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            plan->sync_events.push_back(e);
+        }
+        // events: 0 start / end, 1 .. n_chunks the inputs, n_chunks + 1 the
+        // copied-in p, n_chunks + 2 .. 2 n_chunks + 1 the outputs
+        ev = plan->sync_events;
+        // the copy stream starts after the work already on the caller's stream
+        KIFMM_CUDA_TRY(cudaEventRecord(ev[0], s));
+        KIFMM_CUDA_TRY(cudaStreamWaitEvent(cs, ev[0], 0));
+        if (beta != 0.f)
+            KIFMM_CUDA_TRY(cudaMemcpyAsync(plan->hy.ptr, y_host, (size_t)rows * n * sizeof(float),
+                                           cudaMemcpyHostToDevice, cs));
     }
     const bool fp32_core = plan->prm.precision == KIFMM_PREC_FP32;
     const bool f16_core = plan->prm.precision == KIFMM_PREC_F16X3;
@@ -323,14 +356,32 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
     const long vtiles = (rows + 127) / 128;
     KIFMM_CUDA_TRY(plan->sp.ensure(split_elems(plan, vtiles)));
     {
-        StageTimer timer(plan, s, 0, 2);
-        st = run_compress(plan, x_in, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, plan->qb.ptr, piece_stride,
-                          fp32_core ? plan->qt.ptr : nullptr, plan->pt.ptr, s, f16_core ? plan->qs.ptr : nullptr);
-        if (st != KIFMM_OK) return st;
+        StageTimer timer(plan, s, 0, 2 * n_chunks);
+        for (int c = 0; c < n_chunks; ++c) {
+            const long r0 = c * chunk_rows, mc = std::min(chunk_rows, rows - r0);
+            if (mc <= 0) break;
+            const long t0 = r0 / 128, tc = (mc + 127) / 128;
+            if (host) {
+                KIFMM_CUDA_TRY(cudaMemcpyAsync(plan->hx.ptr + r0 * n, x_host + r0 * n, (size_t)mc * n * sizeof(float),
+                                               cudaMemcpyHostToDevice, cs));
+                KIFMM_CUDA_TRY(cudaEventRecord(ev[1 + c], cs));
+                KIFMM_CUDA_TRY(cudaStreamWaitEvent(s, ev[1 + c], 0));
+            }
+            st = run_compress(plan, x_in + r0 * n, (int)mc, nullptr, 0, (int)tc,
+                              plan->sp.ptr + (size_t)3 * 128 * t0 * plan->n_pad, plan->qb.ptr + r0 * rp, piece_stride,
+                              fp32_core ? plan->qt.ptr + r0 * rp : nullptr, plan->pt.ptr + r0 * rp, s,
+                              f16_core ? plan->qs.ptr + r0 : nullptr);
+            if (st != KIFMM_OK) return st;
+        }
         if (f16_core) {
             st = zero_core_operand_row_f16(plan, rows, plan->qb.ptr, piece_stride, plan->qs.ptr, s);
             if (st != KIFMM_OK) return st;
         }
+    }
+    if (host && beta != 0.f) {
+        // the expansion accumulates into the copied-in p
+        KIFMM_CUDA_TRY(cudaEventRecord(ev[1 + n_chunks], cs));
+        KIFMM_CUDA_TRY(cudaStreamWaitEvent(s, ev[1 + n_chunks], 0));
     }
     ScaleTable scales{};
     for (int l = lo; l <= hi; ++l) {
@@ -352,9 +403,26 @@ int apply_levels(kifmm_m2l_plan plan, int instance, int lo, int hi, int nrhs, co
         if (st != KIFMM_OK) return st;
     }
     {
-        StageTimer timer(plan, s, 2, 2);
-        st = run_expand(plan, plan->pt.ptr, (int)rows, nullptr, 0, (int)vtiles, plan->sp.ptr, y_out, 1.0f, beta, s);
-        if (st != KIFMM_OK) return st;
+        StageTimer timer(plan, s, 2, 2 * n_chunks);
+        for (int c = 0; c < n_chunks; ++c) {
+            const long r0 = c * chunk_rows, mc = std::min(chunk_rows, rows - r0);
+            if (mc <= 0) break;
+            const long t0 = r0 / 128, tc = (mc + 127) / 128;
+            st = run_expand(plan, plan->pt.ptr + r0 * rp, (int)mc, nullptr, 0, (int)tc,
+                            plan->sp.ptr + (size_t)3 * 128 * t0 * rp, y_out + r0 * n, 1.0f, beta, s);
+            if (st != KIFMM_OK) return st;
+            if (host) {
+                KIFMM_CUDA_TRY(cudaEventRecord(ev[2 + n_chunks + c], s));
+                KIFMM_CUDA_TRY(cudaStreamWaitEvent(cs, ev[2 + n_chunks + c], 0));
+                KIFMM_CUDA_TRY(cudaMemcpyAsync(y_host + r0 * n, plan->hy.ptr + r0 * n, (size_t)mc * n * sizeof(float),
+                                               cudaMemcpyDeviceToHost, cs));
+            }
+        }
+    }
+    if (host) {
+        // the caller's stream covers every copy
+        KIFMM_CUDA_TRY(cudaEventRecord(ev[0], cs));
+        KIFMM_CUDA_TRY(cudaStreamWaitEvent(s, ev[0], 0));
     }
     return KIFMM_OK;
 }
@@ -1133,6 +1201,16 @@ int kifmm_m2l_apply_levels(kifmm_m2l_plan plan, int instance, int level_lo, int 
 int kifmm_m2l_apply_levels_adjoint(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
                                    const float* pbar_down, float* qbar_up, float beta, void* stream) {
     return apply_levels(plan, instance, level_lo, level_hi, nrhs, pbar_down, qbar_up, beta, stream, true);
+}
+
+int kifmm_m2l_apply_levels_host(kifmm_m2l_plan plan, int instance, int level_lo, int level_hi, int nrhs,
+                                const float* q_up_host, float* p_down_host, float beta, void* stream) {
+    if (!q_up_host || !p_down_host) {
+        set_error("NULL host density pointer");
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    return apply_levels(plan, instance, level_lo, level_hi, nrhs, nullptr, nullptr, beta, stream, false, q_up_host,
+                        p_down_host);
 }
 
 int kifmm_m2l_apply_dense(kifmm_m2l_plan plan, int instance, int level, int nrhs, const float* q_up, float* p_down,

@@ -194,12 +194,19 @@ struct kifmm_m2l_plan_s {
         cudaEventCreate(&e);
         return e;
     }
+    // host-buffer applies: device copies of the densities, a copy stream and
+    // events (timing off) that order the chunks' copies and kernels
+    kifmm::DevBuf<float> hx, hy;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> sync_events;
     ~kifmm_m2l_plan_s() {
         for (auto& r : recs) {
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
         }
         for (auto e : event_pool) cudaEventDestroy(e);
+        for (auto e : sync_events) cudaEventDestroy(e);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
     }
     // scratch shared by all levels (apply calls on one plan are serialised)
     kifmm::DevBuf<float> qt, pt;

@@ -197,6 +197,26 @@ class M2LPlan:
              _stream_handle(stream))
         return out
 
+    def apply_levels_host(self, x_all, level_lo: int, level_hi: int, out, instance: int = 0, beta: float = 0.0,
+                          stream=None):
+        """apply_levels on HOST float32 tensors (pin them for overlapped
+        copies): the library copies the rows in and the results out in
+        chunks that overlap the compression and the expansion, all ordered
+        on `stream`."""
+        import torch
+
+        nb = sum(self._levels[(instance, l)] for l in range(level_lo, level_hi + 1))
+        nrhs = 1 if x_all.dim() == 2 else x_all.shape[1]
+        shape = (nb, self.n) if x_all.dim() == 2 else (nb, nrhs, self.n)
+        for t, name in ((x_all, "input"), (out, "out")):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32:
+                raise TypeError(f"{name} must be a host float32 tensor")
+            if not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+                raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}")
+        call("kifmm_m2l_apply_levels_host", self._h, int(instance), int(level_lo), int(level_hi), int(nrhs),
+             ctypes.c_void_p(x_all.data_ptr()), ctypes.c_void_p(out.data_ptr()), float(beta), _stream_handle(stream))
+        return out
+
     def apply_dense(self, q_up, level: int, instance: int = 0, out=None, beta: float = 0.0, stream=None):
         """Uncompressed FP32 M2L (the baseline)."""
         return self._run("kifmm_m2l_apply_dense", q_up, level, instance, out, beta, stream)

@@ -414,6 +414,34 @@ def test_f16x3_scaling_extremes(g, oracle_factors, sphere_small):
     assert err <= 1e-6
 
 
+@pytest.mark.parametrize("precision", ["f16x3", "split6"])
+def test_apply_levels_host_matches_device(g, sphere_small, precision):
+    """kifmm_m2l_apply_levels_host (host buffers, chunked copies overlapping
+    the compression and expansion) against kifmm_m2l_apply_levels on device
+    buffers, levels 2-4 with 3 right-hand sides, beta = 0 and beta = 1 (the
+    latter doubles the host array); pinned and pageable host memory."""
+    tree, qs = sphere_small
+    plan = make_plan(g, 8, 1e-7, precision, tree, (2, 3, 4))
+    x = np.concatenate([qs[l] for l in (2, 3, 4)]).astype(np.float32)
+    ref = plan.apply_levels(torch.from_numpy(x).cuda(), 2, 4).cpu()
+    torch.cuda.synchronize()
+    for pin in (True, False):
+        hx = torch.from_numpy(x.copy())
+        hp = torch.full_like(hx, float("nan"))
+        if pin:
+            hx, hp = hx.pin_memory(), hp.pin_memory()
+        plan.apply_levels_host(hx, 2, 4, out=hp)
+        plan.sync()
+        err = float((hp - ref).double().norm() / ref.double().norm())
+        print(f"host apply {precision} pinned={pin}: rel L2 against the device apply {err:.3e}")
+        assert err < 1e-6, err
+        plan.apply_levels_host(hx, 2, 4, out=hp, beta=1.0)
+        plan.sync()
+        err2 = float((hp - 2 * ref).double().norm() / (2 * ref).double().norm())
+        assert err2 < 1e-6, err2
+    plan.close()
+
+
 def test_f16x3_unsupported_paths(g, sphere_small):
     """The allocation-free apply refuses f16x3 plans (its rows-mode kernels
     have no per-row FP16 scaling); nothing is written."""
