@@ -56,9 +56,15 @@ struct BatchEntry {
     bool one_core = false;  // the cores of all groups in one grouped launch
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture_stream = nullptr;
+    // the groups' launch chains run side by side on these streams, forked
+    // from and joined back into the caller's (or the capture) stream
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;
     ~BatchEntry() {
         if (exec) cudaGraphExecDestroy(exec);
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        for (auto x : side) cudaStreamDestroy(x);
+        for (auto x : ev) cudaEventDestroy(x);
     }
 };
 
@@ -248,38 +254,78 @@ bool one_core_launch(const BatchEntry& e) {
     return true;
 }
 
+// Fork: every side stream waits for the work already on s (event k).
+int fork_sides(BatchEntry& e, cudaStream_t s, int k) {
+    KIFMM_CUDA_TRY(cudaEventRecord(e.ev[k], s));
+    for (auto x : e.side) KIFMM_CUDA_TRY(cudaStreamWaitEvent(x, e.ev[k], 0));
+    return KIFMM_OK;
+}
+
+// Join: s waits for everything on the side streams (events k, k + 1, ...).
+int join_sides(BatchEntry& e, cudaStream_t s, int k) {
+    for (size_t i = 0; i < e.side.size(); ++i) {
+        KIFMM_CUDA_TRY(cudaEventRecord(e.ev[k + i], e.side[i]));
+        KIFMM_CUDA_TRY(cudaStreamWaitEvent(s, e.ev[k + i], 0));
+    }
+    return KIFMM_OK;
+}
+
 int enqueue_all(BatchEntry& e, cudaStream_t s) {
+    // group g's launches go to side stream g % k: the groups' small
+    // compressions and expansions (and, without a grouped core, their whole
+    // chains) overlap instead of queueing behind one another
+    const size_t k = std::min<size_t>(e.groups.size(), 4);
+    while (e.side.size() < k) {
+        cudaStream_t x = nullptr;
+        KIFMM_CUDA_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        e.side.push_back(x);
+    }
+    while (e.ev.size() < 3 * k + 2) {
+        cudaEvent_t x = nullptr;
+        KIFMM_CUDA_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        e.ev.push_back(x);
+    }
+    int st = fork_sides(e, s, 0);
+    if (st != KIFMM_OK) return st;
     if (!e.one_core) {
-        for (auto& g : e.groups) {
-            if (g->rows_total == 0) continue;
-            int st = enqueue_compress(*g, s);
+        for (size_t i = 0; i < e.groups.size(); ++i) {
+            PlanGroup& g = *e.groups[i];
+            cudaStream_t x = e.side[i % k];
+            if (g.rows_total == 0) continue;
+            st = enqueue_compress(g, x);
             if (st != KIFMM_OK) return st;
-            const UmmaArgs a = core_args(*g);
-            KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, g->plan->num_sms, s));
-            st = enqueue_expand(*g, s);
+            const UmmaArgs a = core_args(g);
+            KIFMM_CUDA_TRY(launch_umma(A_GATHER, E_RED, a, g.plan->num_sms, x));
+            st = enqueue_expand(g, x);
             if (st != KIFMM_OK) return st;
         }
-        return KIFMM_OK;
+        return join_sides(e, s, 1);
     }
     std::vector<UmmaArgs> args;
-    for (auto& g : e.groups) {
-        if (g->rows_total == 0) continue;
-        int st = enqueue_compress(*g, s);
+    for (size_t i = 0; i < e.groups.size(); ++i) {
+        PlanGroup& g = *e.groups[i];
+        if (g.rows_total == 0) continue;
+        st = enqueue_compress(g, e.side[i % k]);
         if (st != KIFMM_OK) return st;
-        args.push_back(core_args(*g));
+        args.push_back(core_args(g));
     }
+    st = join_sides(e, s, 1);
+    if (st != KIFMM_OK) return st;
     if (args.empty()) return KIFMM_OK;
     int dev = 0, max_smem = 0;
     KIFMM_CUDA_TRY(cudaGetDevice(&dev));
     KIFMM_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     KIFMM_CUDA_TRY(launch_core_stage_grouped(args.data(), (int)args.size(), e.groups[0]->plan->num_sms, max_smem,
                                              dev, s));
-    for (auto& g : e.groups) {
-        if (g->rows_total == 0) continue;
-        int st = enqueue_expand(*g, s);
+    st = fork_sides(e, s, 1 + k);
+    if (st != KIFMM_OK) return st;
+    for (size_t i = 0; i < e.groups.size(); ++i) {
+        PlanGroup& g = *e.groups[i];
+        if (g.rows_total == 0) continue;
+        st = enqueue_expand(g, e.side[i % k]);
         if (st != KIFMM_OK) return st;
     }
-    return KIFMM_OK;
+    return join_sides(e, s, 2 + k);
 }
 
 }  // namespace
