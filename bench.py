@@ -647,7 +647,7 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:  # a secondary leg: reported, the headline line still prints
             yukawa = {"error": f"{type(exc).__name__}: {exc}"}
 
-    # ---- config 3 (p = 10 torus) and config 4 (64-instance batch) ----------
+    # ---- the p = 10 torus and the 64-instance batch -------------------------
     torus = batch64 = None
     if args.precision != "fp32" and not args.no_extra and "torus" in legs:
         try:
@@ -664,8 +664,9 @@ def run_ours(args, rank, world, local_rank):
                                     "frac": bach / bf16_peak, "flops_per_unit": "2 r^2 per box pair and rhs",
                                     "time": "whole batch (compression, core and expansion of three operators)"},
                        "parity": "tests/test_gpu_m2l.py::test_batch64_full_config",
-                       "arithmetic": "config 4 names FP32; the batch runs the plan's tensor-core arithmetic "
-                                     f"({args.precision}), which meets the FP32 gate of 1e-6 against the oracle"}
+                       "arithmetic": "the batch64 workload is stated in FP32; the batch runs the plan's "
+                                     f"tensor-core arithmetic ({args.precision}), which meets the FP32 gate of 1e-6 "
+                                     "against the oracle"}
         except Exception as exc:
             batch64 = {"error": f"{type(exc).__name__}: {exc}"}
 
@@ -714,7 +715,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 def torus_measure(args, dev, steps, peak):
-    """Config 3: the 4,194,304-point torus (R = 1, r = 0.3), depth 6, p = 10,
+    """The 4,194,304-point torus (R = 1, r = 0.3), depth 6, p = 10,
     eps = 1e-8 (r = 271, r_pad = 272: the core splits N in two parts), levels
     2-6 in one apply per step; the core's roofline with 2 r^2 FLOPs per pair."""
     import numpy as np
@@ -771,7 +772,7 @@ def torus_measure(args, dev, steps, peak):
 
 
 def batch64_measure(args, rank, world, dev, steps, warmup, sample_clocks):
-    """Config 4: 64 ellipsoid instances (N log-uniform 5e4-1e6, depth 3-6,
+    """64 ellipsoid instances (N log-uniform 5e4-1e6, depth 3-6,
     p in {6, 8, 10}, 16 rhs), all M2L levels, one grouped batch replayed from a
     CUDA graph per step (rank k takes instances 64 k .. 64 k + 63).  Returns
     (units per second over all ranks, slowest rank's ms, units, achieved
